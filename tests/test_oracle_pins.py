@@ -1,0 +1,427 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Every check here is independent of the oracle's own arithmetic: closed-form
+values of the sparse kernel (Eq. kernel), exact quadratures, brute-force
+all-pairs sums (Eq. alpha_kernel) written with numpy, Dirichlet moments from
+scipy (Eq. mode, Eq. variance), the binary counting/BKI special case
+(Sec. III), and finite differences of the oracle's own forward for its
+analytic gradient.  None of them needs a GPU.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate, optimize, stats
+
+from synth import scenes
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- kernel (Eq. kernel)
+
+def test_kernel_closed_form_values(orc):
+    # f(0) = 1 (k = sigma0 at d = 0), f(1/2) = 1/6, f(r >= 1) = 0
+    assert orc.kernel_f(0.0) == pytest.approx(1.0, abs=1e-15)
+    assert orc.kernel_f(0.5) == pytest.approx(1.0 / 6.0, abs=1e-15)
+    for r in (1.0, 1.0 + 1e-12, 1.5, 10.0):
+        assert orc.kernel_f(r) == 0.0
+    # FP64 cancellation near r = 1 leaves at most a few 1e-16 below zero
+    assert orc.kernel_f(1.0 - 1e-9) >= -1e-15
+
+
+def test_kernel_zero_slope_and_fifth_order_contact(orc):
+    h = 1e-6
+    assert (orc.kernel_f(h) - orc.kernel_f(0.0)) / h == pytest.approx(0.0, abs=1e-5)
+    # near r = 1 the kernel touches zero to fifth order: f ~ (4 pi^4 / 45) (1 - r)^5
+    for eps in (1e-2, 3e-3):
+        assert orc.kernel_f(1.0 - eps) / eps ** 5 == pytest.approx(4 * math.pi ** 4 / 45, rel=2e-2)
+    assert orc.kernel_df(0.0) == pytest.approx(0.0, abs=1e-14)
+    assert orc.kernel_df(1.0 - 1e-9) == pytest.approx(0.0, abs=1e-12)
+
+
+def test_kernel_monotone_nonnegative_and_derivative(orc):
+    r = np.linspace(0.0, 1.0, 2001)
+    f = np.array([orc.kernel_f(x) for x in r])
+    assert np.all(f >= -1e-15)
+    assert np.all(np.diff(f) <= 1e-15)
+    # derivative agrees with a central difference of f
+    rng = np.random.default_rng(0)
+    for x in rng.uniform(0.01, 0.99, size=50):
+        h = 1e-6
+        fd = (orc.kernel_f(x + h) - orc.kernel_f(x - h)) / (2 * h)
+        assert orc.kernel_df(x) == pytest.approx(fd, abs=1e-8)
+
+
+def test_kernel_integrals(orc):
+    # exact: int_0^1 f dr = 1/3 ; ball integral int_{|u|<1} f(|u|) du = 2 (pi^2 - 6) / (9 pi)
+    i1, _ = integrate.quad(orc.kernel_f, 0.0, 1.0, epsabs=1e-13)
+    assert i1 == pytest.approx(1.0 / 3.0, abs=1e-12)
+    i3, _ = integrate.quad(lambda r: 4 * math.pi * r * r * orc.kernel_f(r), 0.0, 1.0, epsabs=1e-13)
+    assert i3 == pytest.approx(2 * (math.pi ** 2 - 6) / (9 * math.pi), abs=1e-12)
+    i2, _ = integrate.quad(lambda r: 2 * math.pi * r * orc.kernel_f(r), 0.0, 1.0, epsabs=1e-13)
+    assert i2 == pytest.approx((4 * math.pi ** 2 - 15) / (18 * math.pi), abs=1e-12)
+
+
+def test_paper_parameter_defaults(orc):
+    gold = json.load(open(os.path.join(GOLD, "paper_parameters.json")))
+    p = orc.params()
+    for k in ("length_scale", "sigma0", "alpha0", "res", "free_thresh", "occ_thresh"):
+        assert getattr(p, k) == pytest.approx(gold[k])
+
+
+# ---------------------------------------------------------------- a1: transform and validate
+
+def test_transform_exact_yaw90_and_drops(orc):
+    p = orc.params(min_range=0.5, max_range=10.0)
+    T = np.eye(4)
+    T[:3, :3] = [[0, -1, 0], [1, 0, 0], [0, 0, 1]]
+    T[:3, 3] = [1.0, 2.0, 3.0]
+    pts = np.array([[1, 0, 0], [0, 2, 0], [np.nan, 0, 1], [0.1, 0, 0], [20, 0, 0], [0, 0, np.inf], [0, 0, -4]],
+                   np.float32)
+    w, idx = orc.transform(p, pts, T)
+    assert idx.tolist() == [0, 1, 6]
+    np.testing.assert_array_equal(w, np.array([[1, 3, 3], [-1, 2, 3], [1, 2, -1]], np.float32))
+
+
+# ---------------------------------------------------------------- a2: free samples (Sec. III)
+
+def test_free_samples_exact_binary_step(orc):
+    p = orc.params(free_step=0.25, num_classes=3)
+    T = np.eye(4)
+    xyz, lab = orc.samples(p, np.array([[1.0, 0, 0], [0, 0, 0.5]], np.float32), np.array([2, 3]), T)
+    # hits first (input order), then samples of ray 0 (j = 1, 2, 3) and ray 1 (j = 1)
+    np.testing.assert_array_equal(lab, [2, 3, 0, 0, 0, 0])
+    np.testing.assert_array_equal(xyz, np.array([[1, 0, 0], [0, 0, 0.5], [0.75, 0, 0], [0.5, 0, 0], [0.25, 0, 0],
+                                                 [0, 0, 0.25]], np.float32))
+
+
+def test_free_samples_geometry(orc):
+    """Samples lie on the segment from the origin to the hit, spaced by s,
+    the last within (0, s] of the sensor; count = ceil(r/s) - 1 away from ties."""
+    rng = np.random.default_rng(1)
+    s = 0.3
+    p = orc.params(free_step=s, num_classes=2)
+    T = np.eye(4)
+    T[:3, 3] = [0.5, -0.25, 1.5]
+    d = rng.normal(size=(40, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    rr = rng.uniform(0.05, 12.0, size=40)
+    pts = (d * rr[:, None]).astype(np.float32)
+    xyz, lab = orc.samples(p, pts, np.ones(40, np.int32), T)
+    free = xyz[40:].astype(np.float64)
+    o = T[:3, 3]
+    pos = 0
+    for i in range(40):
+        n = int(math.ceil(rr[i] / s)) - 1
+        seg = free[pos:pos + n]
+        pos += n
+        t = np.linalg.norm(seg - o, axis=1)
+        np.testing.assert_allclose(t, rr[i] - s * np.arange(1, n + 1), atol=2e-5)
+        cr = np.cross(seg - o, np.tile(d[i], (n, 1)))
+        assert np.abs(cr).max(initial=0.0) < 2e-5
+        if n:
+            assert 0.0 < t[-1] <= s + 2e-5
+    assert pos == len(free)
+    assert np.all(lab[40:] == 0)
+
+
+# ---------------------------------------------------------------- a3: downsampling
+
+def test_downsample_centroids_by_cell_and_label(orc):
+    p = orc.params(res=1.0, free_step=100.0, num_classes=3)  # no free samples: every r < s
+    T = np.eye(4)
+    pts = np.array([[0.25, 0.25, 0.25], [0.75, 0.25, 0.25], [0.5, 0.75, 0.75],  # cell (0,0,0) label 1
+                    [0.5, 0.5, 0.5],                                         # cell (0,0,0) label 2
+                    [1.5, 0.5, 0.5], [-0.5, 0.5, 0.5]], np.float32)          # cells (1,0,0), (-1,0,0)
+    lab = np.array([1, 1, 1, 2, 1, 1], np.int32)
+    xyz, ol, st = orc.training_set(p, pts, lab, T)
+    got = {(tuple(np.floor(x).astype(int)), int(l)): tuple(x) for x, l in zip(xyz, ol)}
+    assert st == dict(hits=6, free=0, train=4)
+    assert got[((0, 0, 0), 1)] == (0.5, np.float32(1.25 / 3), np.float32(1.25 / 3))
+    assert got[((0, 0, 0), 2)] == (0.5, 0.5, 0.5)
+    assert got[((1, 0, 0), 1)] == (1.5, 0.5, 0.5)
+    assert got[((-1, 0, 0), 1)] == (-0.5, 0.5, 0.5)
+
+
+def test_voxel_index_floor_boundaries(orc):
+    # floorf(x * fp32(1/res)): negative side floors down; 0.1f * 10f rounds to 1
+    p = orc.params(res=0.1, length_scale=0.05, sigma0=1.0, num_classes=1)
+    m = orc.OracleMap(p)
+    m.insert_training(np.array([[-0.05, 0.05, 0.05], [0.1, 0.05, 0.05]], np.float32), np.array([1, 1]))
+    keys, alpha, pairs = m.export()
+    touched = keys[pairs > 0]
+    assert sorted(map(tuple, touched)) == [(-1, 0, 0), (1, 0, 0)]
+
+
+# ---------------------------------------------------------------- a5: accumulation (Eq. alpha_kernel)
+
+def _bruteforce(orc, p, xyz, lab):
+    """numpy all-pairs: every voxel centre in the padded bounding box x every point."""
+    res, l = p.res, p.length_scale
+    lo = np.floor(xyz.min(0) / res).astype(int) - int(math.ceil(l / res)) - 2
+    hi = np.floor(xyz.max(0) / res).astype(int) + int(math.ceil(l / res)) + 2
+    g = np.stack(np.meshgrid(*[np.arange(a, b + 1) for a, b in zip(lo, hi)], indexing="ij"), -1).reshape(-1, 3)
+    c = (g + 0.5) * res
+    K1 = p.num_classes + 1
+    acc = {}
+    x64 = xyz.astype(np.float64)
+    for i in range(len(x64)):
+        e = c - x64[i]
+        d2 = (e[:, 0] * e[:, 0] + e[:, 1] * e[:, 1]) + e[:, 2] * e[:, 2]
+        for j in np.nonzero(d2 < l * l)[0]:
+            key = tuple(g[j])
+            if key not in acc:
+                acc[key] = [np.zeros(K1), 0]
+            acc[key][0][lab[i]] += p.sigma0 * orc.kernel_f(math.sqrt(d2[j]) / l)
+            acc[key][1] += 1
+    return acc
+
+
+@pytest.mark.parametrize("seed,res,l", [(0, 0.1, 0.3), (1, 0.1, 0.25), (2, 0.05, 0.15), (3, 0.2, 0.3)])
+def test_stencil_equals_bruteforce(orc, seed, res, l):
+    rng = np.random.default_rng(seed)
+    xyz = rng.uniform(-0.6, 0.6, size=(150, 3)).astype(np.float32)
+    xyz[:5] = np.round(xyz[:5] / res) * res  # points on voxel faces
+    lab = rng.integers(0, 4, size=150).astype(np.int32)
+    p = orc.params(res=res, length_scale=l, sigma0=0.7, num_classes=3, block_edge=4)
+    m = orc.OracleMap(p)
+    m.insert_training(xyz, lab)
+    keys, alpha, pairs = m.export()
+    ref = _bruteforce(orc, p, xyz, lab)
+    touched = {tuple(k): i for i, k in enumerate(keys) if pairs[i] > 0}
+    assert set(touched) == set(ref)
+    for k, i in touched.items():
+        assert pairs[i] == ref[k][1]
+        np.testing.assert_allclose(alpha[i] - p.alpha0, ref[k][0], rtol=1e-12, atol=1e-15)
+    # voxels of allocated blocks that no point reached hold exactly the prior
+    assert np.all(alpha[pairs == 0] == p.alpha0)
+    # blocks: exactly those holding a touched voxel (block edge 4)
+    bk = {tuple(np.floor_divide(np.array(k), 4)) for k in ref}
+    assert set(map(tuple, m.block_keys())) == bk
+
+
+def test_alpha_bruteforce_entry_matches_numpy(orc):
+    rng = np.random.default_rng(5)
+    xyz = rng.uniform(-0.5, 0.5, size=(80, 3)).astype(np.float32)
+    lab = rng.integers(0, 3, size=80).astype(np.int32)
+    p = orc.params(res=0.1, length_scale=0.3, sigma0=0.5, num_classes=2)
+    ref = _bruteforce(orc, p, xyz, lab)
+    keys = np.array(list(ref.keys()))
+    a, pc = orc.alpha_bruteforce(p, xyz, lab, keys)
+    for i, k in enumerate(ref):
+        assert pc[i] == ref[k][1]
+        np.testing.assert_allclose(a[i] - p.alpha0, ref[k][0], rtol=1e-12, atol=1e-15)
+
+
+def test_lattice_mass_matches_ball_integral(orc):
+    """Sum over voxel centres of k(c_v, x), averaged over uniform offsets of x,
+    equals sigma0 (l/res)^3 * 2(pi^2-6)/(9 pi) (the lattice sum of a smooth
+    compactly supported function equals its integral up to a tiny aliasing term)."""
+    rng = np.random.default_rng(7)
+    res, l, s0 = 0.1, 0.3, 1.0
+    n = 3000
+    grid = np.stack(np.meshgrid(np.arange(15), np.arange(15), np.arange(14), indexing="ij"), -1).reshape(-1, 3)[:n]
+    xyz = (grid * 1.0 + rng.uniform(0.0, res, size=(n, 3))).astype(np.float32)  # 1 m apart: no overlap
+    p = orc.params(res=res, length_scale=l, sigma0=s0, num_classes=1)
+    m = orc.OracleMap(p)
+    m.insert_training(xyz, np.ones(n, np.int32))
+    keys, alpha, pairs = m.export()
+    per_point = (alpha[:, 1] - p.alpha0).sum() / n
+    expect = s0 * (l / res) ** 3 * 2 * (math.pi ** 2 - 6) / (9 * math.pi)
+    assert per_point == pytest.approx(expect, rel=2e-3)
+    # in-support pairs per point ~ ball volume in voxels = 4/3 pi 3^3
+    assert pairs.sum() / n == pytest.approx(4 / 3 * math.pi * 27, rel=2e-2)
+
+
+def test_binary_reversion_to_bki_occupancy(orc):
+    """With one occupied class (K = 1), alpha^0 and alpha^1 are the two counts of
+    binary BKI occupancy (Sec. III reverts to the counting sensor model); with
+    K > 1 and only class c observed, alpha^c equals the occupied count and every
+    other occupied class keeps the prior."""
+    rng = np.random.default_rng(11)
+    xyz = rng.uniform(-0.5, 0.5, size=(120, 3)).astype(np.float32)
+    occ = rng.random(120) < 0.4
+    p1 = orc.params(res=0.1, length_scale=0.3, sigma0=1.0, num_classes=1)
+    m1 = orc.OracleMap(p1)
+    m1.insert_training(xyz, occ.astype(np.int32))
+    keys, a1, pairs = m1.export()
+    # binary BKI: beta = sum_free k, alpha = sum_occ k  (numpy brute force)
+    c = (keys + 0.5) * 0.1
+    d = np.linalg.norm(c[:, None, :] - xyz[None].astype(np.float64), axis=2)
+    kf = np.vectorize(orc.kernel_f)(np.minimum(d / 0.3, 1.0))
+    np.testing.assert_allclose(a1[:, 1] - 0.001, kf[:, occ].sum(1), rtol=1e-10, atol=1e-13)
+    np.testing.assert_allclose(a1[:, 0] - 0.001, kf[:, ~occ].sum(1), rtol=1e-10, atol=1e-13)
+    p5 = orc.params(res=0.1, length_scale=0.3, sigma0=1.0, num_classes=5)
+    m5 = orc.OracleMap(p5)
+    m5.insert_training(xyz, np.where(occ, 4, 0).astype(np.int32))
+    k5, a5, _ = m5.export()
+    np.testing.assert_array_equal(k5, keys)
+    np.testing.assert_allclose(a5[:, [0, 4]], a1, rtol=1e-12)
+    assert np.all(a5[:, [1, 2, 3, 5]] == 0.001)
+
+
+def test_scan_additivity_and_sigma0_linearity(orc):
+    sc = scenes.small_region_scan(0, n_az=30, n_el=20)
+    pts, lab, T = sc["points"], sc["labels"], sc["pose"]
+    half = len(pts) // 2
+    p = orc.params(**{**scenes.SMALL_SCENE_PARAMS, "sigma0": 1.0})
+    both = orc.OracleMap(p)
+    both.insert_scan(pts[:half], lab[:half], T)
+    both.insert_scan(pts[half:], lab[half:], T)
+    kb, ab, pb = both.export()
+    A = orc.OracleMap(p)
+    A.insert_scan(pts[:half], lab[:half], T)
+    B = orc.OracleMap(p)
+    B.insert_scan(pts[half:], lab[half:], T)
+    aa, pa = A.alpha_at(kb)
+    bb, pbb = B.alpha_at(kb)
+    np.testing.assert_allclose(ab, aa + bb - p.alpha0, rtol=1e-12)
+    np.testing.assert_array_equal(pb, pa + pbb)
+    p2 = orc.params(**{**scenes.SMALL_SCENE_PARAMS, "sigma0": 0.25})
+    C = orc.OracleMap(p2)
+    C.insert_scan(pts[:half], lab[:half], T)
+    C.insert_scan(pts[half:], lab[half:], T)
+    kc, ac, _ = C.export()
+    np.testing.assert_array_equal(kc, kb)
+    np.testing.assert_allclose(ac - p.alpha0, 0.25 * (ab - p.alpha0), rtol=1e-12, atol=1e-16)
+
+
+def test_conservation_per_voxel(orc):
+    """sum_k (alpha_v^k - alpha0) = sum_i k(c_v, x_i) over all labels."""
+    rng = np.random.default_rng(13)
+    xyz = rng.uniform(-0.4, 0.4, size=(60, 3)).astype(np.float32)
+    lab = rng.integers(0, 6, size=60).astype(np.int32)
+    p = orc.params(res=0.1, length_scale=0.3, sigma0=0.3, num_classes=5)
+    m = orc.OracleMap(p)
+    m.insert_training(xyz, lab)
+    keys, alpha, _ = m.export()
+    a_one, _ = orc.alpha_bruteforce(orc.params(res=0.1, length_scale=0.3, sigma0=0.3, num_classes=1), xyz,
+                                    np.zeros(60, np.int32), keys)
+    np.testing.assert_allclose((alpha - p.alpha0).sum(1), a_one[:, 0] - p.alpha0, rtol=1e-12, atol=1e-15)
+
+
+# ---------------------------------------------------------------- read-off (Eq. mode, Eq. variance)
+
+def test_readoff_matches_dirichlet_moments(orc):
+    rng = np.random.default_rng(17)
+    xyz = rng.uniform(-0.3, 0.3, size=(400, 3)).astype(np.float32)
+    lab = rng.integers(0, 4, size=400).astype(np.int32)
+    p = orc.params(res=0.1, length_scale=0.3, sigma0=2.0, num_classes=3)
+    m = orc.OracleMap(p)
+    m.insert_training(xyz, lab)
+    keys, alpha, pairs = m.export()
+    sel = np.nonzero(pairs > 0)[0][:200]
+    q = ((keys[sel] + 0.5) * 0.1).astype(np.float32)
+    out = m.query(q)
+    for j, i in enumerate(sel):
+        a = alpha[i]
+        np.testing.assert_allclose(out["probs"][j], stats.dirichlet.mean(a), rtol=1e-12)
+        np.testing.assert_allclose(out["var"][j], stats.dirichlet.var(a), rtol=1e-10)
+        assert out["label"][j] == int(np.argmax(a))
+        assert out["p_occ"][j] == pytest.approx(1.0 - stats.dirichlet.mean(a)[0], abs=1e-12)
+        if np.all(a > 1):
+            # MAP of Dir(a): maximise the log density on the simplex
+            def neg(z):
+                t = np.exp(z - z.max())
+                t /= t.sum()
+                return -stats.dirichlet.logpdf(np.clip(t, 1e-300, 1), a)
+            z0 = np.log(a)
+            zz = optimize.minimize(neg, z0, method="Nelder-Mead", options=dict(xatol=1e-12, fatol=1e-14,
+                                                                               maxiter=20000)).x
+            t = np.exp(zz - zz.max())
+            t /= t.sum()
+            np.testing.assert_allclose(out["mode"][j], t, atol=2e-5)
+        else:
+            assert np.all(np.isnan(out["mode"][j]))
+
+
+def test_readoff_prior_ties_and_states(orc):
+    p = orc.params(res=0.1, length_scale=0.3, sigma0=1.0, num_classes=3)
+    m = orc.OracleMap(p)
+    out = m.query(np.array([[5.0, 5.0, 5.0]], np.float32))  # nothing mapped: prior
+    np.testing.assert_allclose(out["probs"][0], 0.25)
+    assert out["label"][0] == 0  # tie -> lowest index
+    assert out["state"][0] == 1  # unknown
+    # a voxel reached only by free points is free; only by class-2 points is occupied
+    m.insert_training(np.array([[0.05, 0.05, 0.05]], np.float32), np.array([0]))
+    m.insert_training(np.array([[2.05, 0.05, 0.05]], np.float32), np.array([2]))
+    out = m.query(np.array([[0.05, 0.05, 0.05], [2.05, 0.05, 0.05]], np.float32))
+    assert out["state"].tolist() == [0, 2]
+    assert out["label"].tolist() == [0, 2]
+
+
+# ---------------------------------------------------------------- differentiable form
+
+def _grad_case(orc, seed=19, n=40, nh=60):
+    rng = np.random.default_rng(seed)
+    xyz = rng.uniform(-0.35, 0.35, size=(n, 3))
+    lab = rng.integers(0, 4, size=n).astype(np.int32)
+    held = rng.uniform(-0.3, 0.3, size=(nh, 3)).astype(np.float32)
+    hl = rng.integers(0, 4, size=nh).astype(np.int32)
+    return xyz, lab, held, hl
+
+
+def test_gradient_matches_central_differences(orc):
+    xyz, lab, held, hl = _grad_case(orc)
+    base = dict(res=0.1, length_scale=0.3, sigma0=0.8, num_classes=3)
+    p = orc.params(**base)
+    ll, gl, gs, gx = orc.heldout_grad(p, xyz, lab, held, hl)
+    h = 1e-4
+    fd_l = (orc.heldout_ll(orc.params(**{**base, "length_scale": 0.3 + h}), xyz, lab, held, hl) -
+            orc.heldout_ll(orc.params(**{**base, "length_scale": 0.3 - h}), xyz, lab, held, hl)) / (2 * h)
+    fd_s = (orc.heldout_ll(orc.params(**{**base, "sigma0": 0.8 + h}), xyz, lab, held, hl) -
+            orc.heldout_ll(orc.params(**{**base, "sigma0": 0.8 - h}), xyz, lab, held, hl)) / (2 * h)
+    assert gl == pytest.approx(fd_l, rel=1e-3)
+    assert gs == pytest.approx(fd_s, rel=1e-3)
+    for i in range(0, len(xyz), 4):
+        for d in range(3):
+            xp, xm = xyz.copy(), xyz.copy()
+            xp[i, d] += h
+            xm[i, d] -= h
+            fd = (orc.heldout_ll(p, xp, lab, held, hl) - orc.heldout_ll(p, xm, lab, held, hl)) / (2 * h)
+            assert gx[i, d] == pytest.approx(fd, rel=1e-3, abs=1e-6)
+
+
+def test_gradient_sigma0_and_euler_identities(orc):
+    """alpha - alpha0 is linear in sigma0; alpha_v depends on (x_i - c_v)/l only,
+    so l dLL/dl + sum_i (x_i - c_v) . dLL/dx_i = 0 when every held-out point is
+    in one voxel v."""
+    xyz, lab, held, hl = _grad_case(orc, seed=23)
+    held = np.tile(np.array([[0.05, 0.05, 0.05]], np.float32), (20, 1))
+    hl = np.arange(20, dtype=np.int32) % 4
+    p = orc.params(res=0.1, length_scale=0.3, sigma0=0.8, num_classes=3)
+    ll, gl, gs, gx = orc.heldout_grad(p, xyz, lab, held, hl)
+    c = np.array([0.05, 0.05, 0.05])
+    euler = 0.3 * gl + np.sum((xyz - c) * gx)
+    assert abs(euler) < 1e-9 * max(1.0, abs(0.3 * gl))
+    # d alpha / d sigma0 = (alpha - alpha0) / sigma0  =>  dLL/dsigma0 = sum_v g_v . (alpha_v - alpha0) / sigma0
+    m = orc.OracleMap(p)
+    m.insert_training(xyz.astype(np.float32), lab)
+    a, _ = m.alpha_at(np.array([[0, 0, 0]]))
+    S = a[0].sum()
+    g = np.array([np.sum(hl == k) / a[0][k] for k in range(4)]) - len(hl) / S
+    assert gs == pytest.approx(float(g @ (a[0] - 0.001) / 0.8), rel=1e-5)
+
+
+# ---------------------------------------------------------------- a whole scan
+
+def test_small_scan_training_set_invariants(orc):
+    sc = scenes.small_region_scan(0, n_az=40, n_el=30)
+    p = orc.params(**scenes.SMALL_SCENE_PARAMS)
+    xyz, lab, st = orc.training_set(p, sc["points"], sc["labels"], sc["pose"])
+    samp, slab = orc.samples(p, sc["points"], sc["labels"], sc["pose"])
+    assert st["hits"] + st["free"] == len(samp)
+    assert st["train"] == len(xyz)
+    # one training point per distinct (cell, label) of the samples
+    cells = np.floor(samp * np.float32(1 / 0.1)).astype(np.int64)
+    distinct = {(tuple(c), int(l)) for c, l in zip(cells, slab)}
+    assert len(distinct) == len(xyz)
+    # every centroid lies in (or on the FP32 edge of) its cell's box
+    tc = np.floor(xyz * np.float32(10.0)).astype(np.int64)
+    inside = {(tuple(c), int(l)) for c, l in zip(tc, lab)}
+    assert len(inside & distinct) >= len(xyz) - 2
+    with pytest.raises(ValueError):
+        orc.training_set(p, sc["points"][:3], np.array([1, 11, 2]), sc["pose"])
