@@ -1,0 +1,337 @@
+#!/usr/bin/env python3
+"""Benchmark of the S-BKI per-scan map update on one GB300 (or N replicas).
+
+Workload: the LiDAR street sequence (64 x 2048 beams over +2 to -24.8 deg,
+max range 50 m, 19 occupied classes + free, 0.1 m voxels, l = 0.3 m, free
+samples every 0.3 m, sigma0 = 0.1, alpha0 = 0.001), synthetic and seeded.
+A step is one whole scan update through the C ABI (transform, free-space
+sampling, downsampling, block hash, kernel accumulation) into a map that
+persists over the sequence; scans are resident in HBM before timing.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+on bounded samples of the same scans (azimuth sectors) instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from synth import scenes  # noqa: E402
+
+METRIC = "LiDAR scans/sec (64x2048 street sequence, S-BKI per-scan update)"
+# roofline model of one in-support pair of Eq. (kernel) as the paper writes it:
+# ~14 FP32 operations and 3 MUFU operations (sqrt, sin, cos); per SM and clock
+# 128 FP32 lanes and 16 MUFU lanes
+PAIR_CLK_PER_SM = max(14.0 / 128.0, 3.0 / 16.0)
+
+
+def _gen(args):
+    first, count = args
+    return [dict(points=s["points"], labels=s["labels"], pose=s["pose"])
+            for s in scenes.street_sequence(count, first=first)]
+
+
+def generate_scans(first, count, workers):
+    """Scans first..first+count-1, generated on the host with a spawn pool."""
+    if count <= 0:
+        return []
+    chunks = []
+    per = max(1, math.ceil(count / max(1, workers)))
+    for a in range(first, first + count, per):
+        chunks.append((a, min(per, first + count - a)))
+    if workers <= 1 or len(chunks) == 1:
+        out = []
+        for c in chunks:
+            out += _gen(c)
+        return out
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(workers, len(chunks))) as pool:
+        parts = pool.map(_gen, chunks)
+    return [s for p in parts for s in p]
+
+
+def sector(scan, k, nsec):
+    """Points of scan in azimuth sector k of nsec (sensor frame)."""
+    p = scan["points"]
+    az = np.arctan2(p[:, 1], p[:, 0])
+    s = np.floor((az + np.pi) / (2 * np.pi) * nsec).astype(int) % nsec
+    sel = s == k
+    return p[sel], scan["labels"][sel]
+
+
+def oracle_rate(scans, n_steps, nsec=8, progress=None):
+    """FP64 oracle on azimuth sectors: step i processes sector i % nsec of
+    scan i // nsec into one persistent map.  Returns (scans/s, pairs/s,
+    seconds, steps)."""
+    from oracle import oracle as O
+    p = O.params(**scenes.STREET_PARAMS)
+    m = O.OracleMap(p)
+    t_total = 0.0
+    for i in range(n_steps):
+        sc = scans[(i // nsec) % len(scans)]
+        pts, lab = sector(sc, i % nsec, nsec)
+        t0 = time.perf_counter()
+        m.insert_scan(pts, lab, sc["pose"])
+        t_total += time.perf_counter() - t0
+    _, _, pc = m.export()
+    return (n_steps / nsec) / t_total, float(pc.sum()) / t_total, t_total
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((float(f[1]), float(f[2]), f[5], f[6], f[7], f[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        reasons = set()
+        for r in rows:
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"), r[2:]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median([r[0] for r in rows])), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), float(d.get("sm_max_mhz", 2070.0)), "measured"
+    return 6800.0, 2070.0, "fallback"
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    scans = generate_scans(0, max(1, math.ceil((args.warmup + args.steps) / 8)), args.workers)
+    nsec = 8
+    # warm-up steps (untimed) then timed steps, each one azimuth sector (1/8 scan)
+    oracle_rate(scans, args.warmup, nsec)
+    rate, prate, secs = oracle_rate(scans, args.steps, nsec)
+    cores = 1
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "scans/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded street scene, ray-cast)",
+            "config": {"workload": "lidar-street-64x2048", "beams": 64, "azimuths": 2048, "classes": 19,
+                       "res_m": 0.1, "length_scale_m": 0.3, "free_step_m": 0.3},
+            "pairs_per_s": prate,
+            "cpu_baseline": {"value": rate, "unit": "scans/s", "cores": cores, "kind": "oracle",
+                             "sample": "each step = one 45-degree azimuth sector (1/8) of a scan; "
+                                       "scans/s = sectors processed / 8 / seconds"},
+            "e2e": {"value": rate, "unit": "scans/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_1909_04631_gb300 as sb
+
+    # host-side generation before any GPU call (spawn pool)
+    nscan = min(args.scans, args.warmup + args.steps)
+    per_rank_first = rank * 1000  # replicas: every rank maps its own stretch of street
+    scans = generate_scans(per_rank_first, nscan, args.workers)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the oracle on a bounded sample: 2 of 8 azimuth sectors of scan 0 (about 10 s)
+        rate, prate, secs = oracle_rate(scans[:1], 2, 8)
+        cpu = {"value": rate, "unit": "scans/s", "cores": 1, "kind": "oracle",
+               "sample": "2 azimuth sectors (1/4) of one 64x2048 scan, FP64, one host core; "
+                         "scans/s = 0.25 / %.2f s" % secs, "pairs_per_s": prate}
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    stream = torch.cuda.current_stream(dev)
+    p = sb.default_params(**{k: v for k, v in scenes.STREET_PARAMS.items()}, pool_blocks=args.pool_blocks,
+                          sample_capacity=args.sample_capacity, device=local_rank)
+    m = sb.Map(p, stream=stream)
+    dpts = [torch.from_numpy(s["points"]).to(dev) for s in scans]
+    dlab = [torch.from_numpy(s["labels"]).to(dev) for s in scans]
+    poses = [s["pose"] for s in scans]
+    torch.cuda.synchronize()
+
+    for i in range(args.warmup):
+        j = i % nscan
+        m.insert_scan(dpts[j], dlab[j], poses[j])
+    m.profile(True, reset=True)
+    launches0 = m.profile_read()["launches"]
+    stats = []
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        ev0.record(stream)
+        for i in range(args.steps):
+            j = (args.warmup + i) % nscan
+            stats.append(m.insert_scan(dpts[j], dlab[j], poses[j]))
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    prof = m.profile_read()
+    launches = prof["launches"] - launches0
+    m.profile(False, reset=True)
+
+    # end to end through the C ABI from pinned host buffers (H2D inside the call, stats D2H)
+    hp = [torch.from_numpy(s["points"]).pin_memory() for s in scans]
+    hl = [torch.from_numpy(s["labels"]).pin_memory() for s in scans]
+    e2e_steps = min(args.steps, nscan)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h2d = 0
+    for i in range(e2e_steps):
+        j = (args.warmup + i) % nscan
+        m.insert_scan(hp[j].numpy(), hl[j].numpy(), poses[j])
+        h2d += hp[j].numel() * 4 + hl[j].numel() * 4
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    if rank != 0:
+        m.close()
+        return 0
+    K1 = scenes.STREET_PARAMS["num_classes"] + 1
+    B3 = 512
+    pairs = sum(s["pairs"] for s in stats)
+    vt = sum(s["touched_voxels"] for s in stats)
+    newb = sum(s["new_blocks"] for s in stats)
+    # algorithmic work of the accumulation step per launch (one launch per scan):
+    # read+write alpha[K+1] of each touched voxel, zero-fill of new blocks
+    bytes_alg = (8.0 * K1 * vt + 4.0 * K1 * B3 * newb) / args.steps
+    pairs_per = pairs / args.steps
+    acc_s = prof["accumulate_ms"] / 1e3 / max(1, prof["inserts"])
+    bw, sm_mhz_max, src = peaks()
+    props = torch.cuda.get_device_properties(dev)
+    n_sm = props.multi_processor_count
+    t_hbm = bytes_alg / (bw * 1e9)
+    t_alu = pairs_per * PAIR_CLK_PER_SM / (n_sm * sm_mhz_max * 1e6)
+    if t_alu >= t_hbm:
+        peak = n_sm * sm_mhz_max * 1e6 / PAIR_CLK_PER_SM / 1e9
+        roof = {"bound": "alu", "achieved": pairs_per / acc_s / 1e9, "peak": peak, "unit": "Gpair/s",
+                "frac": (pairs_per / acc_s / 1e9) / peak, "traffic": None,
+                "kernel": "accumulate_kernel", "peak_source": "%d SMs x %.0f MHz / %.4f clk per pair (3 MUFU)"
+                                                             % (n_sm, sm_mhz_max, PAIR_CLK_PER_SM),
+                "hbm_frac": (bytes_alg / acc_s / 1e9) / bw}
+    else:
+        roof = {"bound": "hbm", "achieved": bytes_alg / acc_s / 1e9, "peak": bw, "unit": "GB/s",
+                "frac": (bytes_alg / acc_s / 1e9) / bw, "traffic": None, "kernel": "accumulate_kernel",
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (%s)" % src}
+    value = args.steps * world / (ms / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "scans/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded street scene, ray-cast)",
+        "config": {"workload": "lidar-street-64x2048", "beams": 64, "azimuths": 2048, "classes": 19,
+                   "res_m": 0.1, "length_scale_m": 0.3, "free_step_m": 0.3, "distinct_scans": nscan,
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "not flushed: each step touches %.0f MB of alpha blocks (> 129 MB L2)"
+                         % (sum(s["touched_blocks"] for s in stats) / args.steps * K1 * B3 * 4 / 1e6)},
+        "pairs_per_s": pairs * world / (ms / 1e3),
+        "per_scan": {"hits": stats[-1]["hits"], "free_samples": stats[-1]["free_samples"],
+                     "train_points": stats[-1]["train_points"], "pairs": int(pairs_per),
+                     "touched_blocks": stats[-1]["touched_blocks"], "touched_voxels": int(vt / args.steps)},
+        "stage_ms": {"ingest": prof["ingest_ms"] / max(1, prof["inserts"]),
+                     "blocks": prof["blocks_ms"] / max(1, prof["inserts"]),
+                     "accumulate": prof["accumulate_ms"] / max(1, prof["inserts"])},
+        "roofline": roof,
+        "clocks": clk.summary(),
+        "gpu_launches": launches,
+        "e2e": {"value": e2e_steps * world / e2e_s, "unit": "scans/s",
+                "h2d_bytes_per_step": h2d // max(1, e2e_steps), "d2h_bytes_per_step": 80},
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    m.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--scans", type=int, default=100, help="distinct scans of the sequence to cycle over")
+    ap.add_argument("--workers", type=int, default=min(16, os.cpu_count() or 1))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--pool-blocks", type=int, default=1 << 18, help="map block pool capacity")
+    ap.add_argument("--sample-capacity", type=int, default=1 << 23, help="hits + free samples per scan")
+    args = ap.parse_args()
+    if args.warmup < 0 or args.steps < 1:
+        raise SystemExit("need --steps >= 1 and --warmup >= 0")
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,174 @@
+/* sbki.h - C ABI of libsbki, a GB300 (sm_103a) implementation of the
+ * semantic Bayesian kernel inference (S-BKI) map update of Gan et al.,
+ * "Bayesian Spatial Kernel Smoothing for Scalable Dense Semantic Mapping".
+ *
+ * The map holds, for every voxel of every allocated block, the Dirichlet
+ * concentrations alpha[K+1] of Eq. (alpha_kernel): class 0 is the free class,
+ * classes 1..K are the occupied semantic classes.  A scan update turns a
+ * labelled point cloud into training points (Sec. III: hits plus free-space
+ * samples interpolated along each beam, then voxel downsampling) and adds
+ * k(x_*, x_i) y_i into every voxel centre x_* within the support l of a
+ * training point x_i, with the sparse kernel of Eq. (kernel); the update is
+ * recursive over scans (Sec. IV).  Read-off follows Eq. (mode), Eq. (variance)
+ * and the occupancy rule of Sec. V-C.
+ *
+ * Conventions shared by every entry point
+ *  - Buffers are owned by the caller.  Pointer arguments may be host or device
+ *    memory of the map's device (detected with cudaPointerGetAttributes);
+ *    device buffers are read/written in stream order on params.cuda_stream.
+ *  - Coordinates are float32, row-major [n,3] (x, y, z).  Poses are float64
+ *    4x4 row-major world_from_sensor matrices.
+ *  - No function aborts or traps.  Every failure is a returned sbki_status;
+ *    sbki_last_error() gives a message.  On SBKI_ERR_CAPACITY and
+ *    SBKI_ERR_LABEL_RANGE an insert leaves the map unchanged.
+ *  - Device-side waits are bounded; nothing spins without a limit.
+ */
+#ifndef SBKI_H
+#define SBKI_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SBKI_OK = 0,
+  SBKI_ERR_INVALID_ARG = 1, /* null/negative/unsupported argument or parameter */
+  SBKI_ERR_LABEL_RANGE = 2, /* a label outside 1..K (scans) or 0..K (training sets) */
+  SBKI_ERR_CAPACITY = 3,    /* a fixed-size pool, hash or scratch buffer would overflow */
+  SBKI_ERR_CUDA = 4,        /* a CUDA runtime call failed (message has the CUDA error) */
+  SBKI_ERR_TIMEOUT = 5,     /* a bounded device-side wait ran out */
+  SBKI_ERR_NOT_FOUND = 6    /* lookup of something that does not exist */
+} sbki_status;
+
+/* Parameters.  Defaults (sbki_default_params) follow Table (parameters):
+ * l = 0.3 m, sigma0 = 0.1, alpha0 = 0.001; Sec. V-A: res = 0.1 m, free and
+ * occupied thresholds 0.47 and 0.6. */
+typedef struct sbki_params {
+  double res;          /* voxel edge [m] */
+  double length_scale; /* kernel support l [m], Eq. (kernel); 0 < l <= 0.75 * block edge * res */
+  double sigma0;       /* kernel scale sigma0, Eq. (kernel) */
+  double alpha0;       /* Dirichlet prior alpha_0^k, equal for all K+1 classes */
+  double free_step;    /* spacing of free-space samples along a beam [m], Sec. III */
+  double ds_res;       /* downsampling cell edge [m]; <= 0 means res */
+  double min_range;    /* hits closer than this to the sensor are dropped [m] */
+  double max_range;    /* hits farther than this are dropped [m]; must be finite */
+  double free_thresh;  /* p_occ below this reads as free (Sec. V-A) */
+  double occ_thresh;   /* p_occ above this reads as occupied (Sec. V-A) */
+  int32_t num_classes; /* K occupied classes; alpha has K+1 entries; K+1 <= 32 */
+  int32_t block_edge;  /* voxels per block edge: 4 or 8 */
+  int64_t pool_blocks; /* capacity of the block pool (alpha storage) */
+  int64_t sample_capacity; /* max hits + free samples of one scan */
+  int32_t track_pairs; /* nonzero: keep per-voxel in-support pair counts (parity aid) */
+  int32_t device;      /* CUDA device ordinal */
+  void* cuda_stream;   /* cudaStream_t for every launch and copy; NULL = legacy default stream */
+} sbki_params;
+
+/* Per-insert counters (all for the last insert). */
+typedef struct sbki_stats {
+  int64_t hits;           /* input points kept (finite, within range) */
+  int64_t dropped;        /* input points dropped */
+  int64_t free_samples;   /* free-space samples generated (Sec. III) */
+  int64_t train_points;   /* training points after downsampling */
+  int64_t touched_blocks; /* blocks with at least one in-support pair */
+  int64_t new_blocks;     /* blocks allocated by this insert */
+  int64_t pairs;          /* in-support (voxel, training point) pairs, Eq. (alpha_kernel) */
+  int64_t touched_voxels; /* voxels whose alpha changed */
+  int64_t total_blocks;   /* blocks allocated in the map after the insert */
+} sbki_stats;
+
+typedef struct sbki_map sbki_map;
+
+/* Fills *p with the defaults above (K = 10, block edge 8, pool 2^16 blocks,
+ * 2^24 samples per scan, device 0, default stream). */
+sbki_status sbki_default_params(sbki_params* p);
+
+/* Allocates the map (block hash, alpha pool and per-scan scratch) on
+ * params->device.  *out receives the handle; release with sbki_destroy_map. */
+sbki_status sbki_create_map(const sbki_params* params, sbki_map** out);
+void sbki_destroy_map(sbki_map* map);
+
+/* One scan update, Sec. III + Eq. (alpha_kernel) + Sec. IV:
+ *   points [n,3] sensor frame, labels [n] in 1..K, sensor_pose = world_from_sensor.
+ * Hits that are non-finite or outside [min_range, max_range] are dropped and
+ * counted, not an error.  Free samples lie at distance r - j*free_step from
+ * the sensor origin for j >= 1 while positive.  Hits and free samples are
+ * grouped per (downsampling cell, label) into centroids, and every centroid
+ * adds sigma0 * f(d/l) into class y of every voxel centre with d < l.
+ * Synchronises the stream before returning (stats may be NULL). */
+sbki_status sbki_insert_scan(sbki_map* map, const float* points, const int32_t* labels, int64_t n,
+                             const double sensor_pose[16], sbki_stats* stats);
+
+/* Same update, without the final synchronisation: errors raised on the device
+ * surface at the next sbki_sync or synchronising call.  Buffers must stay
+ * valid until then. */
+sbki_status sbki_insert_scan_async(sbki_map* map, const float* points, const int32_t* labels, int64_t n,
+                                   const double sensor_pose[16]);
+/* Waits for the map's stream and returns the first pending error (and the
+ * stats of the last insert, if stats is not NULL). */
+sbki_status sbki_sync(sbki_map* map, sbki_stats* stats);
+
+/* Steps a1-a3 only (Sec. III): the training set of a scan, without touching
+ * the map.  xyzl_out [cap,4] float32 = (x, y, z, label as float), ordered by
+ * (downsampling tile, cell, label); *count receives the number of points (if
+ * count > cap only cap are written and SBKI_ERR_CAPACITY is returned). */
+sbki_status sbki_training_set(sbki_map* map, const float* points, const int32_t* labels, int64_t n,
+                              const double sensor_pose[16], float* xyzl_out, int64_t cap, int64_t* count);
+
+/* Eq. (alpha_kernel) for a given training set (no sampling or downsampling):
+ * xyzl [p,4] float32 world (x, y, z, label as float) with labels 0..K. */
+sbki_status sbki_insert_training(sbki_map* map, const float* xyzl, int64_t p, sbki_stats* stats);
+
+/* Read-off at world points xyz [q,3] (Eq. mode, Eq. variance, Sec. V-C): the
+ * voxel containing each point is looked up; a voxel never reached reads as
+ * the prior.  probs [q,K+1] = E[theta] (required); var [q,K+1] = V[theta];
+ * mode [q,K+1] = (alpha^k - 1)/(sum alpha - (K+1)) where every alpha^k > 1,
+ * else NaN; label [q] = argmax alpha (ties to the lowest class); p_occ [q] =
+ * sum of the occupied-class probabilities; state [q] = 0 free / 1 unknown /
+ * 2 occupied (a voxel with no kernel mass is unknown).  All but probs may be
+ * NULL. */
+sbki_status sbki_query_probs(const sbki_map* map, const float* xyz, int64_t q, float* probs, float* var,
+                             float* mode, int32_t* label, float* p_occ, int32_t* state);
+
+/* Number of allocated voxels (blocks * block_edge^3). */
+sbki_status sbki_voxel_count(const sbki_map* map, int64_t* count);
+
+/* Every voxel of every allocated block, sorted by voxel index (x, y, z)
+ * lexicographically: keys [cap,3] int64 voxel indices (centre = (key+0.5)*res),
+ * alpha [cap,K+1] float32 including alpha0, pairs [cap] in-support pair counts
+ * (NULL, or requires track_pairs).  Host buffers only. */
+sbki_status sbki_export(const sbki_map* map, int64_t* keys, float* alpha, int32_t* pairs, int64_t cap,
+                        int64_t* count);
+
+/* Per-stage device timing and launch counting (tracing aid).  With profiling
+ * on, each synchronous insert records CUDA events on the map's stream around
+ * step a1-a3 (sampling + downsampling), a4 (block hash) and a5 (accumulation)
+ * and adds the elapsed times; launches counts every kernel the library
+ * launched on the map since creation (profiling on or off). */
+typedef struct sbki_profile_data {
+  int64_t inserts;     /* synchronous inserts timed since the last reset */
+  int64_t launches;    /* kernels launched by this map since creation */
+  double ingest_ms;    /* a1-a3 */
+  double blocks_ms;    /* a4 */
+  double accumulate_ms;/* a5 */
+} sbki_profile_data;
+sbki_status sbki_profile(sbki_map* map, int32_t enable, int32_t reset);
+sbki_status sbki_profile_read(const sbki_map* map, sbki_profile_data* out);
+
+/* The sparse kernel of Eq. (kernel): f[i] = f(r[i]) for r = d/l (f = 0 for
+ * r >= 1), so k(d) = sigma0 * f(d/l).  method 0 is the form the update uses
+ * (u^5 Q(u^2), u = 1 - r, Q a Chebyshev interpolant), method 1 the textbook
+ * trigonometric form.  r and f are device buffers of n floats; synchronises
+ * `stream` (a cudaStream_t, NULL = legacy default stream).  Diagnostic aid. */
+sbki_status sbki_kernel_values(const float* r, int64_t n, float* f, int32_t method, void* stream);
+
+/* Message of the last failure on this map (or of the last sbki_create_map
+ * failure when map is NULL). */
+const char* sbki_last_error(const sbki_map* map);
+const char* sbki_status_string(sbki_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SBKI_H */

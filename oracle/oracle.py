@@ -60,6 +60,8 @@ def lib():
             L.orc_kernel_f.argtypes = [f64]
             L.orc_kernel_df.restype = f64
             L.orc_kernel_df.argtypes = [f64]
+            L.orc_exact_mean_f32.restype = C.c_float
+            L.orc_exact_mean_f32.argtypes = [vp, i64]
             L.orc_transform.restype = i64
             L.orc_transform.argtypes = [_P(OrcParams), vp, i64, vp, vp, vp]
             L.orc_samples.restype = i64
@@ -108,6 +110,12 @@ def kernel_f(r: float) -> float:
 
 def kernel_df(r: float) -> float:
     return lib().orc_kernel_df(float(r))
+
+
+def exact_mean_f32(values):
+    """Reading K4: exact mean of FP32 values rounded once to FP32."""
+    v = _f32(values).reshape(-1)
+    return float(lib().orc_exact_mean_f32(_ptr(v), len(v)))
 
 
 def transform(p, points, pose):

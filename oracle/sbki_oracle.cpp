@@ -26,8 +26,9 @@
 //   K3  Free samples: for a hit at range r from the sensor origin o, samples at
 //       t_j = r - j*s for j = 1, 2, ... while t_j > 0 (never at the hit itself).
 //   K4  Downsampling groups hits and free samples by (ds cell, label); the
-//       representative is the centroid (FP64 sum in ascending source order:
-//       hits in input order, then free samples in (ray, j) order), rounded to FP32.
+//       representative is the centroid: per axis the exact mean of the
+//       members' FP32 coordinates, rounded once to FP32 (nearest, ties to
+//       even).  Being exact, it does not depend on the order of the members.
 //   K5  Every voxel centre with ||c_v - x_i||^2 < l^2 (FP64) receives the pair.
 //   K6  Geometry that decides integer keys is a fixed FP32 operation sequence
 //       (this file is compiled with -ffp-contract=off): world = fp32(FP64 R p + t)
@@ -161,31 +162,126 @@ void build_samples(const Params& p, const std::vector<std::array<float, 3>>& wor
   *n_free = nf;
 }
 
+// Exact mean of FP32 values, rounded once to FP32 (nearest, ties to even),
+// with plain big-integer fixed point: every FP32 value is an integer multiple
+// of 2^-149, so the sum is an integer number of 2^-149 units (below 2^(128+149+32)
+// for up to 2^32 values) held in 32-bit limbs.
+struct BigFix {
+  static const int kLimbs = 14;  // 448 bits
+  uint32_t w[kLimbs];
+  BigFix() { std::memset(w, 0, sizeof(w)); }
+  void add_shifted(uint64_t m, int shift) {  // += m * 2^shift
+    int limb = shift / 32, bit = shift % 32;
+    unsigned __int128 v = (unsigned __int128)m << bit;
+    uint64_t carry = 0;
+    for (int i = limb; i < kLimbs; ++i) {
+      uint64_t part = (uint64_t)(v & 0xffffffffu);
+      v >>= 32;
+      uint64_t t = (uint64_t)w[i] + part + carry;
+      w[i] = (uint32_t)t;
+      carry = t >> 32;
+      if (v == 0 && carry == 0) break;
+    }
+  }
+  void sub(const BigFix& o) {  // *this -= o, requires *this >= o
+    int64_t borrow = 0;
+    for (int i = 0; i < kLimbs; ++i) {
+      int64_t t = (int64_t)w[i] - (int64_t)o.w[i] - borrow;
+      borrow = t < 0 ? 1 : 0;
+      w[i] = (uint32_t)(t + (borrow << 32));
+    }
+  }
+  bool less(const BigFix& o) const {
+    for (int i = kLimbs - 1; i >= 0; --i)
+      if (w[i] != o.w[i]) return w[i] < o.w[i];
+    return false;
+  }
+  bool zero() const {
+    for (int i = 0; i < kLimbs; ++i)
+      if (w[i]) return false;
+    return true;
+  }
+  int bitlen() const {
+    for (int i = kLimbs - 1; i >= 0; --i)
+      if (w[i]) return 32 * i + 32 - __builtin_clz(w[i]);
+    return 0;
+  }
+  bool bit(int i) const { return i >= 0 && ((w[i / 32] >> (i % 32)) & 1u); }
+  // divide by n in place, return the remainder
+  uint64_t divmod(uint64_t n) {
+    unsigned __int128 r = 0;
+    for (int i = kLimbs - 1; i >= 0; --i) {
+      unsigned __int128 cur = (r << 32) | w[i];
+      w[i] = (uint32_t)(cur / n);
+      r = cur % n;
+    }
+    return (uint64_t)r;
+  }
+};
+
+float exact_mean_f32(const std::vector<float>& v) {
+  BigFix pos, neg;
+  for (float x : v) {
+    if (x == 0.0f) continue;
+    int e;
+    float m = std::frexp(std::fabs(x), &e);        // |x| = m 2^e, m in [0.5, 1)
+    uint64_t mi = (uint64_t)std::ldexp(m, 24);      // exact: 24-bit integer
+    int shift = e - 24 + 149;                       // units of 2^-149
+    if (shift < 0) {                                // subnormal: mi has trailing zeros
+      mi >>= -shift;
+      shift = 0;
+    }
+    (x < 0.0f ? neg : pos).add_shifted(mi, shift);
+  }
+  bool negative = pos.less(neg);
+  BigFix mag = negative ? neg : pos;
+  mag.sub(negative ? pos : neg);
+  if (mag.zero()) return 0.0f;
+  // quotient Q = mag / n in units of 2^-149, scaled up so that it has >= 26 bits
+  const uint64_t n = (uint64_t)v.size();
+  BigFix q = mag;
+  int up = 0;
+  while (q.bitlen() < 64 + 27) {  // shift left by limbs until the quotient is long
+    for (int i = BigFix::kLimbs - 1; i > 0; --i) q.w[i] = q.w[i - 1];
+    q.w[0] = 0;
+    up += 32;
+  }
+  const bool sticky_div = q.divmod(n) != 0;  // q = floor(mag 2^up / n)
+  // value = (q + frac) * 2^(-149 - up)
+  const int qb = q.bitlen();
+  int exp2 = qb - 1 - 149 - up;  // binary exponent of the leading bit
+  int keep = 24;                 // significant bits kept (fewer for subnormal results)
+  if (exp2 < -126) keep = 24 - (-126 - exp2);
+  if (keep <= 0) keep = 0;
+  const int drop = qb - keep;    // >= 2 by construction
+  uint64_t mant = 0;
+  for (int i = qb - 1; i >= drop; --i) mant = (mant << 1) | (q.bit(i) ? 1u : 0u);
+  const bool half = q.bit(drop - 1);
+  bool sticky = sticky_div;
+  for (int i = 0; i < drop - 1 && !sticky; ++i) sticky = q.bit(i);
+  if (half && (sticky || (mant & 1u))) mant += 1;  // round to nearest, ties to even
+  const float r = std::ldexp((float)mant, drop - 149 - up);
+  return negative ? -r : r;
+}
+
 // Step a3 (reading K4): centroid per (ds cell, label).
 void downsample(const Params& p, const std::vector<Sample>& in, std::vector<Sample>& out) {
   float inv_ds = (float)(1.0 / p.ds_res);
-  struct Acc {
-    double sx, sy, sz;
-    int64_t n;
+  struct Members {
+    std::vector<float> x, y, z;
   };
-  std::map<std::array<int64_t, 4>, Acc> cells;
-  for (const Sample& s : in) {  // ascending source order
+  std::map<std::array<int64_t, 4>, Members> cells;
+  for (const Sample& s : in) {
     std::array<int64_t, 4> k = {voxel_index(s.x, inv_ds), voxel_index(s.y, inv_ds), voxel_index(s.z, inv_ds),
                                 (int64_t)s.label};
-    auto it = cells.find(k);
-    if (it == cells.end()) {
-      cells[k] = {(double)s.x, (double)s.y, (double)s.z, 1};
-    } else {
-      it->second.sx = it->second.sx + (double)s.x;
-      it->second.sy = it->second.sy + (double)s.y;
-      it->second.sz = it->second.sz + (double)s.z;
-      it->second.n += 1;
-    }
+    Members& m = cells[k];
+    m.x.push_back(s.x);
+    m.y.push_back(s.y);
+    m.z.push_back(s.z);
   }
   for (auto& kv : cells) {
-    const Acc& a = kv.second;
-    out.push_back({(float)(a.sx / (double)a.n), (float)(a.sy / (double)a.n), (float)(a.sz / (double)a.n),
-                   (int32_t)kv.first[3]});
+    const Members& m = kv.second;
+    out.push_back({exact_mean_f32(m.x), exact_mean_f32(m.y), exact_mean_f32(m.z), (int32_t)kv.first[3]});
   }
 }
 
@@ -287,6 +383,9 @@ void orc_map_destroy(void* h) { delete (Map*)h; }
 // Kernel value f(r) (Eq. kernel) and its derivative, for tests.
 double orc_kernel_f(double r) { return kernel_f(r); }
 double orc_kernel_df(double r) { return kernel_df(r); }
+
+// Exact mean of n FP32 values rounded once to FP32 (reading K4), for tests.
+float orc_exact_mean_f32(const float* v, int64_t n) { return exact_mean_f32(std::vector<float>(v, v + n)); }
 
 // a1 only: world coordinates of the kept points; returns the kept count.
 int64_t orc_transform(const orc_params* q, const float* pts, int64_t n, const double* T, float* world_out,

@@ -1,0 +1,339 @@
+// Step a4: the set of blocks touched by this scan's training points, and
+// their allocation in the device block hash (Sec. IV: voxels grouped into
+// blocks; every voxel of a block is a query point of Eq. alpha_kernel).
+//
+// A block is touched iff one of its voxel centres lies strictly within l of a
+// training point under the same membership rule as the accumulation (the
+// FP32 block-local test, re-decided in FP64 inside the band).  Because d^2 is
+// a sum of per-axis terms, the nearest voxel centre of a block is found per
+// axis; the FP32 nearest index is checked with its two neighbours.
+//
+// The hash is open addressing with linear probing on 64-bit block keys;
+// insertion is one atomicCAS per probe, bounded by kMaxProbes (then
+// SBKI_ERR_CAPACITY).  New slots go to a list; commit assigns pool indices
+// in one pass, or - if the pool would overflow or an error is pending -
+// clears exactly the slots this scan created, which restores the table
+// (slots created by this scan lie on no older key's probe chain).
+#include <algorithm>
+
+#include "sbki_internal.cuh"
+
+namespace sbki {
+namespace {
+
+struct TouchArgs {
+  Geom g;
+  const float4* train;
+  unsigned long long* hkeys;
+  int32_t* hvals;
+  uint32_t* hmark;
+  uint32_t* hcnt;
+  uint32_t* hcur;
+  int64_t hash_cap;
+  uint32_t* touched;
+  uint32_t* fresh;
+  uint32_t* blist;
+  uint32_t epoch;
+  DevCounters* dc;
+};
+
+__device__ __forceinline__ int floor_i(float v) { return (int)floorf(v); }
+
+__device__ void mark_touched(const TouchArgs& a, uint32_t slot) {
+  if (atomicExch(&a.hmark[slot], a.epoch) != a.epoch) {
+    const uint32_t t = atomicAdd(&a.dc->n_touched, 1u);
+    a.touched[t] = slot;
+  }
+}
+
+// returns the slot of key (inserted if new), or -1 when the probe bound is hit
+__device__ int64_t insert_block(const TouchArgs& a, unsigned long long key) {
+  uint32_t slot = hash_slot(key, a.hash_cap);
+  for (int probe = 0; probe < kMaxProbes; ++probe) {
+    const unsigned long long prev = atomicCAS(&a.hkeys[slot], kEmpty, key);
+    if (prev == kEmpty) {
+      const uint32_t i = atomicAdd(&a.dc->n_new, 1u);
+      a.fresh[i] = slot;
+      a.hvals[slot] = -1;
+      mark_touched(a, slot);
+      return slot;
+    }
+    if (prev == key) {
+      mark_touched(a, slot);
+      return slot;
+    }
+    slot = (uint32_t)((slot + 1) & (uint32_t)(a.hash_cap - 1));
+  }
+  set_error(a.dc, SBKI_ERR_CAPACITY);
+  return -1;
+}
+
+// slot of a key already in the table, or -1
+__device__ int64_t find_block(const TouchArgs& a, unsigned long long key) {
+  uint32_t slot = hash_slot(key, a.hash_cap);
+  for (int probe = 0; probe < kMaxProbes; ++probe) {
+    const unsigned long long k = a.hkeys[slot];
+    if (k == key) return slot;
+    if (k == kEmpty) return -1;
+    slot = (uint32_t)((slot + 1) & (uint32_t)(a.hash_cap - 1));
+  }
+  return -1;
+}
+
+// per axis: smallest |e| over the block's voxels, e(j) = E0 + j res with E0
+// the compensated offset of the block's first voxel centre (hi + lo)
+__device__ __forceinline__ float axis_min32(float hi, float lo, const Geom& g, int& jbest) {
+  int j = (int)floorf(__fmul_rn(-hi, g.inv_res) + 0.5f);
+  j = min(max(j, 0), g.B - 1);
+  float best = 3.0e38f;
+  jbest = j;
+#pragma unroll
+  for (int d = -1; d <= 1; ++d) {
+    const int jj = j + d;
+    if (jj < 0 || jj >= g.B) continue;
+    const float e = fabsf(centre_offset_at(jj, hi, lo, g));
+    if (e < best) {
+      best = e;
+      jbest = jj;
+    }
+  }
+  return best;
+}
+
+__device__ __forceinline__ double axis_min64(int K0, int jc, float x, const Geom& g) {
+  double best = 1.0e300;
+  for (int d = -2; d <= 2; ++d) {
+    const int jj = jc + d;
+    if (jj < 0 || jj >= g.B) continue;
+    const double e = fabs(__dsub_rn(__dmul_rn(__dadd_rn((double)(K0 + jj), 0.5), g.res64), (double)x));
+    best = fmin(best, e);
+  }
+  return best;
+}
+
+// Does the block with first voxel K0 hold a voxel centre within l of x?
+__device__ bool touches_block(const int K0[3], const float xs[3], const Geom& g) {
+  float m[3];
+  int jb[3];
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    float hi, lo;
+    centre_offset0(K0[ax], xs[ax], g, hi, lo);
+    m[ax] = axis_min32(hi, lo, g, jb[ax]);
+  }
+  const float d2 = __fmaf_rn(m[0], m[0], __fmaf_rn(m[1], m[1], __fmul_rn(m[2], m[2])));
+  if (d2 < g.l2_lo) return true;
+  if (!(d2 < g.l2_hi)) return false;
+  const double ex = axis_min64(K0[0], jb[0], xs[0], g);
+  const double ey = axis_min64(K0[1], jb[1], xs[1], g);
+  const double ez = axis_min64(K0[2], jb[2], xs[2], g);
+  const double d64 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
+  return d64 < g.l2_64;
+}
+
+// candidate block range of a point: at most 3 blocks per axis (l <= 0.75 B res)
+__device__ void candidate_blocks(const float xs[3], const Geom& g, int blo[3], int bhi[3]) {
+  const float lw = __fmul_rn(sqrtf(g.l2_hi), 1.001f);
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    const int vlo = floor_i(__fmul_rn(__fsub_rn(xs[ax], lw), g.inv_res)) - 1;
+    const int vhi = floor_i(__fmul_rn(__fadd_rn(xs[ax], lw), g.inv_res)) + 1;
+    blo[ax] = vlo >> g.B_shift;
+    bhi[ax] = min(vhi >> g.B_shift, blo[ax] + 2);
+  }
+}
+
+// Every lane walks the same cube of candidate blocks around the block of its
+// point (warp-uniform trip count, at most 3x3x3), so the warp-wide match that
+// lets one lane insert a block reached by several lanes always sees all 32
+// lanes.  The
+// inserting lane also adds the number of lanes that touch the block to its
+// point count (used to lay out the per-block point lists).
+__global__ void __launch_bounds__(256) touch_kernel(TouchArgs a) {
+  const Geom& g = a.g;
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = a.dc->err == 0 && i < a.dc->n_train;
+  float xs[3] = {0.f, 0.f, 0.f};
+  int blo[3] = {0, 0, 0}, bhi[3] = {-1, -1, -1};
+  if (active) {
+    const float4 p = a.train[i];
+    xs[0] = p.x;
+    xs[1] = p.y;
+    xs[2] = p.z;
+    candidate_blocks(xs, g, blo, bhi);
+  }
+  // the warp walks the smallest cube of candidate offsets that covers every lane
+  const int mx = __reduce_max_sync(0xffffffffu, (unsigned)max(0, bhi[0] - blo[0] + 1));
+  const int my = __reduce_max_sync(0xffffffffu, (unsigned)max(0, bhi[1] - blo[1] + 1));
+  const int mz = __reduce_max_sync(0xffffffffu, (unsigned)max(0, bhi[2] - blo[2] + 1));
+  const int nc = mx * my * mz;
+  for (int c = 0; c < nc; ++c) {
+    const int bx = blo[0] + c % mx, by = blo[1] + (c / mx) % my, bz = blo[2] + c / (mx * my);
+    bool hit = bx <= bhi[0] && by <= bhi[1] && bz <= bhi[2];
+    if (hit) {
+      const int K0[3] = {bx << g.B_shift, by << g.B_shift, bz << g.B_shift};
+      hit = touches_block(K0, xs, g);
+    }
+    const unsigned long long key = hit ? pack_block(bx, by, bz) : kEmpty;
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    if (hit && (unsigned)(__ffs(peers) - 1) == (threadIdx.x & 31u)) {
+      const int64_t slot = insert_block(a, key);
+      if (slot >= 0) atomicAdd(&a.hcnt[slot], (uint32_t)__popc(peers));
+    }
+  }
+}
+
+// Same walk as touch_kernel: every (point, touched block) pair takes the next
+// entry of the block's list.
+__global__ void __launch_bounds__(256) bin_fill_kernel(TouchArgs a) {
+  const Geom& g = a.g;
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = a.dc->err == 0 && i < a.dc->n_train;
+  float xs[3] = {0.f, 0.f, 0.f};
+  int blo[3] = {0, 0, 0}, bhi[3] = {-1, -1, -1};
+  if (active) {
+    const float4 p = a.train[i];
+    xs[0] = p.x;
+    xs[1] = p.y;
+    xs[2] = p.z;
+    candidate_blocks(xs, g, blo, bhi);
+  }
+  const uint32_t lane_lt = (1u << (threadIdx.x & 31u)) - 1u;
+  // the warp walks the smallest cube of candidate offsets that covers every lane
+  const int mx = __reduce_max_sync(0xffffffffu, (unsigned)max(0, bhi[0] - blo[0] + 1));
+  const int my = __reduce_max_sync(0xffffffffu, (unsigned)max(0, bhi[1] - blo[1] + 1));
+  const int mz = __reduce_max_sync(0xffffffffu, (unsigned)max(0, bhi[2] - blo[2] + 1));
+  const int nc = mx * my * mz;
+  for (int c = 0; c < nc; ++c) {
+    const int bx = blo[0] + c % mx, by = blo[1] + (c / mx) % my, bz = blo[2] + c / (mx * my);
+    bool hit = bx <= bhi[0] && by <= bhi[1] && bz <= bhi[2];
+    if (hit) {
+      const int K0[3] = {bx << g.B_shift, by << g.B_shift, bz << g.B_shift};
+      hit = touches_block(K0, xs, g);
+    }
+    const unsigned long long key = hit ? pack_block(bx, by, bz) : kEmpty;
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (hit && leader == (int)(threadIdx.x & 31u)) {
+      const int64_t slot = find_block(a, key);
+      base = slot >= 0 ? atomicAdd(&a.hcur[slot], (uint32_t)__popc(peers)) : 0xffffffffu;
+    }
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (hit && base != 0xffffffffu) a.blist[base + __popc(peers & lane_lt)] = i;
+  }
+}
+
+// boff[t] = point count of touched block t (beyond n_touched: 0), then scanned
+__global__ void bin_counts_kernel(const uint32_t* touched, const uint32_t* hcnt, uint32_t* boff, uint32_t bound,
+                                  const DevCounters* dc) {
+  const uint32_t nt = dc->n_touched;
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < bound; t += gridDim.x * blockDim.x)
+    boff[t] = t < nt ? hcnt[touched[t]] : 0u;
+}
+
+// cursors from the scanned offsets; counts back to zero for the next update
+__global__ void bin_cursor_kernel(const uint32_t* touched, uint32_t* hcnt, uint32_t* hcur, const uint32_t* boff,
+                                  int64_t list_cap, DevCounters* dc) {
+  const uint32_t nt = dc->n_touched;
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+    const uint32_t slot = touched[t];
+    hcur[slot] = boff[t];
+    hcnt[slot] = 0u;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    dc->n_list = boff[nt];
+    if ((int64_t)boff[nt] > list_cap) set_error(dc, SBKI_ERR_CAPACITY);
+  }
+}
+
+__global__ void commit_kernel(unsigned long long* hkeys, int32_t* hvals, const uint32_t* fresh,
+                              unsigned long long* pool_keys, int64_t pool_blocks, DevCounters* dc) {
+  const uint32_t n_new = dc->n_new;
+  const uint32_t nb = dc->n_blocks;
+  const bool pending = dc->err != 0;
+  const bool overflow = (unsigned long long)nb + n_new > (unsigned long long)pool_blocks;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_new; i += gridDim.x * blockDim.x) {
+    const uint32_t slot = fresh[i];
+    if (pending || overflow) {
+      hkeys[slot] = kEmpty;  // roll back: the map keeps its previous block set
+    } else {
+      const uint32_t pool = nb + i;
+      hvals[slot] = (int32_t)pool;
+      pool_keys[pool] = hkeys[slot];
+    }
+  }
+}
+
+__global__ void commit_counts_kernel(int64_t pool_blocks, DevCounters* dc) {
+  const uint32_t nb = dc->n_blocks;
+  dc->n_blocks_before = nb;
+  if (dc->err != 0) return;
+  if ((unsigned long long)nb + dc->n_new > (unsigned long long)pool_blocks) {
+    set_error(dc, SBKI_ERR_CAPACITY);
+    return;
+  }
+  dc->n_blocks = nb + dc->n_new;
+}
+
+}  // namespace
+
+cudaError_t launch_touch_blocks(MapState& m, const KeyFrame& /*kf*/, int64_t bound) {
+  TouchArgs a;
+  a.g = m.g;
+  a.train = m.s.train;
+  a.hkeys = m.hkeys;
+  a.hvals = m.hvals;
+  a.hmark = m.hmark;
+  a.hash_cap = m.hash_cap;
+  a.touched = m.s.touched;
+  a.fresh = m.s.fresh;
+  a.hcnt = m.hcnt;
+  a.hcur = m.hcur;
+  a.blist = m.blist;
+  a.epoch = m.epoch;
+  a.dc = m.dc;
+  // bound: the training points never exceed the items of the update
+  const int64_t blocks = std::max<int64_t>(1, (bound + 255) / 256);
+  touch_kernel<<<(unsigned)blocks, 256, 0, m.stream>>>(a);
+  m.launches += 1;
+  return cudaGetLastError();
+}
+
+// After commit: per touched block the list of training points that touch it.
+cudaError_t launch_bin_points(MapState& m, int64_t bound) {
+  TouchArgs a;
+  a.g = m.g;
+  a.train = m.s.train;
+  a.hkeys = m.hkeys;
+  a.hvals = m.hvals;
+  a.hmark = m.hmark;
+  a.hash_cap = m.hash_cap;
+  a.touched = m.s.touched;
+  a.fresh = m.s.fresh;
+  a.hcnt = m.hcnt;
+  a.hcur = m.hcur;
+  a.blist = m.blist;
+  a.epoch = m.epoch;
+  a.dc = m.dc;
+  // touched blocks never exceed 27 per training point nor the hash size
+  const int64_t tb = std::min<int64_t>(m.hash_cap, 27 * std::max<int64_t>(bound, 1));
+  bin_counts_kernel<<<(unsigned)std::min<int64_t>((tb + 255) / 256, 4096), 256, 0, m.stream>>>(
+      m.s.touched, m.hcnt, m.boff, (uint32_t)tb, m.dc);
+  cudaError_t e = exclusive_scan_u32(m.boff, tb, m.s.scan_tmp, m.stream);
+  if (e != cudaSuccess) return e;
+  bin_cursor_kernel<<<m.sm_count * 4, 256, 0, m.stream>>>(m.s.touched, m.hcnt, m.hcur, m.boff, m.list_cap, m.dc);
+  const int64_t blocks = std::max<int64_t>(1, (bound + 255) / 256);
+  bin_fill_kernel<<<(unsigned)blocks, 256, 0, m.stream>>>(a);
+  m.launches += 1 + 3 + 1 + 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_commit_blocks(MapState& m) {
+  commit_kernel<<<m.sm_count * 2, 256, 0, m.stream>>>(m.hkeys, m.hvals, m.s.fresh, m.pool_keys, m.pool_blocks, m.dc);
+  commit_counts_kernel<<<1, 1, 0, m.stream>>>(m.pool_blocks, m.dc);
+  m.launches += 2;
+  return cudaGetLastError();
+}
+
+}  // namespace sbki

@@ -1,0 +1,67 @@
+"""Writes kernel_poly.cuh: the sparse kernel of Eq. (kernel) in a form that
+FP32 evaluates to a small *relative* error everywhere on [0, l).
+
+f(r) = (2 + cos 2 pi r)(1 - r)/3 + sin(2 pi r)/(2 pi) has a fifth-order zero at
+r = 1 (f ~ 4 pi^4 / 45 (1 - r)^5), so the textbook form loses all relative
+precision there to cancellation.  With u = 1 - r,
+    f = u^5 Q(u^2),   Q(w) = f(1 - sqrt(w)) / w^(5/2),
+and Q is analytic and bounded on [0, 1] (Q(0) = 4 pi^4 / 45, Q(1) = 1).
+Q is approximated by Chebyshev interpolation of degree N at the N+1
+Chebyshev nodes of [0, 1] (values from mpmath at 60 digits), converted to
+monomials in x = 2w - 1 for a Horner evaluation.
+
+Run:  python gen_kernel_poly.py   (from this directory)
+"""
+import os
+
+import mpmath as mp
+import numpy as np
+from numpy.polynomial import chebyshev as Ch
+
+N = 9
+mp.mp.dps = 60
+
+
+def f(r):
+    r = mp.mpf(r)
+    return (2 + mp.cos(2 * mp.pi * r)) * (1 - r) / 3 + mp.sin(2 * mp.pi * r) / (2 * mp.pi)
+
+
+def Q(w):
+    u = mp.sqrt(mp.mpf(w))
+    return f(1 - u) / u ** 5
+
+
+def coefficients(n=N):
+    k = np.arange(n + 1)
+    x = np.cos(np.pi * (k + 0.5) / (n + 1))
+    vals = np.array([float(Q((xi + 1) / 2)) for xi in x])
+    return Ch.cheb2poly(Ch.chebfit(x, vals, n))
+
+
+def main():
+    c = coefficients()
+    lines = [
+        "// Generated by gen_kernel_poly.py - do not edit.",
+        "// Sparse kernel f(r) of Eq. (kernel) as f = u^5 Q(u^2), u = 1 - r, with Q a degree-%d" % N,
+        "// Chebyshev interpolant on w = u^2 in [0, 1], stored as monomials in x = 2w - 1.",
+        "#pragma once",
+        "",
+        "namespace sbki {",
+        "",
+        "constexpr int kPolyDegree = %d;" % N,
+        "__device__ __forceinline__ float kernel_q(float w) {",
+        "  const float x = __fmaf_rn(2.0f, w, -1.0f);",
+        "  float acc = %.9ef;" % c[-1],
+    ]
+    for a in c[-2::-1]:
+        lines.append("  acc = __fmaf_rn(acc, x, %.9ef);" % a)
+    lines += ["  return acc;", "}", "", "}  // namespace sbki", ""]
+    out = os.path.join(os.path.dirname(os.path.abspath(__file__)), "kernel_poly.cuh")
+    with open(out, "w") as fh:
+        fh.write("\n".join(lines))
+    print("wrote", out)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,739 @@
+// Steps a1-a3 of the per-scan update (Sec. III): transform and validate the
+// hits, generate the free-space samples along every beam, and downsample hits
+// and samples to one centroid per (downsampling cell, label).
+//
+// Every operation that decides an integer (which points survive, how many
+// samples a beam gets, which cell a point falls in) uses round-to-nearest
+// intrinsics in a fixed order, so the compiler cannot contract or reorder it:
+//   world  = fp32( ((r0 px + r1 py) + r2 pz) + t )      (FP64, then one rounding)
+//   r      = sqrt( (dx dx + dy dy) + dz dz ),  d = h - o  (FP32)
+//   t_j    = r - fp32(j) * s,   sample = o + d * (t_j / r) (FP32), j >= 1 while t_j > 0
+//   cell   = floor( x * fp32(1/ds) )                       (FP32)
+// The centroid of a cell is, per axis, the exact mean of its members'
+// coordinates rounded once to FP32 (see the centroid kernels).
+#include <algorithm>
+
+#include "sbki_internal.cuh"
+
+namespace sbki {
+namespace {
+
+constexpr unsigned long long kValidOne = 1ull << 40;
+constexpr unsigned long long kFreeMask = kValidOne - 1;
+
+struct Pose {
+  double r[9];
+  double t[3];
+  float o[3];
+};
+
+__device__ __forceinline__ int floor_i(float v) { return (int)floorf(v); }
+
+// sort key: [rel tile x | rel tile y | rel tile z | local cell (z,y,x) | label]
+__device__ __forceinline__ unsigned long long make_key(float x, float y, float z, int label, const Geom& g,
+                                                       const KeyFrame& kf, DevCounters* dc) {
+  int gx = floor_i(__fmul_rn(x, g.inv_ds));
+  int gy = floor_i(__fmul_rn(y, g.inv_ds));
+  int gz = floor_i(__fmul_rn(z, g.inv_ds));
+  int tx = (gx >> kTileShift) - kf.org[0];
+  int ty = (gy >> kTileShift) - kf.org[1];
+  int tz = (gz >> kTileShift) - kf.org[2];
+  const int lim = 1 << kf.bits;
+  if (tx < 0 || ty < 0 || tz < 0 || tx >= lim || ty >= lim || tz >= lim) {
+    set_error(dc, SBKI_ERR_INVALID_ARG);
+    tx = ty = tz = 0;
+  }
+  unsigned long long tile = ((unsigned long long)tx << (2 * kf.bits)) | ((unsigned long long)ty << kf.bits) |
+                            (unsigned long long)tz;
+  unsigned long long local = (unsigned long long)(((gz & (kTileEdge - 1)) << (2 * kTileShift)) |
+                                                  ((gy & (kTileEdge - 1)) << kTileShift) | (gx & (kTileEdge - 1)));
+  return (((tile << kLocalBits) | local) << g.label_bits) | (unsigned long long)label;
+}
+
+// number of j >= 1 with fp32(j) * s < r  (the set is a prefix since fp32(j)*s is monotone in j)
+__device__ __forceinline__ uint32_t free_count(float r, float s) {
+  if (!(r > 0.0f)) return 0;
+  float q = __fdiv_rn(r, s);
+  int j = q < 1.6e7f ? (int)q : 16000000;
+  for (int it = 0; it < 4 && j > 0 && !(__fmul_rn((float)j, s) < r); ++it) --j;
+  for (int it = 0; it < 4 && __fmul_rn((float)(j + 1), s) < r; ++it) ++j;
+  return (uint32_t)(j < 0 ? 0 : j);
+}
+
+__global__ void transform_count_kernel(const float* __restrict__ pts, const int32_t* __restrict__ labels, int64_t n,
+                                       Pose pose, Geom g, float4* __restrict__ world,
+                                       unsigned long long* __restrict__ cnt, DevCounters* dc) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float px = pts[3 * i], py = pts[3 * i + 1], pz = pts[3 * i + 2];
+  const int lab = labels[i];
+  if (lab < 1 || lab > g.K1 - 1) set_error(dc, SBKI_ERR_LABEL_RANGE);
+  bool ok = isfinite(px) && isfinite(py) && isfinite(pz);
+  unsigned long long c = 0;
+  float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (ok) {
+    const double dx = px, dy = py, dz = pz;
+    const double range = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
+    ok = range >= g.min_range && range <= g.max_range;
+    if (ok) {
+      float wc[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        double acc = __dmul_rn(pose.r[3 * r], dx);
+        acc = __dadd_rn(acc, __dmul_rn(pose.r[3 * r + 1], dy));
+        acc = __dadd_rn(acc, __dmul_rn(pose.r[3 * r + 2], dz));
+        acc = __dadd_rn(acc, pose.t[r]);
+        wc[r] = __double2float_rn(acc);
+      }
+      const float ex = __fsub_rn(wc[0], pose.o[0]);
+      const float ey = __fsub_rn(wc[1], pose.o[1]);
+      const float ez = __fsub_rn(wc[2], pose.o[2]);
+      const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
+      const float rr = __fsqrt_rn(r2);
+      c = kValidOne | (unsigned long long)free_count(rr, g.step);
+      w = make_float4(wc[0], wc[1], wc[2], (float)lab);
+    }
+  }
+  world[i] = w;
+  cnt[i] = c;
+}
+
+__global__ void check_counts_kernel(const unsigned long long* cnt, int64_t n, int64_t cap, DevCounters* dc) {
+  const unsigned long long tot = cnt[n];
+  const uint32_t nv = (uint32_t)(tot >> 40);
+  const unsigned long long nf = tot & kFreeMask;
+  dc->n_valid = nv;
+  dc->n_free = nf;
+  const unsigned long long items = (unsigned long long)nv + nf;
+  if (items > (unsigned long long)cap) {
+    set_error(dc, SBKI_ERR_CAPACITY);
+    dc->n_items = 0;
+  } else {
+    dc->n_items = (uint32_t)items;
+  }
+}
+
+// one warp per 32 input points; the warp writes each beam's samples together
+__global__ void __launch_bounds__(256) emit_kernel(const float4* __restrict__ world,
+                                                   const unsigned long long* __restrict__ cnt, int64_t n, Pose pose,
+                                                   Geom g, KeyFrame kf, float4* __restrict__ items,
+                                                   unsigned long long* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                   DevCounters* dc) {
+  if (dc->err) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const unsigned long long nvalid = cnt[n] >> 40;
+  const float ox = pose.o[0], oy = pose.o[1], oz = pose.o[2];
+  for (int64_t base = warp * 32; base < n; base += nwarps * 32) {
+    const int64_t i = base + lane;
+    uint32_t nfree = 0;
+    unsigned long long fpos = 0;
+    float ex = 0.f, ey = 0.f, ez = 0.f, rr = 0.f;
+    if (i < n) {
+      const unsigned long long c0 = cnt[i], c1 = cnt[i + 1];
+      if ((c1 >> 40) != (c0 >> 40)) {  // a kept hit
+        const float4 w = world[i];
+        const unsigned long long hpos = c0 >> 40;
+        items[hpos] = w;
+        keys[hpos] = make_key(w.x, w.y, w.z, (int)w.w, g, kf, dc);
+        vals[hpos] = (uint32_t)hpos;
+        nfree = (uint32_t)((c1 & kFreeMask) - (c0 & kFreeMask));
+        fpos = nvalid + (c0 & kFreeMask);
+        ex = __fsub_rn(w.x, ox);
+        ey = __fsub_rn(w.y, oy);
+        ez = __fsub_rn(w.z, oz);
+        rr = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez)));
+      }
+    }
+    for (int src = 0; src < 32; ++src) {
+      const uint32_t m = __shfl_sync(0xffffffffu, nfree, src);
+      if (m == 0) continue;
+      const float sx = __shfl_sync(0xffffffffu, ex, src);
+      const float sy = __shfl_sync(0xffffffffu, ey, src);
+      const float sz = __shfl_sync(0xffffffffu, ez, src);
+      const float sr = __shfl_sync(0xffffffffu, rr, src);
+      const unsigned long long sp = __shfl_sync(0xffffffffu, fpos, src);
+      for (uint32_t j = lane + 1; j <= m; j += 32) {
+        const float t = __fsub_rn(sr, __fmul_rn((float)j, g.step));
+        const float q = __fdiv_rn(t, sr);
+        const float x = __fadd_rn(ox, __fmul_rn(sx, q));
+        const float y = __fadd_rn(oy, __fmul_rn(sy, q));
+        const float z = __fadd_rn(oz, __fmul_rn(sz, q));
+        const unsigned long long pos = sp + j - 1;
+        items[pos] = make_float4(x, y, z, 0.f);
+        keys[pos] = make_key(x, y, z, 0, g, kf, dc);
+        vals[pos] = (uint32_t)pos;
+      }
+    }
+  }
+}
+
+__global__ void seg_flags_kernel(const unsigned long long* __restrict__ keys, int64_t n, uint32_t* __restrict__ flags,
+                                 const DevCounters* dc) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || dc->err) return;
+  flags[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1u : 0u;
+}
+
+__global__ void seg_start_kernel(const unsigned long long* __restrict__ keys, int64_t n,
+                                 const uint32_t* __restrict__ segid, uint32_t* __restrict__ seg_start,
+                                 DevCounters* dc) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || dc->err) return;
+  if (i == 0 || keys[i] != keys[i - 1]) seg_start[segid[i]] = (uint32_t)i;
+  if (i == n - 1) {
+    seg_start[segid[n]] = (uint32_t)n;
+    dc->n_train = segid[n];
+  }
+}
+
+// Centroids: per axis the exact mean of the members' FP32 coordinates,
+// rounded once to FP32 (nearest, ties to even).  No floating point is used:
+// every nonzero |x| is m 2^e with an integer m < 2^24 and e = its exponent of
+// the last mantissa bit; with E the smallest such e in the cell,
+//     sum |x| = T 2^E,   T = sum m 2^(e - E)
+// is an integer held exactly in 128 bits whenever the members' e span fewer
+// than 127 - 24 - ceil(log2 n) binades (cells next to a coordinate plane
+// included), and the mean is T 2^E / n, rounded with integer division.  The
+// members of a cell share a sign per axis (the cell index fixes it).  Cells
+// beyond that span, or whose mean is below the FP32 normal range, take a
+// one-thread path with 512-bit arithmetic (exact for every FP32 input).
+// Short segments (<= kShort members) are summed by one lane
+// (centroid_kernel), longer ones by a warp (mid_centroid_kernel), the longest
+// (> kHuge) by a whole CTA (huge_centroid_kernel).
+constexpr uint32_t kShort = 16;
+constexpr uint32_t kHuge = 1024;
+
+struct U128 {
+  unsigned long long lo, hi;
+};
+
+__device__ __forceinline__ float axis_of(const float4& p, int ax) { return ax == 0 ? p.x : (ax == 1 ? p.y : p.z); }
+
+// |v| = m 2^e (m < 2^24 integer); returns false for zero
+__device__ __forceinline__ bool decompose(float v, unsigned& m, int& e) {
+  const unsigned b = __float_as_uint(v) & 0x7fffffffu;
+  if (b == 0u) return false;
+  const unsigned E = b >> 23;
+  m = (b & 0x7fffffu) | (E ? 0x800000u : 0u);
+  e = E ? (int)E - 150 : -149;
+  return true;
+}
+
+__device__ __forceinline__ void u128_add(U128& t, unsigned long long lo, unsigned long long hi) {
+  t.lo += lo;
+  t.hi += hi + (t.lo < lo ? 1ull : 0ull);
+}
+
+// t += m 2^sh, 0 <= sh <= 103
+__device__ __forceinline__ void u128_add_shifted(U128& t, unsigned long long m, int sh) {
+  if (sh == 0) u128_add(t, m, 0ull);
+  else if (sh < 64) u128_add(t, m << sh, m >> (64 - sh));
+  else u128_add(t, 0ull, m << (sh - 64));
+}
+
+__device__ __forceinline__ int bitlen64(unsigned long long v) { return v ? 64 - __clzll((long long)v) : 0; }
+
+struct AxisAcc {
+  int emin, emax;  // range of the members' last-mantissa-bit exponents
+  bool neg;
+  __device__ void init() {
+    emin = 1 << 20;
+    emax = -(1 << 20);
+    neg = false;
+  }
+  __device__ void see(float v) {
+    unsigned m;
+    int e;
+    if (decompose(v, m, e)) {
+      emin = min(emin, e);
+      emax = max(emax, e);
+      neg |= v < 0.0f;
+    }
+  }
+  __device__ bool empty() const { return emax < emin; }
+  __device__ bool fits(uint32_t n) const {  // T stays below 2^127
+    int lg = 0;
+    while ((1u << lg) < n) ++lg;
+    return empty() || emax - emin + 24 + lg <= 126;
+  }
+  __device__ void add(U128& t, float v) const {
+    unsigned m;
+    int e;
+    if (decompose(v, m, e)) u128_add_shifted(t, m, e - emin);
+  }
+};
+
+// round(T 2^s / n) to FP32; false when the result is below the normal range
+__device__ bool round_mean(U128 T, unsigned long long n, int s, float& out) {
+  const int bt = T.hi ? 64 + bitlen64(T.hi) : bitlen64(T.lo);
+  const int bn = bitlen64(n);
+  const int k = 26 + bn - bt;  // q = floor(T 2^k / n) in [2^24, 2^27)
+  unsigned long long q;
+  bool sticky;
+  if (k >= 0) {
+    const unsigned long long num = T.lo << k;  // bt + k = 26 + bn <= 58 bits
+    q = num / n;
+    sticky = num - q * n != 0ull;
+  } else {
+    const int m = -k;
+    unsigned long long ts, lost;
+    if (m < 64) {
+      ts = (T.lo >> m) | (m ? (T.hi << (64 - m)) : 0ull);
+      lost = T.lo & ((1ull << m) - 1ull);
+    } else {
+      ts = T.hi >> (m - 64);
+      lost = T.lo | (T.hi & ((m - 64 == 0) ? 0ull : ((1ull << (m - 64)) - 1ull)));
+    }
+    q = ts / n;
+    sticky = lost != 0ull || ts - q * n != 0ull;
+  }
+  const int qb = bitlen64(q);
+  if (qb - 1 - k + s < -126) return false;
+  const int sh = qb - 24;
+  unsigned long long mant = q >> sh;
+  const unsigned long long rb = q & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+  if (rb > half || (rb == half && (sticky || (mant & 1ull)))) mant += 1ull;
+  int e = sh - k + s;
+  if (mant == (1ull << 24)) {
+    mant >>= 1;
+    e += 1;
+  }
+  out = ldexpf((float)mant, e);
+  return true;
+}
+
+// One thread: exact mean of axis ax of members [a, b) for any FP32 input.
+// The sum is held in 16 32-bit limbs in units of 2^-149 (512 bits).
+__device__ float wide_mean(const float4* __restrict__ items, const uint32_t* __restrict__ perm, uint32_t a,
+                           uint32_t b, int ax) {
+  uint32_t w[16];
+  for (int i = 0; i < 16; ++i) w[i] = 0u;
+  bool neg = false;
+  for (uint32_t i = a; i < b; ++i) {
+    const float v = axis_of(items[perm[i]], ax);
+    unsigned m;
+    int e;
+    if (!decompose(v, m, e)) continue;
+    neg |= v < 0.0f;
+    const int sh = e + 149, li = sh >> 5, bi = sh & 31;
+    unsigned long long add = (unsigned long long)m << bi;  // < 2^55
+    for (int j = li; j < 16 && add; ++j) {
+      const unsigned long long t = (unsigned long long)w[j] + (add & 0xffffffffull);
+      w[j] = (uint32_t)t;
+      add = (add >> 32) + (t >> 32);
+    }
+  }
+  const unsigned long long n = b - a;
+  // quotient of (sum 2^96) / n, limb by limb from the top, in 19 limbs
+  uint32_t q[19];
+  unsigned long long r = 0ull;
+  for (int j = 18; j >= 0; --j) {
+    const unsigned long long cur = (r << 32) | (j >= 3 ? w[j - 3] : 0u);
+    q[j] = (uint32_t)(cur / n);
+    r = cur - (unsigned long long)q[j] * n;
+  }
+  int qb = 0;
+  for (int j = 18; j >= 0 && !qb; --j)
+    if (q[j]) qb = 32 * j + 32 - __clz((int)q[j]);
+  if (qb == 0) return 0.0f;
+  // value = q 2^(-149 - 96); keep 24 bits, fewer for a subnormal result
+  const int lead = qb - 1 - 245;
+  int keep = lead < -126 ? 24 - (-126 - lead) : 24;
+  if (keep < 0) keep = 0;
+  const int drop = qb - keep;
+  auto bit = [&](int i) -> unsigned { return i >= 0 ? (q[i >> 5] >> (i & 31)) & 1u : 0u; };
+  unsigned long long mant = 0ull;
+  for (int i = qb - 1; i >= drop; --i) mant = (mant << 1) | bit(i);
+  bool sticky = r != 0ull;
+  for (int i = 0; i < drop - 1 && !sticky; ++i) sticky = bit(i) != 0u;
+  if (bit(drop - 1) && (sticky || (mant & 1ull))) mant += 1ull;
+  const float f = ldexpf((float)mant, drop - 245);
+  return neg ? -f : f;
+}
+
+__device__ float finish_axis(const AxisAcc& s, bool fits, U128 T, uint32_t n, const float4* items,
+                             const uint32_t* perm, uint32_t a, uint32_t b, int ax) {
+  if (s.empty()) return 0.0f;
+  float f;
+  if (fits && round_mean(T, n, s.emin, f)) return s.neg ? -f : f;
+  return wide_mean(items, perm, a, b, ax);
+}
+
+__device__ __forceinline__ U128 warp_sum_u128(U128 t) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long lo = __shfl_xor_sync(0xffffffffu, t.lo, o);
+    const unsigned long long hi = __shfl_xor_sync(0xffffffffu, t.hi, o);
+    u128_add(t, lo, hi);
+  }
+  return t;
+}
+
+__device__ __forceinline__ void warp_range(AxisAcc& s) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s.emin = min(s.emin, __shfl_xor_sync(0xffffffffu, s.emin, o));
+    s.emax = max(s.emax, __shfl_xor_sync(0xffffffffu, s.emax, o));
+  }
+  s.neg = __any_sync(0xffffffffu, s.neg);
+}
+
+__global__ void __launch_bounds__(256) centroid_kernel(const unsigned long long* __restrict__ keys,
+                                                       const uint32_t* __restrict__ perm,
+                                                       const float4* __restrict__ items,
+                                                       const uint32_t* __restrict__ seg_start, Geom g,
+                                                       float4* __restrict__ train, uint32_t* __restrict__ tflags,
+                                                       uint32_t nbound, uint32_t* __restrict__ huge,
+                                                       uint32_t* __restrict__ mid, DevCounters* dc) {
+  if (dc->err) return;
+  const uint32_t P = dc->n_train;
+  const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t nthreads = gridDim.x * blockDim.x;
+  for (uint32_t s = P + gtid; s < nbound; s += nthreads) tflags[s] = 0u;  // keep the tile-head scan exact
+  const int lane = threadIdx.x & 31;
+  const uint32_t warp = gtid >> 5, nwarps = nthreads >> 5;
+  const int tshift = kLocalBits + g.label_bits;
+  for (uint32_t base = warp * 32; base < P; base += nwarps * 32) {
+    const uint32_t s = base + lane;
+    const bool valid = s < P;
+    const uint32_t a = valid ? seg_start[s] : 0, b = valid ? seg_start[s + 1] : 0;
+    const uint32_t n = b - a;
+    const bool is_huge = valid && n > kHuge;
+    if (is_huge) huge[atomicAdd(&dc->n_huge, 1u)] = s;
+    AxisAcc ax[3];
+    U128 T[3];
+    bool fit[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      ax[c].init();
+      T[c].lo = T[c].hi = 0ull;
+    }
+    if (valid && n <= kShort) {
+      for (uint32_t i = a; i < b; ++i) {
+        const float4 p = items[perm[i]];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) ax[c].see(axis_of(p, c));
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) fit[c] = ax[c].fits(n);
+      for (uint32_t i = a; i < b; ++i) {
+        const float4 p = items[perm[i]];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          if (fit[c]) ax[c].add(T[c], axis_of(p, c));
+      }
+    }
+    const bool is_mid = valid && n > kShort && !is_huge;
+    if (is_mid) mid[atomicAdd(&dc->n_mid, 1u)] = s;
+    if (valid && n <= kShort) {
+      const unsigned long long k = keys[a];
+      const int label = (int)(k & ((1ull << g.label_bits) - 1));
+      float out[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) out[c] = finish_axis(ax[c], fit[c], T[c], n, items, perm, a, b, c);
+      train[s] = make_float4(out[0], out[1], out[2], (float)label);
+      tflags[s] = (s == 0 || (k >> tshift) != (keys[seg_start[s - 1]] >> tshift)) ? 1u : 0u;
+    }
+  }
+}
+
+// Segments of kShort+1 .. kHuge members: one warp each, spread over the grid
+// (neighbouring cells near the sensor are all long; a warp per group of 32
+// consecutive cells would serialise them).
+__global__ void __launch_bounds__(256) mid_centroid_kernel(const unsigned long long* __restrict__ keys,
+                                                           const uint32_t* __restrict__ perm,
+                                                           const float4* __restrict__ items,
+                                                           const uint32_t* __restrict__ seg_start, Geom g,
+                                                           float4* __restrict__ train, uint32_t* __restrict__ tflags,
+                                                           const uint32_t* __restrict__ mid, DevCounters* dc) {
+  if (dc->err) return;
+  const uint32_t nm = dc->n_mid;
+  const int lane = threadIdx.x & 31;
+  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int tshift = kLocalBits + g.label_bits;
+  for (uint32_t j = warp; j < nm; j += nwarps) {
+    const uint32_t s = mid[j];
+    const uint32_t a = seg_start[s], b = seg_start[s + 1], n = b - a;
+    AxisAcc w[3];
+    U128 t[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      w[c].init();
+      t[c].lo = t[c].hi = 0ull;
+    }
+    for (uint32_t i = a + lane; i < b; i += 32) {
+      const float4 p = items[perm[i]];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) w[c].see(axis_of(p, c));
+    }
+    bool fit[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      warp_range(w[c]);
+      fit[c] = w[c].fits(n);
+    }
+    for (uint32_t i = a + lane; i < b; i += 32) {
+      const float4 p = items[perm[i]];
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        if (fit[c]) w[c].add(t[c], axis_of(p, c));
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) t[c] = warp_sum_u128(t[c]);
+    if (lane == 0) {
+      float out[3];
+      for (int c = 0; c < 3; ++c) out[c] = finish_axis(w[c], fit[c], t[c], n, items, perm, a, b, c);
+      const unsigned long long k = keys[a];
+      const int label = (int)(k & ((1ull << g.label_bits) - 1));
+      train[s] = make_float4(out[0], out[1], out[2], (float)label);
+      tflags[s] = (s == 0 || (k >> tshift) != (keys[seg_start[s - 1]] >> tshift)) ? 1u : 0u;
+    }
+  }
+}
+
+// Segments of more than kHuge members (cells next to the sensor): one CTA
+// each, same arithmetic as centroid_kernel.
+__global__ void __launch_bounds__(256) huge_centroid_kernel(const unsigned long long* __restrict__ keys,
+                                                            const uint32_t* __restrict__ perm,
+                                                            const float4* __restrict__ items,
+                                                            const uint32_t* __restrict__ seg_start, Geom g,
+                                                            float4* __restrict__ train, uint32_t* __restrict__ tflags,
+                                                            const uint32_t* __restrict__ huge, DevCounters* dc) {
+  __shared__ int s_emin[3][8], s_emax[3][8], s_neg[3][8];
+  __shared__ unsigned long long s_lo[3][8], s_hi[3][8];
+  if (dc->err) return;
+  const uint32_t nh = dc->n_huge;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int tshift = kLocalBits + g.label_bits;
+  for (uint32_t h = blockIdx.x; h < nh; h += gridDim.x) {
+    const uint32_t s = huge[h];
+    const uint32_t a = seg_start[s], b = seg_start[s + 1], n = b - a;
+    AxisAcc w[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) w[c].init();
+    for (uint32_t i = a + threadIdx.x; i < b; i += 256) {
+      const float4 p = items[perm[i]];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) w[c].see(axis_of(p, c));
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      warp_range(w[c]);
+      if (lane == 0) {
+        s_emin[c][warp] = w[c].emin;
+        s_emax[c][warp] = w[c].emax;
+        s_neg[c][warp] = w[c].neg ? 1 : 0;
+      }
+    }
+    __syncthreads();
+    bool fit[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      int mn = 1 << 20, mx = -(1 << 20), ng = 0;
+      for (int k = 0; k < 8; ++k) {
+        mn = min(mn, s_emin[c][k]);
+        mx = max(mx, s_emax[c][k]);
+        ng |= s_neg[c][k];
+      }
+      w[c].emin = mn;
+      w[c].emax = mx;
+      w[c].neg = ng != 0;
+      fit[c] = w[c].fits(n);
+    }
+    U128 t[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) t[c].lo = t[c].hi = 0ull;
+    uint32_t i = a + threadIdx.x;
+    for (; i + 768 < b; i += 1024) {  // four independent gathers in flight
+      const float4 ps[4] = {items[perm[i]], items[perm[i + 256]], items[perm[i + 512]], items[perm[i + 768]]};
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          if (fit[c]) w[c].add(t[c], axis_of(ps[u], c));
+    }
+    for (; i < b; i += 256) {
+      const float4 p = items[perm[i]];
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        if (fit[c]) w[c].add(t[c], axis_of(p, c));
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      t[c] = warp_sum_u128(t[c]);
+      if (lane == 0) {
+        s_lo[c][warp] = t[c].lo;
+        s_hi[c][warp] = t[c].hi;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float out[3];
+      for (int c = 0; c < 3; ++c) {
+        U128 tt;
+        tt.lo = tt.hi = 0ull;
+        for (int k = 0; k < 8; ++k) u128_add(tt, s_lo[c][k], s_hi[c][k]);
+        out[c] = finish_axis(w[c], fit[c], tt, n, items, perm, a, b, c);
+      }
+      const unsigned long long k = keys[a];
+      const int label = (int)(k & ((1ull << g.label_bits) - 1));
+      train[s] = make_float4(out[0], out[1], out[2], (float)label);
+      tflags[s] = (s == 0 || (k >> tshift) != (keys[seg_start[s - 1]] >> tshift)) ? 1u : 0u;
+    }
+    __syncthreads();
+  }
+}
+
+// tile list: tile_key[t] (relative packed tile), tile_start[t] (first training point)
+__global__ void tile_list_kernel(const unsigned long long* __restrict__ keys, const uint32_t* __restrict__ seg_start,
+                                 const uint32_t* __restrict__ tid, Geom g, unsigned long long* __restrict__ tile_key,
+                                 uint32_t* __restrict__ tile_start, DevCounters* dc) {
+  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  const uint32_t P = dc->n_train;
+  if (dc->err || s >= P) return;
+  const int tshift = kLocalBits + g.label_bits;
+  const unsigned long long tk = keys[seg_start[s]] >> tshift;
+  const bool head = (s == 0) || (tk != (keys[seg_start[s - 1]] >> tshift));
+  if (head) {
+    tile_key[tid[s]] = tk;
+    tile_start[tid[s]] = s;
+  }
+  if (s == P - 1) {
+    tile_start[tid[P]] = P;
+    dc->n_tiles = tid[P];
+  }
+}
+
+// --- given training sets (no sampling or downsampling) ---------------------
+
+__global__ void train_bbox_kernel(const float4* __restrict__ in, int64_t p, Geom g, int* bbox, DevCounters* dc) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= p) return;
+  const float4 v = in[i];
+  const int lab = (int)v.w;
+  if (!(v.w == (float)lab) || lab < 0 || lab > g.K1 - 1) set_error(dc, SBKI_ERR_LABEL_RANGE);
+  if (!isfinite(v.x) || !isfinite(v.y) || !isfinite(v.z)) {
+    set_error(dc, SBKI_ERR_INVALID_ARG);
+    return;
+  }
+  const float c[3] = {v.x, v.y, v.z};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float q = __fmul_rn(c[a], g.inv_ds);
+    if (!(fabsf(q) < 1.0e6f)) {
+      set_error(dc, SBKI_ERR_INVALID_ARG);
+      return;
+    }
+    int t = floor_i(q) >> kTileShift;
+    atomicMin(&bbox[a], t);
+    atomicMax(&bbox[3 + a], t);
+  }
+}
+
+__global__ void train_keys_kernel(const float4* __restrict__ in, int64_t p, Geom g, KeyFrame kf,
+                                  unsigned long long* __restrict__ keys, uint32_t* __restrict__ vals,
+                                  DevCounters* dc) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= p || dc->err) return;
+  const float4 v = in[i];
+  keys[i] = make_key(v.x, v.y, v.z, (int)v.w, g, kf, dc);
+  vals[i] = (uint32_t)i;
+}
+
+// every point is its own segment; gather into tile order and flag tile heads
+__global__ void train_gather_kernel(const float4* __restrict__ in, const unsigned long long* __restrict__ keys,
+                                    const uint32_t* __restrict__ perm, int64_t p, Geom g,
+                                    float4* __restrict__ train, uint32_t* __restrict__ seg_start,
+                                    uint32_t* __restrict__ tflags, DevCounters* dc) {
+  int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= p || dc->err) return;
+  train[s] = in[perm[s]];
+  seg_start[s] = (uint32_t)s;
+  const int tshift = kLocalBits + g.label_bits;
+  tflags[s] = (s == 0 || (keys[s] >> tshift) != (keys[s - 1] >> tshift)) ? 1u : 0u;
+  if (s == p - 1) {
+    seg_start[p] = (uint32_t)p;
+    dc->n_train = (uint32_t)p;
+  }
+}
+
+Pose make_pose(const double T[16]) {
+  Pose p;
+  for (int r = 0; r < 3; ++r) {
+    for (int c = 0; c < 3; ++c) p.r[3 * r + c] = T[4 * r + c];
+    p.t[r] = T[4 * r + 3];
+    p.o[r] = (float)T[4 * r + 3];
+  }
+  return p;
+}
+
+inline unsigned grid_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+}  // namespace
+
+cudaError_t launch_transform_count(MapState& m, const float* pts, const int32_t* labels, int64_t n,
+                                   const double* /*unused*/, const double pose[16], const KeyFrame& /*kf*/) {
+  Pose P = make_pose(pose);
+  transform_count_kernel<<<grid_for(n, 256), 256, 0, m.stream>>>(pts, labels, n, P, m.g, m.s.world, m.s.cnt, m.dc);
+  m.launches += 1 + 3 + 1;  // transform, scan, check
+  cudaError_t e = exclusive_scan_u64(m.s.cnt, n, m.s.scan_tmp, m.stream);
+  if (e != cudaSuccess) return e;
+  check_counts_kernel<<<1, 1, 0, m.stream>>>(m.s.cnt, n, m.s.s_cap, m.dc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_emit(MapState& m, int64_t n, const double pose[16], const KeyFrame& kf) {
+  Pose P = make_pose(pose);
+  int64_t warps = (n + 31) / 32;
+  unsigned blocks = (unsigned)std::min<int64_t>((warps + 7) / 8, (int64_t)m.sm_count * 16);
+  if (blocks == 0) blocks = 1;
+  emit_kernel<<<blocks, 256, 0, m.stream>>>(m.s.world, m.s.cnt, n, P, m.g, kf, m.s.items, m.s.keys, m.s.vals, m.dc);
+  m.launches += 1;
+  return cudaGetLastError();
+}
+
+// Sorts the items and reduces each (cell, label) segment to its centroid; builds the tile list.
+// Host-known item count nitems (read back after the count step).
+cudaError_t launch_downsample_n(MapState& m, const KeyFrame& kf, int64_t nitems) {
+  Scratch& s = m.s;
+  m.launches += 5 * ((kf.total_bits + 7) / 8) + 1 + 3 + 1 + 3;  // sort, segments, centroids
+  cudaError_t e = radix_sort_pairs(s.keys, s.vals, s.keys2, s.vals2, &m.dc->n_items, nitems, kf.total_bits, s.hist,
+                                   s.scan_tmp, m.dc, m.stream);
+  if (e != cudaSuccess) return e;
+  seg_flags_kernel<<<grid_for(nitems, 256), 256, 0, m.stream>>>(s.keys, nitems, s.flags, m.dc);
+  e = exclusive_scan_u32(s.flags, nitems, s.scan_tmp, m.stream);
+  if (e != cudaSuccess) return e;
+  seg_start_kernel<<<grid_for(nitems, 256), 256, 0, m.stream>>>(s.keys, nitems, s.flags, s.seg_start, m.dc);
+  {
+    const unsigned cblocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((nitems + 255) / 256, (int64_t)m.sm_count * 16));
+    centroid_kernel<<<cblocks, 256, 0, m.stream>>>(s.keys, s.vals, s.items, s.seg_start, m.g, s.train, s.tflags,
+                                                   (uint32_t)nitems, s.huge, s.mid, m.dc);
+    mid_centroid_kernel<<<(unsigned)m.sm_count * 8, 256, 0, m.stream>>>(s.keys, s.vals, s.items, s.seg_start, m.g,
+                                                                        s.train, s.tflags, s.mid, m.dc);
+    huge_centroid_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(nitems / kHuge + 1, 1024)), 256, 0,
+                           m.stream>>>(s.keys, s.vals, s.items, s.seg_start, m.g, s.train, s.tflags, s.huge, m.dc);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_train_bbox(MapState& m, const float4* in, int64_t p, int* bbox_dev) {
+  train_bbox_kernel<<<grid_for(p, 256), 256, 0, m.stream>>>(in, p, m.g, bbox_dev, m.dc);
+  m.launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_train_prepare(MapState& m, const float4* in, int64_t p, const KeyFrame& kf) {
+  Scratch& s = m.s;
+  m.launches += 1 + 5 * ((kf.total_bits + 7) / 8) + 1;
+  train_keys_kernel<<<grid_for(p, 256), 256, 0, m.stream>>>(in, p, m.g, kf, s.keys, s.vals, m.dc);
+  cudaError_t e = radix_sort_pairs(s.keys, s.vals, s.keys2, s.vals2, &m.dc->n_items, p, kf.total_bits, s.hist,
+                                   s.scan_tmp, m.dc, m.stream);
+  if (e != cudaSuccess) return e;
+  train_gather_kernel<<<grid_for(p, 256), 256, 0, m.stream>>>(in, s.keys, s.vals, p, m.g, s.train, s.seg_start,
+                                                               s.tflags, m.dc);
+  return cudaGetLastError();
+}
+
+}  // namespace sbki

@@ -1,0 +1,769 @@
+// The C ABI of include/sbki.h: argument checks, memory ownership, pointer-kind
+// handling and the order of launches of one update.  All arithmetic of the
+// update runs in the kernels of ingest.cu, blocks.cu and accumulate.cu.
+#include <algorithm>
+#include <climits>
+#include <cstdarg>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "sbki_internal.cuh"
+
+using namespace sbki;
+
+struct sbki_map {
+  MapState st;
+};
+
+namespace {
+
+char g_create_error[512] = {0};
+
+sbki_status fail(MapState* m, sbki_status s, const char* fmt, ...) __attribute__((format(printf, 3, 4)));
+sbki_status fail(MapState* m, sbki_status s, const char* fmt, ...) {
+  char* buf = m ? m->last_error : g_create_error;
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, 512, fmt, ap);
+  va_end(ap);
+  return s;
+}
+
+#define CK(m, expr)                                                                              \
+  do {                                                                                           \
+    cudaError_t e_ = (expr);                                                                     \
+    if (e_ != cudaSuccess) {                                                                     \
+      return fail((m), SBKI_ERR_CUDA, "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_),   \
+                  __FILE__, __LINE__);                                                           \
+    }                                                                                            \
+  } while (0)
+
+// Restores the caller's current device when a call returns.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int ceil_log2(int64_t v) {
+  int b = 0;
+  while ((1ll << b) < v) ++b;
+  return b;
+}
+
+int64_t floor_div64(int64_t a, int64_t b) {
+  int64_t q = a / b;
+  if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
+  return q;
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  return cudaMalloc((void**)p, sizeof(T) * count);
+}
+
+__global__ void begin_kernel(DevCounters* dc, uint32_t epoch) {
+  dc->pairs = 0;
+  dc->touched_voxels = 0;
+  dc->n_free = 0;
+  dc->err = 0;
+  dc->n_valid = 0;
+  dc->n_items = 0;
+  dc->n_train = 0;
+  dc->n_tiles = 0;
+  dc->n_touched = 0;
+  dc->n_new = 0;
+  dc->n_huge = 0;
+  dc->n_mid = 0;
+  dc->work_next = 0;
+  dc->epoch = epoch;
+  dc->n_blocks_before = dc->n_blocks;
+}
+
+__global__ void bbox_init_kernel(int* bbox) {
+  if (threadIdx.x < 3) bbox[threadIdx.x] = INT_MAX;
+  else if (threadIdx.x < 6) bbox[threadIdx.x] = INT_MIN;
+}
+
+__global__ void set_items_kernel(DevCounters* dc, uint32_t n) { dc->n_items = n; }
+
+sbki_status check_params(const sbki_params* p) {
+  if (!p) return fail(nullptr, SBKI_ERR_INVALID_ARG, "params is NULL");
+  const double ds = p->ds_res > 0 ? p->ds_res : p->res;
+  if (!(p->res > 0) || !std::isfinite(p->res)) return fail(nullptr, SBKI_ERR_INVALID_ARG, "res must be > 0");
+  if (!(ds > 0) || !std::isfinite(ds)) return fail(nullptr, SBKI_ERR_INVALID_ARG, "ds_res must be > 0");
+  if (!(p->length_scale > 0)) return fail(nullptr, SBKI_ERR_INVALID_ARG, "length_scale must be > 0");
+  if (!(p->sigma0 >= 0) || !std::isfinite(p->sigma0)) return fail(nullptr, SBKI_ERR_INVALID_ARG, "sigma0 must be >= 0");
+  if (!(p->alpha0 > 0) || !std::isfinite(p->alpha0)) return fail(nullptr, SBKI_ERR_INVALID_ARG, "alpha0 must be > 0");
+  if (!(p->free_step > 0)) return fail(nullptr, SBKI_ERR_INVALID_ARG, "free_step must be > 0");
+  if (!(p->min_range >= 0) || !(p->max_range >= p->min_range) || !std::isfinite(p->max_range))
+    return fail(nullptr, SBKI_ERR_INVALID_ARG, "need 0 <= min_range <= max_range < inf");
+  if (p->num_classes < 1 || p->num_classes + 1 > kMaxClasses)
+    return fail(nullptr, SBKI_ERR_INVALID_ARG, "num_classes must be in 1..%d", kMaxClasses - 1);
+  if (p->block_edge != 4 && p->block_edge != 8)
+    return fail(nullptr, SBKI_ERR_INVALID_ARG, "block_edge must be 4 or 8");
+  if (p->length_scale > 0.75 * p->block_edge * p->res)
+    return fail(nullptr, SBKI_ERR_INVALID_ARG, "length_scale must be <= 0.75 * block_edge * res");
+  if (p->pool_blocks < 1 || p->pool_blocks > (1ll << 28))
+    return fail(nullptr, SBKI_ERR_INVALID_ARG, "pool_blocks must be in 1..2^28");
+  if (p->sample_capacity < 1 || p->sample_capacity > (1ll << 27))
+    return fail(nullptr, SBKI_ERR_INVALID_ARG, "sample_capacity must be in 1..2^27");
+  // tiles of training points overlapping one dilated block must stay few
+  const double span = p->block_edge * p->res + 2.0 * p->length_scale * 1.001 + 2.0 * ds;
+  const int per_axis = (int)std::ceil(span / (kTileEdge * ds)) + 1;
+  if (per_axis * per_axis * per_axis > 64)
+    return fail(nullptr, SBKI_ERR_INVALID_ARG, "ds_res too small relative to the block size and length scale");
+  // a scan's keys must fit in 64 bits
+  const int64_t half = (int64_t)std::ceil((p->max_range + 2.0 * ds) / (kTileEdge * ds)) + 2;
+  const int bits = ceil_log2(2 * half + 1);
+  if (3 * bits + kLocalBits + ceil_log2(p->num_classes + 1) > 64 || p->max_range / p->res > kKeyLimit / 4)
+    return fail(nullptr, SBKI_ERR_INVALID_ARG, "max_range too large for res/ds_res");
+  return SBKI_OK;
+}
+
+Geom make_geom(const sbki_params& p) {
+  Geom g;
+  const double ds = p.ds_res > 0 ? p.ds_res : p.res;
+  const double band = 2e-6;  // relative: the FP32 d^2 is within ~5e-7 (compensated offsets)
+  g.res = (float)p.res;
+  g.inv_res = (float)(1.0 / p.res);
+  g.res_lo = (float)(p.res - (double)g.res);
+  g.ds = (float)ds;
+  g.inv_ds = (float)(1.0 / ds);
+  g.l = (float)p.length_scale;
+  g.inv_l = (float)(1.0 / p.length_scale);
+  g.l2 = (float)(p.length_scale * p.length_scale);
+  g.l2_lo = (float)(p.length_scale * p.length_scale * (1.0 - band));
+  g.l2_hi = (float)(p.length_scale * p.length_scale * (1.0 + band));
+  g.sigma0 = (float)p.sigma0;
+  g.step = (float)p.free_step;
+  g.res64 = p.res;
+  g.l64 = p.length_scale;
+  g.l2_64 = p.length_scale * p.length_scale;
+  g.min_range = p.min_range;
+  g.max_range = p.max_range;
+  g.K1 = p.num_classes + 1;
+  g.B = p.block_edge;
+  g.B_shift = p.block_edge == 8 ? 3 : 2;
+  g.B3 = p.block_edge * p.block_edge * p.block_edge;
+  g.label_bits = std::max(1, ceil_log2(g.K1));
+  return g;
+}
+
+// Key frame of a scan: tiles relative to the sensor origin's tile.
+KeyFrame scan_frame(const MapState& m, const double T[16]) {
+  KeyFrame kf;
+  const double ds = m.prm.ds_res > 0 ? m.prm.ds_res : m.prm.res;
+  const int64_t half = (int64_t)std::ceil((m.prm.max_range + 2.0 * ds) / (kTileEdge * ds)) + 2;
+  kf.bits = ceil_log2(2 * half + 1);
+  for (int a = 0; a < 3; ++a) {
+    const float o = (float)T[4 * a + 3];
+    const float q = o * m.g.inv_ds;
+    const int64_t gcell = (int64_t)std::floor(q);
+    kf.org[a] = (int32_t)(floor_div64(gcell, kTileEdge) - half);
+  }
+  kf.total_bits = 3 * kf.bits + kLocalBits + m.g.label_bits;
+  return kf;
+}
+
+cudaError_t free_scratch_points(Scratch& s) {
+  cudaFree(s.pts);
+  cudaFree(s.labels);
+  cudaFree(s.world);
+  cudaFree(s.cnt);
+  s.pts = nullptr;
+  s.labels = nullptr;
+  s.world = nullptr;
+  s.cnt = nullptr;
+  s.n_cap = 0;
+  return cudaSuccess;
+}
+
+sbki_status ensure_point_capacity(MapState& m, int64_t n) {
+  Scratch& s = m.s;
+  if (n <= s.n_cap) return SBKI_OK;
+  CK(&m, cudaStreamSynchronize(m.stream));
+  free_scratch_points(s);
+  int64_t cap = std::max<int64_t>(n, 1 << 16);
+  CK(&m, dalloc(&s.pts, 3 * cap));
+  CK(&m, dalloc(&s.labels, cap));
+  CK(&m, dalloc(&s.world, cap));
+  CK(&m, dalloc(&s.cnt, cap + 1));
+  s.n_cap = cap;  // scan partials are sized at creation for 2^27 entries
+  return SBKI_OK;
+}
+
+sbki_status read_counters(MapState& m) {
+  CK(&m, cudaMemcpyAsync(m.hc, m.dc, sizeof(DevCounters), cudaMemcpyDeviceToHost, m.stream));
+  CK(&m, cudaStreamSynchronize(m.stream));
+  return SBKI_OK;
+}
+
+sbki_status status_from_device(MapState& m) {
+  const int e = m.hc->err;
+  if (e == 0) return SBKI_OK;
+  switch (e) {
+    case SBKI_ERR_LABEL_RANGE:
+      return fail(&m, SBKI_ERR_LABEL_RANGE, "a label is outside the allowed range; the map is unchanged");
+    case SBKI_ERR_CAPACITY:
+      return fail(&m, SBKI_ERR_CAPACITY,
+                  "capacity exceeded (samples %u of %lld, blocks %u+%u of %lld); the map is unchanged",
+                  m.hc->n_items, (long long)m.s.s_cap, m.hc->n_blocks, m.hc->n_new, (long long)m.pool_blocks);
+    case SBKI_ERR_TIMEOUT:
+      return fail(&m, SBKI_ERR_TIMEOUT, "a bounded device wait ran out");
+    default:
+      return fail(&m, (sbki_status)e, "device reported error %d", e);
+  }
+}
+
+void fill_stats(const MapState& m, int64_t n, sbki_stats* st) {
+  sbki_stats s{};
+  const DevCounters& c = *m.hc;
+  s.hits = c.n_valid;
+  s.dropped = n - (int64_t)c.n_valid;
+  s.free_samples = (int64_t)c.n_free;
+  s.train_points = c.n_train;
+  s.touched_blocks = c.n_touched;
+  s.new_blocks = c.err == 0 ? c.n_new : 0;
+  s.pairs = (int64_t)c.pairs;
+  s.touched_voxels = (int64_t)c.touched_voxels;
+  s.total_blocks = c.n_blocks;
+  if (st) *st = s;
+}
+
+// Steps a1-a3 on device; leaves the training set in s.train.  On return
+// *nitems holds the number of hits + free samples (0 on a pending error).
+sbki_status run_ingest(MapState& m, const float* points, const int32_t* labels, int64_t n, const double T[16],
+                       KeyFrame& kf, int64_t* nitems) {
+  *nitems = 0;
+  for (int i = 0; i < 16; ++i)
+    if (!std::isfinite(T[i])) return fail(&m, SBKI_ERR_INVALID_ARG, "sensor_pose has a non-finite entry");
+  for (int a = 0; a < 3; ++a) {
+    const double reach = std::fabs(T[4 * a + 3]) + m.prm.max_range;
+    if (reach / m.prm.res > (double)(kKeyLimit - 1024))
+      return fail(&m, SBKI_ERR_INVALID_ARG, "sensor origin too far from the map origin");
+  }
+  sbki_status st = ensure_point_capacity(m, n);
+  if (st != SBKI_OK) return st;
+  const float* dpts = points;
+  const int32_t* dlab = labels;
+  if (!is_device_ptr(points)) {
+    CK(&m, cudaMemcpyAsync(m.s.pts, points, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, m.stream));
+    dpts = m.s.pts;
+  }
+  if (!is_device_ptr(labels)) {
+    CK(&m, cudaMemcpyAsync(m.s.labels, labels, sizeof(int32_t) * n, cudaMemcpyHostToDevice, m.stream));
+    dlab = m.s.labels;
+  }
+  m.epoch += 1;
+  if (m.profiling) CK(&m, cudaEventRecord(m.ev[0], m.stream));
+  begin_kernel<<<1, 1, 0, m.stream>>>(m.dc, m.epoch);
+  m.launches += 1;
+  kf = scan_frame(m, T);
+  CK(&m, launch_transform_count(m, dpts, dlab, n, nullptr, T, kf));
+  st = read_counters(m);
+  if (st != SBKI_OK) return st;
+  if (m.hc->err != 0) return status_from_device(m);
+  *nitems = m.hc->n_items;
+  if (*nitems == 0) return SBKI_OK;
+  CK(&m, launch_emit(m, n, T, kf));
+  CK(&m, launch_downsample_n(m, kf, *nitems));
+  return SBKI_OK;
+}
+
+sbki_status run_update(MapState& m, const KeyFrame& kf, int64_t bound) {
+  if (m.profiling) CK(&m, cudaEventRecord(m.ev[1], m.stream));
+  CK(&m, launch_touch_blocks(m, kf, bound));
+  CK(&m, launch_commit_blocks(m));
+  if (m.acc_mode == 1) CK(&m, launch_bin_points(m, bound));
+  if (m.profiling) CK(&m, cudaEventRecord(m.ev[2], m.stream));
+  if (m.acc_mode == 1) CK(&m, launch_accumulate(m, kf));
+  else CK(&m, launch_accumulate_points(m));
+  if (m.profiling) CK(&m, cudaEventRecord(m.ev[3], m.stream));
+  return SBKI_OK;
+}
+
+// after a synchronising read: add the stage times of the update just finished
+void profile_collect(MapState& m) {
+  if (!m.profiling) return;
+  float t01 = 0.f, t12 = 0.f, t23 = 0.f;
+  if (cudaEventElapsedTime(&t01, m.ev[0], m.ev[1]) != cudaSuccess ||
+      cudaEventElapsedTime(&t12, m.ev[1], m.ev[2]) != cudaSuccess ||
+      cudaEventElapsedTime(&t23, m.ev[2], m.ev[3]) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  m.prof.inserts += 1;
+  m.prof.ingest_ms += t01;
+  m.prof.blocks_ms += t12;
+  m.prof.accumulate_ms += t23;
+}
+
+sbki_status insert_scan_impl(sbki_map* map, const float* points, const int32_t* labels, int64_t n,
+                             const double pose[16], bool sync_end, sbki_stats* stats) {
+  if (!map) return fail(nullptr, SBKI_ERR_INVALID_ARG, "map is NULL");
+  MapState& m = map->st;
+  if (n < 0 || (n > 0 && (!points || !labels)) || !pose)
+    return fail(&m, SBKI_ERR_INVALID_ARG, "need n >= 0, points/labels non-NULL for n > 0, pose non-NULL");
+  if (n > (1ll << 26)) return fail(&m, SBKI_ERR_INVALID_ARG, "n too large");
+  DeviceGuard dg(m.device);
+  if (n == 0) {
+    if (stats) {
+      *stats = sbki_stats{};
+      stats->total_blocks = m.host_blocks;
+    }
+    return SBKI_OK;
+  }
+  KeyFrame kf;
+  int64_t nitems = 0;
+  sbki_status st = run_ingest(m, points, labels, n, pose, kf, &nitems);
+  if (st != SBKI_OK) {
+    fill_stats(m, n, &m.last_stats);
+    if (stats) *stats = m.last_stats;
+    return st;
+  }
+  if (nitems > 0) {
+    st = run_update(m, kf, nitems);
+    if (st != SBKI_OK) return st;
+  }
+  if (!sync_end) return SBKI_OK;
+  st = read_counters(m);
+  if (st != SBKI_OK) return st;
+  if (nitems > 0 && m.hc->err == 0) profile_collect(m);
+  m.host_blocks = m.hc->n_blocks;
+  fill_stats(m, n, &m.last_stats);
+  if (stats) *stats = m.last_stats;
+  return status_from_device(m);
+}
+
+}  // namespace
+
+extern "C" {
+
+sbki_status sbki_default_params(sbki_params* p) {
+  if (!p) return SBKI_ERR_INVALID_ARG;
+  std::memset(p, 0, sizeof(*p));
+  p->res = 0.1;
+  p->length_scale = 0.3;
+  p->sigma0 = 0.1;
+  p->alpha0 = 0.001;
+  p->free_step = 0.3;
+  p->ds_res = 0.0;
+  p->min_range = 0.0;
+  p->max_range = 50.0;
+  p->free_thresh = 0.47;
+  p->occ_thresh = 0.6;
+  p->num_classes = 10;
+  p->block_edge = 8;
+  p->pool_blocks = 1 << 16;
+  p->sample_capacity = 1 << 24;
+  p->track_pairs = 0;
+  p->device = 0;
+  p->cuda_stream = nullptr;
+  return SBKI_OK;
+}
+
+sbki_status sbki_create_map(const sbki_params* params, sbki_map** out) {
+  if (!out) return fail(nullptr, SBKI_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  sbki_status st = check_params(params);
+  if (st != SBKI_OK) return st;
+  int ndev = 0;
+  cudaError_t ce = cudaGetDeviceCount(&ndev);
+  if (ce != cudaSuccess || params->device < 0 || params->device >= ndev)
+    return fail(nullptr, SBKI_ERR_CUDA, "no CUDA device %d (%s)", params->device,
+                ce != cudaSuccess ? cudaGetErrorString(ce) : "out of range");
+  sbki_map* map = new (std::nothrow) sbki_map();
+  if (!map) return fail(nullptr, SBKI_ERR_CAPACITY, "host allocation failed");
+  MapState& m = map->st;
+  m.prm = *params;
+  m.device = params->device;
+  m.stream = (cudaStream_t)params->cuda_stream;
+  m.g = make_geom(m.prm);
+  if (const char* am = getenv("SBKI_ACCUMULATE")) m.acc_mode = (strcmp(am, "blocks") == 0) ? 1 : 0;
+  DeviceGuard dg(m.device);
+  auto bail = [&](const char* what, cudaError_t e) {
+    snprintf(g_create_error, sizeof(g_create_error), "%s: %s", what, cudaGetErrorString(e));
+    sbki_destroy_map(map);
+    return SBKI_ERR_CUDA;
+  };
+  cudaDeviceProp prop;
+  if ((ce = cudaGetDeviceProperties(&prop, m.device)) != cudaSuccess) return bail("cudaGetDeviceProperties", ce);
+  m.sm_count = prop.multiProcessorCount;
+  m.pool_blocks = params->pool_blocks;
+  m.hash_cap = 1024;
+  while (m.hash_cap < 2 * m.pool_blocks) m.hash_cap <<= 1;
+  const size_t blk = (size_t)m.g.K1 * m.g.B3;
+  if ((ce = dalloc(&m.hkeys, m.hash_cap)) != cudaSuccess) return bail("hash keys", ce);
+  if ((ce = dalloc(&m.hvals, m.hash_cap)) != cudaSuccess) return bail("hash values", ce);
+  if ((ce = dalloc(&m.hmark, m.hash_cap)) != cudaSuccess) return bail("hash marks", ce);
+  if ((ce = dalloc(&m.hcnt, m.hash_cap)) != cudaSuccess) return bail("block point counts", ce);
+  if ((ce = dalloc(&m.hcur, m.hash_cap)) != cudaSuccess) return bail("block cursors", ce);
+  if ((ce = dalloc(&m.boff, m.hash_cap + 1)) != cudaSuccess) return bail("block offsets", ce);
+  m.list_cap = std::min<int64_t>(4 * params->sample_capacity, (1ll << 31) - 1);
+  if ((ce = dalloc(&m.blist, m.list_cap)) != cudaSuccess) return bail("block point lists", ce);
+  if ((ce = dalloc(&m.alpha, (size_t)m.pool_blocks * blk)) != cudaSuccess) return bail("alpha pool", ce);
+  if ((ce = dalloc(&m.pool_keys, m.pool_blocks)) != cudaSuccess) return bail("pool keys", ce);
+  if (params->track_pairs)
+    if ((ce = dalloc(&m.pairs, (size_t)m.pool_blocks * m.g.B3)) != cudaSuccess) return bail("pair counts", ce);
+  if ((ce = dalloc(&m.dc, 1)) != cudaSuccess) return bail("counters", ce);
+  if ((ce = cudaMallocHost((void**)&m.hc, sizeof(DevCounters))) != cudaSuccess) return bail("host counters", ce);
+  Scratch& s = m.s;
+  const int64_t S = params->sample_capacity;
+  s.s_cap = S;
+  if ((ce = dalloc(&s.items, S)) != cudaSuccess) return bail("items", ce);
+  if ((ce = dalloc(&s.keys, S)) != cudaSuccess) return bail("keys", ce);
+  if ((ce = dalloc(&s.keys2, S)) != cudaSuccess) return bail("keys2", ce);
+  if ((ce = dalloc(&s.vals, S)) != cudaSuccess) return bail("vals", ce);
+  if ((ce = dalloc(&s.vals2, S)) != cudaSuccess) return bail("vals2", ce);
+  if ((ce = dalloc(&s.flags, S + 1)) != cudaSuccess) return bail("flags", ce);
+  if ((ce = dalloc(&s.seg_start, S + 1)) != cudaSuccess) return bail("seg_start", ce);
+  if ((ce = dalloc(&s.train, S)) != cudaSuccess) return bail("train", ce);
+  if ((ce = dalloc(&s.tflags, S + 1)) != cudaSuccess) return bail("tflags", ce);
+  if ((ce = dalloc(&s.tile_key, S)) != cudaSuccess) return bail("tile keys", ce);
+  if ((ce = dalloc(&s.tile_start, S + 1)) != cudaSuccess) return bail("tile starts", ce);
+  s.hist_cap = radix_hist_entries(S);
+  if ((ce = dalloc(&s.hist, s.hist_cap)) != cudaSuccess) return bail("histogram", ce);
+  const int64_t scan_n = std::max<int64_t>(std::max<int64_t>(s.hist_cap, S + 1), (int64_t)1 << 27);
+  if ((ce = cudaMalloc(&s.scan_tmp, scan_tmp_bytes(scan_n))) != cudaSuccess) return bail("scan partials", ce);
+  if ((ce = dalloc(&s.touched, m.hash_cap)) != cudaSuccess) return bail("touched list", ce);
+  if ((ce = dalloc(&s.bbox, 8)) != cudaSuccess) return bail("bbox", ce);
+  if ((ce = dalloc(&s.huge, S / 1024 + 2)) != cudaSuccess) return bail("huge cells", ce);
+  if ((ce = dalloc(&s.mid, S / 16 + 2)) != cudaSuccess) return bail("long cells", ce);
+  if ((ce = dalloc(&s.fresh, m.hash_cap)) != cudaSuccess) return bail("fresh list", ce);
+  if ((ce = cudaMemsetAsync(m.hkeys, 0xff, sizeof(unsigned long long) * m.hash_cap, m.stream)) != cudaSuccess)
+    return bail("hash init", ce);
+  if ((ce = cudaMemsetAsync(m.hmark, 0, sizeof(uint32_t) * m.hash_cap, m.stream)) != cudaSuccess)
+    return bail("mark init", ce);
+  if ((ce = cudaMemsetAsync(m.hcnt, 0, sizeof(uint32_t) * m.hash_cap, m.stream)) != cudaSuccess)
+    return bail("count init", ce);
+  if ((ce = cudaMemsetAsync(m.dc, 0, sizeof(DevCounters), m.stream)) != cudaSuccess) return bail("counters init", ce);
+  for (int i = 0; i < 4; ++i)
+    if ((ce = cudaEventCreate(&m.ev[i])) != cudaSuccess) return bail("events", ce);
+  if ((ce = build_candidate_tables(m)) != cudaSuccess) return bail("candidate tables", ce);
+  if ((ce = cudaStreamSynchronize(m.stream)) != cudaSuccess) return bail("create sync", ce);
+  std::memset(m.hc, 0, sizeof(DevCounters));
+  *out = map;
+  return SBKI_OK;
+}
+
+void sbki_destroy_map(sbki_map* map) {
+  if (!map) return;
+  MapState& m = map->st;
+  {
+    DeviceGuard dg(m.device);
+    if (m.stream || m.dc) cudaStreamSynchronize(m.stream);
+    void* ptrs[] = {m.ctab, m.hkeys, m.hvals, m.hmark, m.hcnt, m.hcur, m.boff, m.blist, m.alpha, m.pool_keys, m.pairs, m.dc, m.s.items, m.s.keys, m.s.keys2,
+                    m.s.vals, m.s.vals2, m.s.flags, m.s.seg_start, m.s.train, m.s.tflags, m.s.tile_key,
+                    m.s.tile_start, m.s.hist, m.s.scan_tmp, m.s.touched, m.s.fresh, m.s.bbox, m.s.huge, m.s.mid};
+    for (void* p : ptrs)
+      if (p) cudaFree(p);
+    free_scratch_points(m.s);
+    if (m.hc) cudaFreeHost(m.hc);
+    for (int i = 0; i < 4; ++i)
+      if (m.ev[i]) cudaEventDestroy(m.ev[i]);
+  }
+  delete map;
+}
+
+sbki_status sbki_insert_scan(sbki_map* map, const float* points, const int32_t* labels, int64_t n,
+                             const double sensor_pose[16], sbki_stats* stats) {
+  return insert_scan_impl(map, points, labels, n, sensor_pose, true, stats);
+}
+
+sbki_status sbki_insert_scan_async(sbki_map* map, const float* points, const int32_t* labels, int64_t n,
+                                   const double sensor_pose[16]) {
+  return insert_scan_impl(map, points, labels, n, sensor_pose, false, nullptr);
+}
+
+sbki_status sbki_sync(sbki_map* map, sbki_stats* stats) {
+  if (!map) return fail(nullptr, SBKI_ERR_INVALID_ARG, "map is NULL");
+  MapState& m = map->st;
+  DeviceGuard dg(m.device);
+  sbki_status st = read_counters(m);
+  if (st != SBKI_OK) return st;
+  m.host_blocks = m.hc->n_blocks;
+  if (stats) {
+    sbki_stats s{};
+    const DevCounters& c = *m.hc;
+    s.hits = c.n_valid;
+    s.free_samples = (int64_t)c.n_free;
+    s.train_points = c.n_train;
+    s.touched_blocks = c.n_touched;
+    s.new_blocks = c.err == 0 ? c.n_new : 0;
+    s.pairs = (int64_t)c.pairs;
+    s.touched_voxels = (int64_t)c.touched_voxels;
+    s.total_blocks = c.n_blocks;
+    *stats = s;
+  }
+  return status_from_device(m);
+}
+
+sbki_status sbki_training_set(sbki_map* map, const float* points, const int32_t* labels, int64_t n,
+                              const double sensor_pose[16], float* xyzl_out, int64_t cap, int64_t* count) {
+  if (!map) return fail(nullptr, SBKI_ERR_INVALID_ARG, "map is NULL");
+  MapState& m = map->st;
+  if (n < 0 || (n > 0 && (!points || !labels)) || !sensor_pose || !count || cap < 0 || (cap > 0 && !xyzl_out))
+    return fail(&m, SBKI_ERR_INVALID_ARG, "bad arguments");
+  DeviceGuard dg(m.device);
+  *count = 0;
+  if (n == 0) return SBKI_OK;
+  KeyFrame kf;
+  int64_t nitems = 0;
+  sbki_status st = run_ingest(m, points, labels, n, sensor_pose, kf, &nitems);
+  if (st != SBKI_OK) return st;
+  st = read_counters(m);
+  if (st != SBKI_OK) return st;
+  if (m.hc->err != 0) return status_from_device(m);
+  const int64_t P = nitems > 0 ? m.hc->n_train : 0;
+  *count = P;
+  const int64_t c = std::min(P, cap);
+  if (c > 0) {
+    CK(&m, cudaMemcpyAsync(xyzl_out, m.s.train, sizeof(float4) * c, cudaMemcpyDefault, m.stream));
+    CK(&m, cudaStreamSynchronize(m.stream));
+  }
+  if (P > cap) return fail(&m, SBKI_ERR_CAPACITY, "training set has %lld points, cap %lld", (long long)P,
+                           (long long)cap);
+  return SBKI_OK;
+}
+
+sbki_status sbki_insert_training(sbki_map* map, const float* xyzl, int64_t p, sbki_stats* stats) {
+  if (!map) return fail(nullptr, SBKI_ERR_INVALID_ARG, "map is NULL");
+  MapState& m = map->st;
+  if (p < 0 || (p > 0 && !xyzl)) return fail(&m, SBKI_ERR_INVALID_ARG, "bad arguments");
+  if (p > m.s.s_cap) return fail(&m, SBKI_ERR_CAPACITY, "training set larger than sample_capacity");
+  DeviceGuard dg(m.device);
+  if (p == 0) {
+    if (stats) *stats = sbki_stats{};
+    return SBKI_OK;
+  }
+  const float4* din = reinterpret_cast<const float4*>(xyzl);
+  if (!is_device_ptr(xyzl)) {
+    CK(&m, cudaMemcpyAsync(m.s.items, xyzl, sizeof(float4) * p, cudaMemcpyHostToDevice, m.stream));
+    din = m.s.items;
+  } else if ((reinterpret_cast<uintptr_t>(xyzl) & 15u) != 0) {
+    CK(&m, cudaMemcpyAsync(m.s.items, xyzl, sizeof(float4) * p, cudaMemcpyDeviceToDevice, m.stream));
+    din = m.s.items;
+  }
+  m.epoch += 1;
+  if (m.profiling) CK(&m, cudaEventRecord(m.ev[0], m.stream));
+  begin_kernel<<<1, 1, 0, m.stream>>>(m.dc, m.epoch);
+  m.launches += 1;
+  int* bbox = m.s.bbox;
+  sbki_status st = SBKI_OK;
+  bbox_init_kernel<<<1, 32, 0, m.stream>>>(bbox);
+  m.launches += 1;
+  CK(&m, launch_train_bbox(m, din, p, bbox));
+  int hb[6];
+  CK(&m, cudaMemcpyAsync(hb, bbox, sizeof(hb), cudaMemcpyDeviceToHost, m.stream));
+  st = read_counters(m);
+  if (st != SBKI_OK) return st;
+  if (m.hc->err != 0) return status_from_device(m);
+  KeyFrame kf;
+  int64_t ext = 1;
+  for (int a = 0; a < 3; ++a) {
+    kf.org[a] = hb[a];
+    ext = std::max<int64_t>(ext, (int64_t)hb[3 + a] - hb[a] + 1);
+  }
+  kf.bits = std::max(1, ceil_log2(ext));
+  kf.total_bits = 3 * kf.bits + kLocalBits + m.g.label_bits;
+  if (kf.total_bits > 64) return fail(&m, SBKI_ERR_INVALID_ARG, "training set spans too large a region");
+  set_items_kernel<<<1, 1, 0, m.stream>>>(m.dc, (uint32_t)p);
+  m.launches += 1;
+  CK(&m, launch_train_prepare(m, din, p, kf));
+  st = run_update(m, kf, p);
+  if (st != SBKI_OK) return st;
+  st = read_counters(m);
+  if (st != SBKI_OK) return st;
+  if (m.hc->err == 0) profile_collect(m);
+  m.host_blocks = m.hc->n_blocks;
+  fill_stats(m, 0, &m.last_stats);
+  m.last_stats.hits = 0;
+  m.last_stats.dropped = 0;
+  m.last_stats.free_samples = 0;
+  if (stats) *stats = m.last_stats;
+  return status_from_device(m);
+}
+
+sbki_status sbki_query_probs(const sbki_map* cmap, const float* xyz, int64_t q, float* probs, float* var,
+                             float* mode, int32_t* label, float* p_occ, int32_t* state) {
+  if (!cmap) return fail(nullptr, SBKI_ERR_INVALID_ARG, "map is NULL");
+  sbki_map* map = const_cast<sbki_map*>(cmap);
+  MapState& m = map->st;
+  if (q < 0 || (q > 0 && (!xyz || !probs))) return fail(&m, SBKI_ERR_INVALID_ARG, "bad arguments");
+  if (q == 0) return SBKI_OK;
+  DeviceGuard dg(m.device);
+  const int K1 = m.g.K1;
+  const bool dev_all = is_device_ptr(xyz) && is_device_ptr(probs) && (!var || is_device_ptr(var)) &&
+                       (!mode || is_device_ptr(mode)) &&
+                       (!label || is_device_ptr(label)) && (!p_occ || is_device_ptr(p_occ)) &&
+                       (!state || is_device_ptr(state));
+  if (dev_all) {
+    CK(&m, launch_query(m, xyz, q, probs, var, mode, label, p_occ, state));
+    m.launches += 1;
+    CK(&m, cudaStreamSynchronize(m.stream));
+    return SBKI_OK;
+  }
+  // stage through device temporaries
+  float *dx = nullptr, *dp = nullptr, *dv = nullptr, *dm = nullptr, *dpo = nullptr;
+  int32_t *dl = nullptr, *ds = nullptr;
+  sbki_status rs = SBKI_OK;
+  cudaError_t e = cudaSuccess;
+  do {
+    if ((e = dalloc(&dx, 3 * q)) != cudaSuccess) break;
+    if ((e = dalloc(&dp, (size_t)K1 * q)) != cudaSuccess) break;
+    if (var && (e = dalloc(&dv, (size_t)K1 * q)) != cudaSuccess) break;
+    if (mode && (e = dalloc(&dm, (size_t)K1 * q)) != cudaSuccess) break;
+    if (label && (e = dalloc(&dl, q)) != cudaSuccess) break;
+    if (p_occ && (e = dalloc(&dpo, q)) != cudaSuccess) break;
+    if (state && (e = dalloc(&ds, q)) != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(dx, xyz, sizeof(float) * 3 * q, cudaMemcpyDefault, m.stream)) != cudaSuccess) break;
+    if ((e = launch_query(m, dx, q, dp, dv, dm, dl, dpo, ds)) != cudaSuccess) break;
+    m.launches += 1;
+    if ((e = cudaMemcpyAsync(probs, dp, sizeof(float) * K1 * q, cudaMemcpyDefault, m.stream)) != cudaSuccess) break;
+    if (var && (e = cudaMemcpyAsync(var, dv, sizeof(float) * K1 * q, cudaMemcpyDefault, m.stream)) != cudaSuccess)
+      break;
+    if (mode && (e = cudaMemcpyAsync(mode, dm, sizeof(float) * K1 * q, cudaMemcpyDefault, m.stream)) != cudaSuccess)
+      break;
+    if (label && (e = cudaMemcpyAsync(label, dl, sizeof(int32_t) * q, cudaMemcpyDefault, m.stream)) != cudaSuccess)
+      break;
+    if (p_occ && (e = cudaMemcpyAsync(p_occ, dpo, sizeof(float) * q, cudaMemcpyDefault, m.stream)) != cudaSuccess)
+      break;
+    if (state && (e = cudaMemcpyAsync(state, ds, sizeof(int32_t) * q, cudaMemcpyDefault, m.stream)) != cudaSuccess)
+      break;
+    e = cudaStreamSynchronize(m.stream);
+  } while (0);
+  if (e != cudaSuccess) rs = fail(&m, SBKI_ERR_CUDA, "query: %s", cudaGetErrorString(e));
+  cudaStreamSynchronize(m.stream);
+  void* tmp[] = {dx, dp, dv, dm, dl, dpo, ds};
+  for (void* t : tmp)
+    if (t) cudaFree(t);
+  return rs;
+}
+
+sbki_status sbki_voxel_count(const sbki_map* cmap, int64_t* count) {
+  if (!cmap || !count) return fail(nullptr, SBKI_ERR_INVALID_ARG, "bad arguments");
+  MapState& m = const_cast<sbki_map*>(cmap)->st;
+  DeviceGuard dg(m.device);
+  sbki_status st = read_counters(m);
+  if (st != SBKI_OK) return st;
+  *count = (int64_t)m.hc->n_blocks * m.g.B3;
+  return SBKI_OK;
+}
+
+sbki_status sbki_export(const sbki_map* cmap, int64_t* keys, float* alpha, int32_t* pairs, int64_t cap,
+                        int64_t* count) {
+  if (!cmap || !count) return fail(nullptr, SBKI_ERR_INVALID_ARG, "bad arguments");
+  MapState& m = const_cast<sbki_map*>(cmap)->st;
+  if (pairs && !m.pairs) return fail(&m, SBKI_ERR_INVALID_ARG, "pairs requested but track_pairs is off");
+  DeviceGuard dg(m.device);
+  sbki_status st = read_counters(m);
+  if (st != SBKI_OK) return st;
+  const int64_t nb = m.hc->n_blocks;
+  const int B = m.g.B, B3 = m.g.B3, K1 = m.g.K1;
+  *count = nb * B3;
+  if (!keys && !alpha && !pairs) return SBKI_OK;
+  if (cap < *count) return fail(&m, SBKI_ERR_CAPACITY, "export needs %lld rows, cap %lld", (long long)*count,
+                                (long long)cap);
+  std::vector<unsigned long long> bkeys((size_t)nb);
+  std::vector<float> a((size_t)nb * K1 * B3);
+  std::vector<int32_t> pc(m.pairs ? (size_t)nb * B3 : 0);
+  if (nb > 0) {
+    CK(&m, cudaMemcpyAsync(bkeys.data(), m.pool_keys, sizeof(unsigned long long) * nb, cudaMemcpyDeviceToHost,
+                           m.stream));
+    CK(&m, cudaMemcpyAsync(a.data(), m.alpha, sizeof(float) * a.size(), cudaMemcpyDeviceToHost, m.stream));
+    if (m.pairs)
+      CK(&m, cudaMemcpyAsync(pc.data(), m.pairs, sizeof(int32_t) * pc.size(), cudaMemcpyDeviceToHost, m.stream));
+    CK(&m, cudaStreamSynchronize(m.stream));
+  }
+  struct Row {
+    int32_t k[3];
+    int64_t src;  // pool block * B3 + local
+  };
+  std::vector<Row> rows((size_t)nb * B3);
+  for (int64_t b = 0; b < nb; ++b) {
+    int32_t bx, by, bz;
+    unpack_block(bkeys[(size_t)b], bx, by, bz);
+    for (int li = 0; li < B3; ++li) {
+      Row& r = rows[(size_t)(b * B3 + li)];
+      r.k[0] = bx * B + li % B;
+      r.k[1] = by * B + (li / B) % B;
+      r.k[2] = bz * B + li / (B * B);
+      r.src = b * B3 + li;
+    }
+  }
+  std::sort(rows.begin(), rows.end(), [](const Row& x, const Row& y) {
+    if (x.k[0] != y.k[0]) return x.k[0] < y.k[0];
+    if (x.k[1] != y.k[1]) return x.k[1] < y.k[1];
+    return x.k[2] < y.k[2];
+  });
+  const float a0 = (float)m.prm.alpha0;
+  for (size_t i = 0; i < rows.size(); ++i) {
+    const Row& r = rows[i];
+    if (keys)
+      for (int d = 0; d < 3; ++d) keys[3 * i + d] = r.k[d];
+    if (alpha) {
+      const int64_t b = r.src / B3, li = r.src % B3;
+      for (int k = 0; k < K1; ++k) alpha[i * K1 + k] = a0 + a[(size_t)((b * K1 + k) * B3 + li)];
+    }
+    if (pairs) pairs[i] = pc[(size_t)r.src];
+  }
+  return SBKI_OK;
+}
+
+sbki_status sbki_profile(sbki_map* map, int32_t enable, int32_t reset) {
+  if (!map) return fail(nullptr, SBKI_ERR_INVALID_ARG, "map is NULL");
+  map->st.profiling = enable != 0;
+  if (reset) {
+    const int64_t l = map->st.prof.launches;
+    map->st.prof = sbki_profile_data{};
+    map->st.prof.launches = l;
+  }
+  return SBKI_OK;
+}
+
+sbki_status sbki_profile_read(const sbki_map* map, sbki_profile_data* out) {
+  if (!map || !out) return fail(nullptr, SBKI_ERR_INVALID_ARG, "bad arguments");
+  *out = map->st.prof;
+  out->launches = map->st.launches;
+  return SBKI_OK;
+}
+
+const char* sbki_last_error(const sbki_map* map) { return map ? map->st.last_error : g_create_error; }
+
+const char* sbki_status_string(sbki_status s) {
+  switch (s) {
+    case SBKI_OK: return "ok";
+    case SBKI_ERR_INVALID_ARG: return "invalid argument";
+    case SBKI_ERR_LABEL_RANGE: return "label out of range";
+    case SBKI_ERR_CAPACITY: return "capacity exceeded";
+    case SBKI_ERR_CUDA: return "CUDA error";
+    case SBKI_ERR_TIMEOUT: return "device wait timed out";
+    case SBKI_ERR_NOT_FOUND: return "not found";
+  }
+  return "unknown status";
+}
+
+}  // extern "C"

@@ -1,0 +1,240 @@
+// Internal declarations shared by the CUDA translation units of libsbki.
+// Nothing here is part of the public C ABI (include/sbki.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sbki.h"
+
+namespace sbki {
+
+// ---------------------------------------------------------------- limits
+constexpr int kMaxClasses = 32;          // K+1 <= 32 (shared-memory alpha tile)
+constexpr int32_t kKeyLimit = 1 << 20;   // |voxel index| < kKeyLimit on every axis
+constexpr int kKeyBits = 21;             // bits per axis in a packed block key
+constexpr unsigned long long kEmpty = ~0ull;
+constexpr int kMaxProbes = 4096;         // hash probe bound (then SBKI_ERR_CAPACITY)
+constexpr int kTileShift = 3;            // training-point tiles are 8^3 ds cells
+constexpr int kTileEdge = 1 << kTileShift;
+constexpr int kLocalBits = 3 * kTileShift;
+
+// ---------------------------------------------------------------- device counters
+// One instance per map, in device memory; every kernel reads its sizes here so
+// that the per-scan sequence needs no host round trip.
+struct DevCounters {
+  unsigned long long pairs;           // in-support (voxel, point) pairs, this scan
+  unsigned long long touched_voxels;  // voxels with a nonzero increment, this scan
+  unsigned long long n_free;          // free samples, this scan
+  int32_t err;                        // first error (sbki_status), 0 = ok
+  uint32_t n_valid;                   // kept hits
+  uint32_t n_items;                   // hits + free samples
+  uint32_t n_train;                   // training points after downsampling
+  uint32_t n_tiles;                   // occupied training-point tiles
+  uint32_t n_touched;                 // touched blocks, this scan
+  uint32_t n_new;                     // blocks allocated by this scan
+  uint32_t n_blocks;                  // pool blocks in use (persistent)
+  uint32_t work_next;                 // accumulate work queue head
+  uint32_t epoch;                     // scan counter (touched marks)
+  uint32_t n_blocks_before;           // n_blocks when this scan started
+  uint32_t n_list;                    // (training point, touched block) pairs, this scan
+  uint32_t n_huge;                    // downsampling cells summed by a whole CTA, this scan
+  uint32_t n_mid;                     // downsampling cells summed by a warp, this scan
+};
+
+// ---------------------------------------------------------------- geometry constants
+// Every value that decides an integer (key, count, membership) is computed
+// with one fixed IEEE operation sequence (see the kernels); these are the
+// rounded constants those sequences use.
+struct Geom {
+  float res, inv_res;      // voxel edge and fp32(1/res)
+  float res_lo;            // fp32(res64 - res): res64 = res + res_lo to ~2^-48
+  float ds, inv_ds;        // downsampling cell edge and fp32(1/ds)
+  float l, inv_l, l2;      // length scale, 1/l, fp32(l*l)
+  float l2_lo, l2_hi;      // l2 (1 -/+ band): outside, the fp32 test decides
+  float sigma0;
+  float step;              // fp32(free_step)
+  double res64, l64, l2_64, min_range, max_range;
+  int K1;                  // classes incl. free
+  int B, B_shift, B3;      // block edge (power of two), log2, B^3
+  int label_bits;          // bits for a label in a sort key
+};
+
+// Per-scan key frame: training-point tiles are packed relative to an origin tile.
+struct KeyFrame {
+  int32_t org[3];   // origin tile (ds-tile index) minus half range
+  int bits;         // bits per axis of a relative tile index
+  int total_bits;   // bits of a full sort key
+};
+
+// ---------------------------------------------------------------- scratch of one map
+struct Scratch {
+  // per input point
+  float* pts = nullptr;           // staged host points [n_cap,3]
+  int32_t* labels = nullptr;      // staged host labels [n_cap]
+  float4* world = nullptr;        // [n_cap] world xyz + label bits
+  unsigned long long* cnt = nullptr;  // [n_cap+1] packed (valid<<40 | n_free), scanned in place
+  int64_t n_cap = 0;
+  // per item (hits + free samples)
+  float4* items = nullptr;        // [s_cap] xyz + label at source position
+  unsigned long long* keys = nullptr;   // [s_cap]
+  unsigned long long* keys2 = nullptr;  // [s_cap]
+  uint32_t* vals = nullptr;       // [s_cap] source positions
+  uint32_t* vals2 = nullptr;      // [s_cap]
+  uint32_t* flags = nullptr;      // [s_cap+1] segment heads, scanned
+  uint32_t* seg_start = nullptr;  // [s_cap+1]
+  float4* train = nullptr;        // [s_cap] training points (xyz, label bits), tile-sorted
+  uint32_t* tflags = nullptr;     // [s_cap+1] tile heads, scanned
+  unsigned long long* tile_key = nullptr;  // [s_cap] relative packed tile index
+  uint32_t* tile_start = nullptr; // [s_cap+1]
+  int64_t s_cap = 0;
+  // radix sort / scan temporaries
+  uint32_t* hist = nullptr;       // [256 * sort_ctas + 1]
+  void* scan_tmp = nullptr;       // partial sums
+  int64_t hist_cap = 0;
+  // per touched block
+  uint32_t* touched = nullptr;    // [hash_cap] hash slots touched this scan
+  uint32_t* fresh = nullptr;      // [hash_cap] hash slots created this scan
+  int* bbox = nullptr;            // [6] tile bounding box of a given training set
+  uint32_t* huge = nullptr;       // [s_cap / 1024 + 2] very long downsampling cells
+  uint32_t* mid = nullptr;        // [s_cap / 16 + 2] long downsampling cells
+};
+
+// ---------------------------------------------------------------- the map
+struct MapState {
+  sbki_params prm;
+  Geom g;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int sm_count = 0;
+  // block hash: key -> pool index
+  unsigned long long* hkeys = nullptr;  // [hash_cap]
+  int32_t* hvals = nullptr;             // [hash_cap]
+  uint32_t* hmark = nullptr;            // [hash_cap] epoch of last touch
+  uint32_t* hcnt = nullptr;             // [hash_cap] points touching the block (zero between scans)
+  uint32_t* hcur = nullptr;             // [hash_cap] fill cursor of the block's point list
+  int64_t hash_cap = 0;                 // power of two
+  uint32_t* boff = nullptr;             // [hash_cap + 1] per touched block: first entry in blist
+  uint32_t* blist = nullptr;            // [list_cap] training-point indices grouped by touched block
+  int64_t list_cap = 0;
+  // pool
+  float* alpha = nullptr;               // [pool_blocks][K1][B3] increments
+  unsigned long long* pool_keys = nullptr;  // [pool_blocks]
+  int32_t* pairs = nullptr;             // [pool_blocks][B3] (only if track_pairs)
+  int64_t pool_blocks = 0;
+  DevCounters* dc = nullptr;            // device counters
+  DevCounters* hc = nullptr;            // pinned host mirror
+  Scratch s;
+  uint32_t epoch = 0;
+  uint32_t host_blocks = 0;             // last known n_blocks (host view)
+  sbki_status sticky = SBKI_OK;
+  int64_t launches = 0;                 // kernels launched on this map
+  int acc_mode = 0;                     // 0: point-major (global reductions), 1: block-major (shared tile)
+  int32_t* ctab = nullptr;              // point-major candidate lists [27][ctab_pad]
+  int ctab_pad = 0, ctab_R = 0;
+  bool profiling = false;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  sbki_profile_data prof{};
+  char last_error[512] = {0};
+  sbki_stats last_stats{};
+};
+
+// ---------------------------------------------------------------- device helpers
+__host__ __device__ inline unsigned long long pack_block(int32_t bx, int32_t by, int32_t bz) {
+  const unsigned long long off = 1ull << (kKeyBits - 1);
+  return (((unsigned long long)(bx + (int64_t)off)) << (2 * kKeyBits)) |
+         (((unsigned long long)(by + (int64_t)off)) << kKeyBits) | ((unsigned long long)(bz + (int64_t)off));
+}
+__host__ __device__ inline void unpack_block(unsigned long long k, int32_t& bx, int32_t& by, int32_t& bz) {
+  const int64_t off = 1ll << (kKeyBits - 1);
+  const unsigned long long m = (1ull << kKeyBits) - 1;
+  bx = (int32_t)((int64_t)((k >> (2 * kKeyBits)) & m) - off);
+  by = (int32_t)((int64_t)((k >> kKeyBits) & m) - off);
+  bz = (int32_t)((int64_t)(k & m) - off);
+}
+__device__ __forceinline__ uint32_t hash_slot(unsigned long long k, int64_t cap) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  k *= 0xc4ceb9fe1a85ec53ull;
+  k ^= k >> 33;
+  return (uint32_t)(k & (unsigned long long)(cap - 1));
+}
+__device__ __forceinline__ void set_error(DevCounters* dc, int code) { atomicCAS(&dc->err, 0, code); }
+
+// x / n for 0 <= x < 4096 and 1 <= n <= 32, as a multiply and a shift by a
+// reciprocal m = ceil(2^20 / n) (exact over that range; checked exhaustively)
+__device__ __forceinline__ uint32_t small_recip(uint32_t n) { return ((1u << 20) + n - 1u) / n; }
+__device__ __forceinline__ uint32_t small_div(uint32_t x, uint32_t m) { return (x * m) >> 20; }
+
+// ---------------------------------------------------------------- compensated offsets
+// Membership d^2 < l^2 is decided in FP32 from offsets e = c_v - x formed to
+// about one ulp: for a reference voxel index K the offset of its centre,
+// E0 = (K + 1/2) res64 - x, is held as an unevaluated sum hi + lo (the product
+// through an exact FMA residual, the difference through an exact two-sum),
+// and e(K + d) = E0 + d res64 is rounded once more.  d^2 from such offsets is
+// within ~5e-7 relative of the exact value, so a pair whose FP32 d^2 lies in
+// the relative band [l2_lo, l2_hi] = l^2 (1 -/+ 2e-6) is re-decided in FP64
+// exactly as the plain definition states: c = (v + 0.5)*res64, e = c - x,
+// d^2 = (ex^2 + ey^2) + ez^2 < l^2.  Round-to-nearest intrinsics keep the
+// compiler from contracting or reordering any of it.
+__device__ __forceinline__ void centre_offset0(int K, float x, const Geom& g, float& hi, float& lo) {
+  const float c0 = (float)K + 0.5f;  // exact: |K| < 2^22
+  const float p_hi = __fmul_rn(c0, g.res);
+  const float p_lo = __fmaf_rn(c0, g.res_lo, __fmaf_rn(c0, g.res, -p_hi));
+  const float s = __fsub_rn(p_hi, x);
+  const float bb = __fsub_rn(s, p_hi);
+  const float err = __fadd_rn(__fsub_rn(p_hi, __fsub_rn(s, bb)), __fsub_rn(-x, bb));
+  hi = s;
+  lo = __fadd_rn(err, p_lo);
+}
+// c_{K+d} - x = E0 + d res, rounded once (d a small integer)
+__device__ __forceinline__ float centre_offset_at(int d, float hi, float lo, const Geom& g) {
+  const float fd = (float)d;
+  return __fadd_rn(__fmaf_rn(fd, g.res, hi), __fmaf_rn(fd, g.res_lo, lo));
+}
+__device__ __forceinline__ bool in_support64(int vx, int vy, int vz, float x, float y, float z, const Geom& g) {
+  const double ex = __dsub_rn(__dmul_rn(__dadd_rn((double)vx, 0.5), g.res64), (double)x);
+  const double ey = __dsub_rn(__dmul_rn(__dadd_rn((double)vy, 0.5), g.res64), (double)y);
+  const double ez = __dsub_rn(__dmul_rn(__dadd_rn((double)vz, 0.5), g.res64), (double)z);
+  const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
+  return d2 < g.l2_64;
+}
+
+// ---------------------------------------------------------------- launchers (one per .cu)
+// scan.cu: exclusive prefix sums in place over n+1 entries (entry n receives the total)
+cudaError_t exclusive_scan_u32(uint32_t* data, int64_t n, void* tmp, cudaStream_t st);
+cudaError_t exclusive_scan_u64(unsigned long long* data, int64_t n, void* tmp, cudaStream_t st);
+int64_t scan_tmp_bytes(int64_t n);
+
+// radix_sort.cu: stable LSD sort of (keys, vals) over bits [0, bits); count read
+// from *n_dev; capacity cap bounds the launch; result in (keys, vals).
+cudaError_t radix_sort_pairs(unsigned long long* keys, uint32_t* vals, unsigned long long* keys_alt,
+                             uint32_t* vals_alt, const uint32_t* n_dev, int64_t cap, int bits, uint32_t* hist,
+                             void* scan_tmp, DevCounters* dc, cudaStream_t st);
+int64_t radix_hist_entries(int64_t cap);
+
+// ingest.cu
+cudaError_t launch_transform_count(MapState& m, const float* pts, const int32_t* labels, int64_t n,
+                                   const double* pose_dev_or_null, const double pose[16], const KeyFrame& kf);
+cudaError_t launch_emit(MapState& m, int64_t n, const double pose[16], const KeyFrame& kf);
+cudaError_t launch_downsample_n(MapState& m, const KeyFrame& kf, int64_t nitems);
+cudaError_t launch_train_bbox(MapState& m, const float4* in, int64_t p, int* bbox_dev);
+cudaError_t launch_train_prepare(MapState& m, const float4* in, int64_t p, const KeyFrame& kf);
+
+// blocks.cu
+cudaError_t launch_touch_blocks(MapState& m, const KeyFrame& kf, int64_t bound);
+cudaError_t launch_commit_blocks(MapState& m);
+cudaError_t launch_bin_points(MapState& m, int64_t bound);
+
+// accumulate.cu
+cudaError_t launch_accumulate(MapState& m, const KeyFrame& kf);
+cudaError_t launch_accumulate_points(MapState& m);
+cudaError_t build_candidate_tables(MapState& m);
+size_t accumulate_smem_bytes(const Geom& g);
+
+// readoff.cu
+cudaError_t launch_query(const MapState& m, const float* xyz, int64_t q, float* probs, float* var, float* mode,
+                         int32_t* label, float* p_occ, int32_t* state);
+cudaError_t launch_gather_alpha(const MapState& m, float* out, int64_t nblocks);
+
+}  // namespace sbki

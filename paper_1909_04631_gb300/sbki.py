@@ -1,0 +1,299 @@
+"""Thin ctypes binding of libsbki (include/sbki.h).
+
+Argument marshalling only: every step of the map update runs in the CUDA
+kernels of libsbki.so.  Arrays may be numpy arrays (host memory) or torch
+tensors (host or CUDA); CUDA tensors are passed by device pointer and used in
+stream order on the map's stream.  There is no CPU fallback: if the library
+is missing or no GPU is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+OK, ERR_INVALID_ARG, ERR_LABEL_RANGE, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, ERR_NOT_FOUND = range(7)
+STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "label out of range", 3: "capacity exceeded", 4: "CUDA error",
+                5: "device wait timed out", 6: "not found"}
+
+EXPORTED = ["sbki_default_params", "sbki_create_map", "sbki_destroy_map", "sbki_insert_scan",
+            "sbki_insert_scan_async", "sbki_sync", "sbki_training_set", "sbki_insert_training", "sbki_query_probs",
+            "sbki_voxel_count", "sbki_export", "sbki_profile", "sbki_profile_read", "sbki_kernel_values", "sbki_last_error", "sbki_status_string"]
+
+
+class SbkiError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), message))
+        self.status = status
+
+
+class Params(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("res", "length_scale", "sigma0", "alpha0", "free_step", "ds_res",
+                                          "min_range", "max_range", "free_thresh", "occ_thresh")] + \
+               [("num_classes", C.c_int32), ("block_edge", C.c_int32), ("pool_blocks", C.c_int64),
+                ("sample_capacity", C.c_int64), ("track_pairs", C.c_int32), ("device", C.c_int32),
+                ("cuda_stream", C.c_void_p)]
+
+
+class ProfileData(C.Structure):
+    _fields_ = [("inserts", C.c_int64), ("launches", C.c_int64), ("ingest_ms", C.c_double),
+                ("blocks_ms", C.c_double), ("accumulate_ms", C.c_double)]
+
+    def as_dict(self):
+        return {n: (float(getattr(self, n)) if n.endswith("_ms") else int(getattr(self, n))) for n, _ in self._fields_}
+
+
+class Stats(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in ("hits", "dropped", "free_samples", "train_points", "touched_blocks",
+                                         "new_blocks", "pairs", "touched_voxels", "total_blocks")]
+
+    def as_dict(self):
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libsbki.so (building it first if it is missing and nvcc exists)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_build.LIB):
+            if not build_if_missing:
+                raise RuntimeError("libsbki.so is not built; run paper_1909_04631_gb300.build.build()")
+            _build.build()
+        L = C.CDLL(_build.LIB)
+        vp, i64, i32 = C.c_void_p, C.c_int64, C.c_int32
+        P = C.POINTER
+        L.sbki_default_params.argtypes = [P(Params)]
+        L.sbki_create_map.argtypes = [P(Params), P(vp)]
+        L.sbki_destroy_map.argtypes = [vp]
+        L.sbki_destroy_map.restype = None
+        L.sbki_insert_scan.argtypes = [vp, vp, vp, i64, vp, P(Stats)]
+        L.sbki_insert_scan_async.argtypes = [vp, vp, vp, i64, vp]
+        L.sbki_sync.argtypes = [vp, P(Stats)]
+        L.sbki_training_set.argtypes = [vp, vp, vp, i64, vp, vp, i64, P(i64)]
+        L.sbki_insert_training.argtypes = [vp, vp, i64, P(Stats)]
+        L.sbki_query_probs.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp]
+        L.sbki_voxel_count.argtypes = [vp, P(i64)]
+        L.sbki_export.argtypes = [vp, vp, vp, vp, i64, P(i64)]
+        L.sbki_last_error.argtypes = [vp]
+        L.sbki_last_error.restype = C.c_char_p
+        L.sbki_profile.argtypes = [vp, i32, i32]
+        L.sbki_profile.restype = C.c_int
+        L.sbki_profile_read.argtypes = [vp, P(ProfileData)]
+        L.sbki_profile_read.restype = C.c_int
+        L.sbki_kernel_values.argtypes = [vp, i64, vp, i32, vp]
+        L.sbki_kernel_values.restype = C.c_int
+        L.sbki_status_string.argtypes = [C.c_int]
+        L.sbki_status_string.restype = C.c_char_p
+        for f in ("sbki_default_params", "sbki_create_map", "sbki_insert_scan", "sbki_insert_scan_async", "sbki_sync",
+                  "sbki_training_set", "sbki_insert_training", "sbki_query_probs", "sbki_voxel_count",
+                  "sbki_export"):
+            getattr(L, f).restype = C.c_int
+        _lib = L
+        return L
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    load().sbki_default_params(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise TypeError("unknown parameter %r" % k)
+        setattr(p, k, v)
+    return p
+
+
+def kernel_values(r, method=0):
+    """f(r) of Eq. (kernel) on the GPU (method 0: update form, 1: trigonometric form)."""
+    import torch
+    rt = torch.as_tensor(r, dtype=torch.float32).cuda().contiguous()
+    out = torch.empty_like(rt)
+    st = load().sbki_kernel_values(C.c_void_p(rt.data_ptr()), rt.numel(), C.c_void_p(out.data_ptr()), int(method),
+                                   C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if st != OK:
+        raise SbkiError(st, "sbki_kernel_values failed")
+    return out.cpu().numpy()
+
+
+def _ptr(x):
+    """(pointer, keepalive) for a numpy array or torch tensor (contiguous)."""
+    if x is None:
+        return None, None
+    if hasattr(x, "data_ptr"):  # torch tensor
+        if not x.is_contiguous():
+            x = x.contiguous()
+        return C.c_void_p(x.data_ptr()), x
+    a = np.ascontiguousarray(x)
+    return a.ctypes.data_as(C.c_void_p), a
+
+
+def _as(x, dtype, shape_tail=None):
+    if hasattr(x, "data_ptr"):
+        import torch
+        tdt = {np.float32: torch.float32, np.int32: torch.int32, np.float64: torch.float64}[dtype]
+        if x.dtype != tdt:
+            x = x.to(tdt)
+        return x.contiguous()
+    a = np.ascontiguousarray(x, dtype=dtype)
+    if shape_tail is not None:
+        a = a.reshape(-1, shape_tail)
+    return a
+
+
+class Map:
+    """A semantic S-BKI map on one GPU (owner of its device pool and hash)."""
+
+    def __init__(self, params: Params | None = None, stream=None, **kw):
+        L = load()
+        self.params = params if params is not None else default_params(**kw)
+        if params is not None and kw:
+            for k, v in kw.items():
+                setattr(self.params, k, v)
+        if stream is not None:
+            self.params.cuda_stream = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        self.K1 = self.params.num_classes + 1
+        h = C.c_void_p()
+        st = L.sbki_create_map(C.byref(self.params), C.byref(h))
+        if st != OK:
+            raise SbkiError(st, L.sbki_last_error(None).decode())
+        self._h = h
+        self._L = L
+
+    def close(self):
+        h, self._h = getattr(self, "_h", None), None
+        if h:
+            self._L.sbki_destroy_map(h)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _check(self, st):
+        if st != OK:
+            raise SbkiError(st, self._L.sbki_last_error(self._h).decode())
+
+    # ----------------------------------------------------------- updates
+    def insert_scan(self, points, labels, pose, sync=True):
+        pts = _as(points, np.float32, 3)
+        lab = _as(labels, np.int32)
+        T = np.ascontiguousarray(pose, dtype=np.float64).reshape(16)
+        pp, k1 = _ptr(pts)
+        lp, k2 = _ptr(lab)
+        n = pts.shape[0] if hasattr(pts, "shape") else len(pts)
+        if sync:
+            s = Stats()
+            self._check(self._L.sbki_insert_scan(self._h, pp, lp, n, T.ctypes.data_as(C.c_void_p), C.byref(s)))
+            return s.as_dict()
+        self._check(self._L.sbki_insert_scan_async(self._h, pp, lp, n, T.ctypes.data_as(C.c_void_p)))
+        self._keep = (k1, k2, T)
+        return None
+
+    def sync(self):
+        s = Stats()
+        self._check(self._L.sbki_sync(self._h, C.byref(s)))
+        return s.as_dict()
+
+    def training_set(self, points, labels, pose, cap=None):
+        """(xyz float32 [P,3], labels int32 [P]) of a scan (steps a1-a3), host arrays."""
+        pts = _as(points, np.float32, 3)
+        lab = _as(labels, np.int32)
+        T = np.ascontiguousarray(pose, dtype=np.float64).reshape(16)
+        pp, k1 = _ptr(pts)
+        lp, k2 = _ptr(lab)
+        n = pts.shape[0]
+        cnt = C.c_int64()
+        if cap is None:
+            cap = int(self.params.sample_capacity)
+        out = np.empty((max(cap, 1), 4), np.float32)
+        self._check(self._L.sbki_training_set(self._h, pp, lp, n, T.ctypes.data_as(C.c_void_p),
+                                              out.ctypes.data_as(C.c_void_p), cap, C.byref(cnt)))
+        P = cnt.value
+        return out[:P, :3].copy(), out[:P, 3].astype(np.int32)
+
+    def insert_training(self, xyz, labels):
+        """Eq. (alpha_kernel) for a given training set (world xyz, labels 0..K)."""
+        if hasattr(xyz, "data_ptr"):
+            import torch
+            xyzl = torch.cat([xyz.float().reshape(-1, 3), labels.reshape(-1, 1).float()], 1).contiguous()
+        else:
+            xyzl = np.concatenate([np.asarray(xyz, np.float32).reshape(-1, 3),
+                                   np.asarray(labels, np.float32).reshape(-1, 1)], 1)
+            xyzl = np.ascontiguousarray(xyzl, np.float32)
+        p, keep = _ptr(xyzl)
+        s = Stats()
+        self._check(self._L.sbki_insert_training(self._h, p, xyzl.shape[0], C.byref(s)))
+        return s.as_dict()
+
+    # ----------------------------------------------------------- read-off
+    def query(self, xyz, var=True, mode=True, label=True, p_occ=True, state=True):
+        """Read-off at world points (host arrays out): dict(probs, var, mode, label, p_occ, state)."""
+        x = np.ascontiguousarray(xyz, np.float32).reshape(-1, 3)
+        q = len(x)
+        out = dict(probs=np.empty((q, self.K1), np.float32))
+        if var:
+            out["var"] = np.empty((q, self.K1), np.float32)
+        if mode:
+            out["mode"] = np.empty((q, self.K1), np.float32)
+        if label:
+            out["label"] = np.empty(q, np.int32)
+        if p_occ:
+            out["p_occ"] = np.empty(q, np.float32)
+        if state:
+            out["state"] = np.empty(q, np.int32)
+        g = lambda k: out[k].ctypes.data_as(C.c_void_p) if k in out else None  # noqa: E731
+        self._check(self._L.sbki_query_probs(self._h, x.ctypes.data_as(C.c_void_p), q, g("probs"), g("var"),
+                                             g("mode"), g("label"), g("p_occ"), g("state")))
+        return out
+
+    def query_device(self, xyz, probs, var=None, mode=None, label=None, p_occ=None, state=None):
+        """Read-off with caller-owned (e.g. torch CUDA) buffers."""
+        ptrs = [_ptr(a) for a in (xyz, probs, var, mode, label, p_occ, state)]
+        q = xyz.shape[0]
+        self._check(self._L.sbki_query_probs(self._h, *[p for p, _ in ptrs[:1]], q, *[p for p, _ in ptrs[1:]]))
+
+    def profile(self, enable=True, reset=True):
+        """Turn per-stage CUDA-event timing on/off (and reset the totals)."""
+        self._check(self._L.sbki_profile(self._h, int(enable), int(reset)))
+
+    def profile_read(self):
+        d = ProfileData()
+        self._check(self._L.sbki_profile_read(self._h, C.byref(d)))
+        return d.as_dict()
+
+    def voxel_count(self):
+        c = C.c_int64()
+        self._check(self._L.sbki_voxel_count(self._h, C.byref(c)))
+        return c.value
+
+    def export(self, pairs=False):
+        """(keys int64 [n,3], alpha float32 [n,K+1], pairs int32 [n] or None), sorted by key."""
+        n = self.voxel_count()
+        keys = np.empty((max(n, 1), 3), np.int64)
+        alpha = np.empty((max(n, 1), self.K1), np.float32)
+        pc = np.empty(max(n, 1), np.int32) if pairs else None
+        cnt = C.c_int64()
+        self._check(self._L.sbki_export(self._h, keys.ctypes.data_as(C.c_void_p), alpha.ctypes.data_as(C.c_void_p),
+                                        pc.ctypes.data_as(C.c_void_p) if pairs else None, n, C.byref(cnt)))
+        n = cnt.value
+        return keys[:n], alpha[:n], (pc[:n] if pairs else None)

@@ -1,0 +1,67 @@
+"""The C-ABI library loads and exports every symbol include/sbki.h declares
+(no compute calls: these run without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "sbki.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(sbki_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for f in ("sbki_create_map", "sbki_insert_scan", "sbki_query_probs", "sbki_export", "sbki_destroy_map"):
+        assert f in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1909_04631_gb300 import build, sbki
+    if not os.path.exists(build.LIB):
+        try:
+            build.build()
+        except RuntimeError as e:  # no nvcc on this machine
+            pytest.skip(str(e))
+    lib = ctypes.CDLL(build.LIB)
+    for name in _declared():
+        assert hasattr(lib, name), name
+    assert sorted(sbki.EXPORTED) == _declared()
+
+
+def test_status_strings_without_gpu():
+    from paper_1909_04631_gb300 import sbki
+    L = sbki.load()
+    for code, text in sbki.STATUS_NAMES.items():
+        assert L.sbki_status_string(code).decode() == text
+
+
+def test_params_struct_matches_header_defaults():
+    from paper_1909_04631_gb300 import sbki
+    p = sbki.default_params()
+    assert (p.length_scale, p.sigma0, p.alpha0, p.res, p.free_thresh, p.occ_thresh) == (0.3, 0.1, 0.001, 0.1, 0.47,
+                                                                                      0.6)
+    assert ctypes.sizeof(sbki.Params) == 10 * 8 + 4 + 4 + 8 + 8 + 4 + 4 + 8
+
+
+def test_create_map_fails_loudly_without_gpu():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1909_04631_gb300 import sbki
+    with pytest.raises(sbki.SbkiError):
+        sbki.Map(sbki.default_params())
+
+
+def test_create_map_rejects_bad_params():
+    from paper_1909_04631_gb300 import sbki
+    for bad in (dict(res=0.0), dict(block_edge=6), dict(num_classes=40), dict(max_range=float("inf")),
+                dict(length_scale=5.0), dict(alpha0=0.0)):
+        with pytest.raises(sbki.SbkiError) as e:
+            sbki.Map(sbki.default_params(**bad))
+        assert e.value.status == sbki.ERR_INVALID_ARG

@@ -425,3 +425,42 @@ def test_small_scan_training_set_invariants(orc):
     assert len(inside & distinct) >= len(xyz) - 2
     with pytest.raises(ValueError):
         orc.training_set(p, sc["points"][:3], np.array([1, 11, 2]), sc["pose"])
+
+
+def _f32_round_fraction(fr):
+    """Nearest FP32 to a Fraction, ties to even (exact rational comparisons)."""
+    from fractions import Fraction
+    if fr == 0:
+        return 0.0
+    x = np.float32(float(fr))  # within an ulp or two of the answer
+    cands = {x, np.nextafter(x, np.float32(np.inf)), np.nextafter(x, np.float32(-np.inf))}
+    cands |= {np.nextafter(c, np.float32(np.inf)) for c in list(cands)} | \
+        {np.nextafter(c, np.float32(-np.inf)) for c in list(cands)}
+    best = min(cands, key=lambda c: (abs(Fraction(float(c)) - fr),
+                                     int(np.frombuffer(np.float32(c).tobytes(), np.uint32)[0]) & 1))
+    return float(best)
+
+
+def test_exact_mean_against_rational_arithmetic(orc):
+    """Reading K4 (centroid = exact mean rounded once to FP32) against Python
+    Fractions: same-sign cells, mixed magnitudes over many binades, near-ties,
+    subnormals and long segments."""
+    from fractions import Fraction
+    rng = np.random.default_rng(31)
+    cases = []
+    for _ in range(300):
+        n = int(rng.integers(1, 40))
+        base = rng.uniform(-50, 50)
+        cases.append((base + rng.uniform(0, 0.1, size=n)).astype(np.float32))
+    for _ in range(100):  # a cell next to a coordinate plane: values spanning many binades
+        n = int(rng.integers(2, 300))
+        cases.append((rng.uniform(0, 0.1, size=n) * 10.0 ** rng.integers(-30, 0, size=n)).astype(np.float32))
+    for _ in range(50):  # exact halfway cases: two neighbouring floats
+        a = np.float32(rng.uniform(1, 2))
+        cases.append(np.array([a, np.nextafter(a, np.float32(3))], np.float32))
+    cases.append(np.array([1e-45, 3e-45, 1e-44], np.float32))  # subnormals
+    cases.append(np.full(5000, np.float32(0.1)) + rng.uniform(0, 1e-3, 5000).astype(np.float32))
+    cases.append(-np.abs(rng.normal(size=17)).astype(np.float32))
+    for v in cases:
+        exact = sum(Fraction(float(x)) for x in v) / len(v)
+        assert orc.exact_mean_f32(v) == _f32_round_fraction(exact), v[:4]
