@@ -116,6 +116,35 @@ sbki_status sbki_sync(sbki_map* map, sbki_stats* stats);
 sbki_status sbki_training_set(sbki_map* map, const float* points, const int32_t* labels, int64_t n,
                               const double sensor_pose[16], float* xyzl_out, int64_t cap, int64_t* count);
 
+/* The training set of one scan (steps a1-a3, same result as
+ * sbki_training_set) with no device allocation and no map.  The paper has no
+ * counterpart: this is a deployment variant for callers that cannot allocate
+ * device memory while they run - a real-time mapping loop that reserves all of
+ * its memory at start-up, a framework that owns the device heap through its
+ * own pool allocator, or code recorded into a CUDA graph, where cudaMalloc and
+ * cudaFree are not allowed and may synchronise the device.
+ *   params: as for sbki_create_map (pool_blocks, sample_capacity and
+ *     track_pairs are ignored); work runs on params->device and, in stream
+ *     order, on params->cuda_stream; the call synchronises that stream.
+ *   points [n,3] float32 and labels [n] int32 (1..K): DEVICE memory of
+ *     params->device; xyzl_out [cap,4] float32: DEVICE memory, written as for
+ *     sbki_training_set; *count (host) receives the number of points.
+ * Every intermediate buffer lives in one fixed device array of about 9.4 MB
+ * that each GPU loading the library holds until the process exits; nothing
+ * is allocated per call (no cudaMalloc, cudaFree or allocating library call).
+ * Limits: n <= 16384 points (else SBKI_ERR_INVALID_ARG before any GPU work)
+ * and at most 131072 hits + free samples (else SBKI_ERR_CAPACITY after the
+ * counting step); count > cap writes cap points and returns SBKI_ERR_CAPACITY.
+ * All calls share the array and it keeps the last call's contents (its
+ * counters are cleared at the start of each call): calls that overlap on the
+ * GPU - other streams, other host threads - race and must be serialised.
+ * The first call on a device looks up the array's device address with that
+ * device current; make it before any stream capture.  Errors are reported by
+ * sbki_last_error(NULL). */
+sbki_status sbki_training_set_noalloc(const sbki_params* params, const float* points, const int32_t* labels,
+                                      int64_t n, const double sensor_pose[16], float* xyzl_out, int64_t cap,
+                                      int64_t* count);
+
 /* Eq. (alpha_kernel) for a given training set (no sampling or downsampling):
  * xyzl [p,4] float32 world (x, y, z, label as float) with labels 0..K. */
 sbki_status sbki_insert_training(sbki_map* map, const float* xyzl, int64_t p, sbki_stats* stats);

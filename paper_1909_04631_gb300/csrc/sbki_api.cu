@@ -360,6 +360,14 @@ sbki_status insert_scan_impl(sbki_map* map, const float* points, const int32_t* 
 
 }  // namespace
 
+namespace sbki {
+// Shared with entry points defined in other translation units.
+sbki_status validate_params(const sbki_params* p) { return check_params(p); }
+Geom geometry_of(const sbki_params& p) { return make_geom(p); }
+KeyFrame frame_of_scan(const MapState& m, const double T[16]) { return scan_frame(m, T); }
+void set_global_error(const char* msg) { snprintf(g_create_error, sizeof(g_create_error), "%s", msg); }
+}  // namespace sbki
+
 extern "C" {
 
 sbki_status sbki_default_params(sbki_params* p) {

@@ -200,6 +200,12 @@ __device__ __forceinline__ bool in_support64(int vx, int vy, int vz, float x, fl
   return d2 < g.l2_64;
 }
 
+// ---------------------------------------------------------------- shared host helpers (sbki_api.cu)
+sbki_status validate_params(const sbki_params* p);
+Geom geometry_of(const sbki_params& p);
+KeyFrame frame_of_scan(const MapState& m, const double T[16]);
+void set_global_error(const char* msg);
+
 // ---------------------------------------------------------------- launchers (one per .cu)
 // scan.cu: exclusive prefix sums in place over n+1 entries (entry n receives the total)
 cudaError_t exclusive_scan_u32(uint32_t* data, int64_t n, void* tmp, cudaStream_t st);

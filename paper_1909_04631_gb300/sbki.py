@@ -22,7 +22,8 @@ STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "label out of range", 3: "cap
 
 EXPORTED = ["sbki_default_params", "sbki_create_map", "sbki_destroy_map", "sbki_insert_scan",
             "sbki_insert_scan_async", "sbki_sync", "sbki_training_set", "sbki_insert_training", "sbki_query_probs",
-            "sbki_voxel_count", "sbki_export", "sbki_profile", "sbki_profile_read", "sbki_kernel_values", "sbki_last_error", "sbki_status_string"]
+            "sbki_voxel_count", "sbki_export", "sbki_profile", "sbki_profile_read", "sbki_kernel_values", "sbki_last_error", "sbki_status_string",
+            "sbki_training_set_noalloc"]
 
 
 class SbkiError(RuntimeError):
@@ -85,6 +86,7 @@ def load(build_if_missing: bool = True):
         L.sbki_sync.argtypes = [vp, P(Stats)]
         L.sbki_training_set.argtypes = [vp, vp, vp, i64, vp, vp, i64, P(i64)]
         L.sbki_insert_training.argtypes = [vp, vp, i64, P(Stats)]
+        L.sbki_training_set_noalloc.argtypes = [P(Params), vp, vp, i64, vp, vp, i64, P(i64)]
         L.sbki_query_probs.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp]
         L.sbki_voxel_count.argtypes = [vp, P(i64)]
         L.sbki_export.argtypes = [vp, vp, vp, vp, i64, P(i64)]
@@ -100,7 +102,7 @@ def load(build_if_missing: bool = True):
         L.sbki_status_string.restype = C.c_char_p
         for f in ("sbki_default_params", "sbki_create_map", "sbki_insert_scan", "sbki_insert_scan_async", "sbki_sync",
                   "sbki_training_set", "sbki_insert_training", "sbki_query_probs", "sbki_voxel_count",
-                  "sbki_export"):
+                  "sbki_export", "sbki_training_set_noalloc"):
             getattr(L, f).restype = C.c_int
         _lib = L
         return L
@@ -114,6 +116,25 @@ def default_params(**kw) -> Params:
             raise TypeError("unknown parameter %r" % k)
         setattr(p, k, v)
     return p
+
+
+def training_set_noalloc(params: Params, points, labels, pose, out):
+    """Training set of a scan (steps a1-a3) through the entry point that
+    allocates nothing: points [n,3] float32, labels [n] int32 and out [cap,4]
+    float32 are CUDA tensors on params.device (the caller's memory); work runs
+    on params.cuda_stream.  Returns the number of points written to out."""
+    L = load()
+    T = np.ascontiguousarray(pose, dtype=np.float64).reshape(16)
+    for name, t in (("points", points), ("labels", labels), ("out", out)):
+        if not (hasattr(t, "is_cuda") and t.is_cuda and t.is_contiguous()):
+            raise TypeError("%s must be a contiguous CUDA tensor" % name)
+    cnt = C.c_int64()
+    st = L.sbki_training_set_noalloc(C.byref(params), C.c_void_p(points.data_ptr()), C.c_void_p(labels.data_ptr()),
+                                     points.shape[0], T.ctypes.data_as(C.c_void_p), C.c_void_p(out.data_ptr()),
+                                     out.shape[0], C.byref(cnt))
+    if st != OK:
+        raise SbkiError(st, L.sbki_last_error(None).decode())
+    return cnt.value
 
 
 def kernel_values(r, method=0):
