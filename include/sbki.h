@@ -62,6 +62,10 @@ typedef struct sbki_params {
   int64_t sample_capacity; /* max hits + free samples of one scan */
   int32_t track_pairs; /* nonzero: keep per-voxel in-support pair counts (parity aid) */
   int32_t device;      /* CUDA device ordinal */
+  int32_t accumulate_mode; /* step a5 form: 0 point-major (one warp per training
+                            * point, global reductions; default), 1 block-major
+                            * (one CTA per touched block, shared-memory tile;
+                            * also counts touched voxels in sbki_stats) */
   void* cuda_stream;   /* cudaStream_t for every launch and copy; NULL = legacy default stream */
 } sbki_params;
 
@@ -74,7 +78,7 @@ typedef struct sbki_stats {
   int64_t touched_blocks; /* blocks with at least one in-support pair */
   int64_t new_blocks;     /* blocks allocated by this insert */
   int64_t pairs;          /* in-support (voxel, training point) pairs, Eq. (alpha_kernel) */
-  int64_t touched_voxels; /* voxels whose alpha changed */
+  int64_t touched_voxels; /* voxels whose alpha changed (block-major mode only; 0 otherwise) */
   int64_t total_blocks;   /* blocks allocated in the map after the insert */
 } sbki_stats;
 

@@ -128,6 +128,8 @@ sbki_status check_params(const sbki_params* p) {
     return fail(nullptr, SBKI_ERR_INVALID_ARG, "length_scale must be <= 0.75 * block_edge * res");
   if (p->pool_blocks < 1 || p->pool_blocks > (1ll << 28))
     return fail(nullptr, SBKI_ERR_INVALID_ARG, "pool_blocks must be in 1..2^28");
+  if (p->accumulate_mode != 0 && p->accumulate_mode != 1)
+    return fail(nullptr, SBKI_ERR_INVALID_ARG, "accumulate_mode must be 0 (point-major) or 1 (block-major)");
   if (p->sample_capacity < 1 || p->sample_capacity > (1ll << 27))
     return fail(nullptr, SBKI_ERR_INVALID_ARG, "sample_capacity must be in 1..2^27");
   // tiles of training points overlapping one dilated block must stay few
@@ -389,6 +391,7 @@ sbki_status sbki_default_params(sbki_params* p) {
   p->sample_capacity = 1 << 24;
   p->track_pairs = 0;
   p->device = 0;
+  p->accumulate_mode = 0;
   p->cuda_stream = nullptr;
   return SBKI_OK;
 }
@@ -410,7 +413,7 @@ sbki_status sbki_create_map(const sbki_params* params, sbki_map** out) {
   m.device = params->device;
   m.stream = (cudaStream_t)params->cuda_stream;
   m.g = make_geom(m.prm);
-  if (const char* am = getenv("SBKI_ACCUMULATE")) m.acc_mode = (strcmp(am, "blocks") == 0) ? 1 : 0;
+  m.acc_mode = params->accumulate_mode;
   DeviceGuard dg(m.device);
   auto bail = [&](const char* what, cudaError_t e) {
     snprintf(g_create_error, sizeof(g_create_error), "%s: %s", what, cudaGetErrorString(e));

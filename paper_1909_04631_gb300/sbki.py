@@ -37,6 +37,7 @@ class Params(C.Structure):
                                           "min_range", "max_range", "free_thresh", "occ_thresh")] + \
                [("num_classes", C.c_int32), ("block_edge", C.c_int32), ("pool_blocks", C.c_int64),
                 ("sample_capacity", C.c_int64), ("track_pairs", C.c_int32), ("device", C.c_int32),
+                ("accumulate_mode", C.c_int32),
                 ("cuda_stream", C.c_void_p)]
 
 
@@ -179,7 +180,8 @@ class Map:
 
     def __init__(self, params: Params | None = None, stream=None, **kw):
         L = load()
-        self.params = params if params is not None else default_params(**kw)
+        # a private copy: keyword overrides and the stream never alter the caller's params
+        self.params = Params.from_buffer_copy(params) if params is not None else default_params(**kw)
         if params is not None and kw:
             for k, v in kw.items():
                 setattr(self.params, k, v)

@@ -3,6 +3,7 @@
 import ctypes
 import os
 import re
+import subprocess
 
 import pytest
 
@@ -46,7 +47,28 @@ def test_params_struct_matches_header_defaults():
     p = sbki.default_params()
     assert (p.length_scale, p.sigma0, p.alpha0, p.res, p.free_thresh, p.occ_thresh) == (0.3, 0.1, 0.001, 0.1, 0.47,
                                                                                       0.6)
-    assert ctypes.sizeof(sbki.Params) == 10 * 8 + 4 + 4 + 8 + 8 + 4 + 4 + 8
+    assert p.accumulate_mode == 0 and p.track_pairs == 0
+
+
+def test_struct_layouts_match_the_c_compiler(tmp_path):
+    """Offsets and sizes of the ctypes structures equal those gcc gives the header's structs."""
+    from paper_1909_04631_gb300 import sbki
+    structs = {"sbki_params": sbki.Params, "sbki_stats": sbki.Stats, "sbki_profile_data": sbki.ProfileData}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "sbki.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (cname, cname))
+        for f, _ in py._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (cname, f, cname, f))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)])
+    got = dict(l.split() for l in subprocess.check_output([str(exe)]).decode().split("\n") if l)
+    for cname, py in structs.items():
+        assert int(got[cname]) == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert int(got["%s.%s" % (cname, f)]) == getattr(py, f).offset, (cname, f)
 
 
 def test_create_map_fails_loudly_without_gpu():

@@ -15,6 +15,16 @@ from synth import scenes
 pytestmark = pytest.mark.gpu
 
 RTOL = 1e-5
+_MODE = 0  # accumulate_mode of the maps the current test creates
+
+
+@pytest.fixture(params=[0, 1], ids=["point_major", "block_major"], autouse=True)
+def accumulate_mode(request):
+    """Every map test runs with both forms of step a5."""
+    global _MODE
+    _MODE = request.param
+    yield request.param
+    _MODE = 0
 
 
 def _gpu_map(sb, prm, **kw):
@@ -23,7 +33,8 @@ def _gpu_map(sb, prm, **kw):
                           num_classes=prm["num_classes"], min_range=prm.get("min_range", 0.0),
                           max_range=prm.get("max_range", 100.0), block_edge=prm.get("block_edge", 8),
                           pool_blocks=kw.pop("pool_blocks", 1 << 15), sample_capacity=kw.pop("sample_capacity", 1 << 22),
-                          track_pairs=kw.pop("track_pairs", 1), device=0)
+                          track_pairs=kw.pop("track_pairs", 1), device=0,
+                          accumulate_mode=kw.pop("accumulate_mode", _MODE))
     for k, v in kw.items():
         setattr(p, k, v)
     return sb.Map(p)
