@@ -184,6 +184,130 @@ def peaks():
     return 6800.0, 2070.0, "fallback"
 
 
+def replica_first_scan(rank):
+    """Replicas only: rank r maps its own stretch of street, scans from 1000 r on."""
+    return rank * 1000
+
+
+def max_over_ranks(value, world, device):
+    """The slowest rank's figure (every rank returns it)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _gen_batch(n_maps):
+    return scenes.batch_scans(n_maps=n_maps)
+
+
+def _gen_diff(n_scans):
+    return list(scenes.small_region_lidar_sequence(n_scans))
+
+
+def batched_form(sb, torch, dev, stream, scans, reps):
+    """Independent maps, one scan each: one batched update (recorded graph)
+    against one sbki_insert_scan per scan, on the same GPU (device inputs)."""
+    prm = dict(scenes.BATCH_PARAMS, num_classes=19)
+    n = len(scans)
+    total = sum(len(s["points"]) for s in scans)
+    p = sb.default_params(**prm, num_maps=n, pool_blocks=1 << 18, sample_capacity=1 << 26, device=dev.index)
+    dp = [torch.from_numpy(s["points"]).to(dev) for s in scans]
+    dl = [torch.from_numpy(s["labels"]).to(dev) for s in scans]
+    batch = [dict(points=dp[i], labels=dl[i], pose=scans[i]["pose"], map_id=i) for i in range(n)]
+
+    def timed(fn):
+        fn()  # warm-up (and the graph recording of the batched form)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    seq = sb.Map(p, stream=stream)
+
+    def run_seq():
+        for i in range(n):
+            seq.select(i)
+            seq.insert_scan(dp[i], dl[i], scans[i]["pose"])
+
+    ms_seq = timed(run_seq)
+    seq.close()
+    bat = sb.Map(p, stream=stream)
+    st = {}
+
+    def run_batch():
+        st.update(bat.insert_batch(batch))
+
+    ms_batch = timed(run_batch)
+    launches = bat.profile_read()["launches"]
+    bat.close()
+    return {"workload": "%d independent maps, one scan each: N log-uniform 5k..250k, LiDAR- or depth-shaped, "
+                        "0.1 m voxels, l = 0.3 m" % n, "scans": n, "points": total,
+            "train_points": st.get("train_points"), "pairs": st.get("pairs"), "reps": reps,
+            "sequential_ms": ms_seq, "batched_ms": ms_batch, "sequential_scans_per_s": n / (ms_seq / 1e3),
+            "batched_scans_per_s": n / (ms_batch / 1e3), "speedup": ms_seq / ms_batch,
+            "batched_kernels_per_update": launches // (reps + 1)}
+
+
+def differentiable_form(sb, torch, dev, stream, scans, reps):
+    """Held-out log-likelihood and its gradient w.r.t. l, sigma0 and every
+    training point on the small-region LiDAR sequence, against forward only."""
+    prm = dict(scenes.DIFF_PARAMS)
+    p = sb.default_params(**prm, pool_blocks=1 << 16, sample_capacity=1 << 23, device=dev.index)
+    xs, ls, hx, hl = [], [], [], []
+    with sb.Map(p, stream=stream) as m:
+        for sc in scans:
+            x, l = m.training_set(sc["points"], sc["labels"], sc["pose"])
+            xs.append(x)
+            ls.append(l)
+            T = np.asarray(sc["pose"], np.float64).reshape(4, 4)
+            hp = sc["held_points"].astype(np.float64)
+            hw = np.stack([(((T[a, 0] * hp[:, 0] + T[a, 1] * hp[:, 1]) + T[a, 2] * hp[:, 2]) + T[a, 3])
+                           for a in range(3)], 1).astype(np.float32)
+            hx.append(hw)
+            hl.append(sc["held_labels"])
+    xyz = torch.from_numpy(np.concatenate(xs)).to(dev)
+    lab = torch.from_numpy(np.concatenate(ls).astype(np.int32)).to(dev)
+    xyzl = torch.cat([xyz, lab[:, None].float()], 1).contiguous()
+    held = torch.from_numpy(np.concatenate(hx)).to(dev)
+    held_lab = torch.from_numpy(np.concatenate(hl).astype(np.int32)).to(dev)
+    maps = [sb.Map(p, stream=stream) for _ in range(2 * reps + 2)]
+    res = {}
+    for mode in ("forward", "forward_backward"):
+        times = []
+        for r in range(reps + 1):
+            m = maps.pop()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            m.insert_training(xyz, lab)
+            if mode == "forward":
+                ll = m.heldout_loglik(held, held_lab)
+            else:
+                m.grad_clear()
+                ll = m.heldout_loglik(held, held_lab, grad=True)
+                gl, gs, gx = m.backward(xyzl)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if r > 0:
+                times.append(e0.elapsed_time(e1))
+            m.close()
+        res[mode + "_ms"] = float(np.median(times))
+    for m in maps:
+        m.close()
+    return {"workload": "%d LiDAR scans (64x2048) of the 20x20x4 m region, 20%% of hits held out; gradient w.r.t. "
+                        "l, sigma0 and all %d training points" % (len(scans), xyz.shape[0]),
+            "train_points": int(xyz.shape[0]), "held_out": int(held.shape[0]), "reps": reps, **res,
+            "backward_overhead": res["forward_backward_ms"] / res["forward_ms"]}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -214,8 +338,14 @@ def run_ours(args, rank, world, local_rank):
 
     # host-side generation before any GPU call (spawn pool)
     nscan = min(args.scans, args.warmup + args.steps)
-    per_rank_first = rank * 1000  # replicas: every rank maps its own stretch of street
-    scans = generate_scans(per_rank_first, nscan, args.workers)
+    scans = generate_scans(replica_first_scan(rank), nscan, args.workers)
+    forms_input = None
+    if rank == 0 and not args.no_forms:
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(2) as pool:
+            fb = pool.apply_async(_gen_batch, (32,))
+            fd = pool.apply_async(_gen_diff, (20,))
+            forms_input = (fb.get(), fd.get())
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # the oracle on a bounded sample: 12 azimuth sectors of 45 degrees (scan 0
@@ -258,12 +388,7 @@ def run_ours(args, rank, world, local_rank):
             stats.append(m.insert_scan(dpts[j], dlab[j], poses[j]))
         ev1.record(stream)
         torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
     prof = m.profile_read()
     launches = prof["launches"] - launches0
     m.profile(False, reset=True)
@@ -288,13 +413,8 @@ def run_ours(args, rank, world, local_rank):
         m.insert_scan(hp[j].numpy(), hl[j].numpy(), poses[j])
         h2d += hp[j].numel() * 4 + hl[j].numel() * 4
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
     m.close()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
 
     if rank != 0:
         return 0
@@ -363,6 +483,9 @@ def run_ours(args, rank, world, local_rank):
                 "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": 80},
         "cpu_baseline": cpu,
     }
+    if forms_input is not None:
+        line["batched"] = batched_form(sb, torch, dev, stream, forms_input[0], reps=5)
+        line["differentiable"] = differentiable_form(sb, torch, dev, stream, forms_input[1], reps=3)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -376,6 +499,7 @@ def main():
     ap.add_argument("--scans", type=int, default=100, help="distinct scans of the sequence to cycle over")
     ap.add_argument("--workers", type=int, default=min(16, os.cpu_count() or 1))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the batched and differentiable measurements")
     ap.add_argument("--pool-blocks", type=int, default=1 << 18, help="map block pool capacity")
     ap.add_argument("--sample-capacity", type=int, default=1 << 23, help="hits + free samples per scan")
     args = ap.parse_args()

@@ -66,6 +66,9 @@ typedef struct sbki_params {
                             * point, global reductions; default), 1 block-major
                             * (one CTA per touched block, shared-memory tile;
                             * also counts touched voxels in sbki_stats) */
+  int32_t num_maps;    /* independent maps held by the handle (1..64, default 1);
+                        * they share the block pool; see sbki_select_map and
+                        * sbki_insert_batch */
   void* cuda_stream;   /* cudaStream_t for every launch and copy; NULL = legacy default stream */
 } sbki_params;
 
@@ -133,7 +136,7 @@ sbki_status sbki_training_set(sbki_map* map, const float* points, const int32_t*
  *   points [n,3] float32 and labels [n] int32 (1..K): DEVICE memory of
  *     params->device; xyzl_out [cap,4] float32: DEVICE memory, written as for
  *     sbki_training_set; *count (host) receives the number of points.
- * Every intermediate buffer lives in one fixed device array of about 9.4 MB
+ * Every intermediate buffer lives in one fixed device array of about 8.9 MB
  * that each GPU loading the library holds until the process exits; nothing
  * is allocated per call (no cudaMalloc, cudaFree or allocating library call).
  * Limits: n <= 16384 points (else SBKI_ERR_INVALID_ARG before any GPU work)
@@ -148,6 +151,35 @@ sbki_status sbki_training_set(sbki_map* map, const float* points, const int32_t*
 sbki_status sbki_training_set_noalloc(const sbki_params* params, const float* points, const int32_t* labels,
                                       int64_t n, const double sensor_pose[16], float* xyzl_out, int64_t cap,
                                       int64_t* count);
+
+/* One scan of a batched update. */
+typedef struct sbki_scan {
+  const float* points;   /* [n,3] sensor frame (host or device) */
+  const int32_t* labels; /* [n] in 1..K (host or device) */
+  int64_t n;
+  double pose[16];       /* world_from_sensor, row-major */
+  int32_t map_id;        /* target map of the handle, 0..num_maps-1 */
+} sbki_scan;
+
+/* Batched form of the update (Sec. III + Eq. (alpha_kernel) + Sec. IV for
+ * every scan): scans[0..count) (count <= 64), each into map scans[i].map_id
+ * of the handle, go through one pass of the device pipeline - one launch per
+ * stage for all scans together (persistent kernels over the concatenated
+ * points, items and training points; every scan is downsampled on its own,
+ * as sbki_insert_scan would) with no host round trip between stages.  The
+ * stage sequence is recorded once per batch size as a CUDA graph and replayed
+ * on later calls with the same count.  Scans into the same map add up as
+ * consecutive sbki_insert_scan calls would (up to the order of FP32 sums).
+ * The sum of n must fit the staging capacity (grown on demand, outside the
+ * graph) and the hits + free samples of all scans must fit sample_capacity.
+ * Synchronises the stream once, at the end; stats are totals over the batch
+ * (touched_voxels 0).  On any error no map changes. */
+sbki_status sbki_insert_batch(sbki_map* map, const sbki_scan* scans, int32_t count, sbki_stats* stats);
+
+/* Selects the map of the handle (0..num_maps-1) that sbki_insert_scan,
+ * sbki_insert_scan_async, sbki_insert_training, sbki_query_probs,
+ * sbki_voxel_count, sbki_export and the differentiable calls act on. */
+sbki_status sbki_select_map(sbki_map* map, int32_t map_id);
 
 /* Eq. (alpha_kernel) for a given training set (no sampling or downsampling):
  * xyzl [p,4] float32 world (x, y, z, label as float) with labels 0..K. */
@@ -195,6 +227,58 @@ sbki_status sbki_profile_read(const sbki_map* map, sbki_profile_data* out);
  * trigonometric form.  r and f are device buffers of n floats; synchronises
  * `stream` (a cudaStream_t, NULL = legacy default stream).  Diagnostic aid. */
 sbki_status sbki_kernel_values(const float* r, int64_t n, float* f, int32_t method, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Differentiable form.  alpha is a smooth function of the training points,
+ * of l and of sigma0 (Eq. alpha_kernel with Eq. kernel, which has zero slope
+ * at d = l, so the support boundary adds no term).  A map holds a gradient
+ * buffer G = dL/dalpha with the layout of alpha, allocated on first use
+ * (pool_blocks x (K+1) x block_edge^3 floats); the calls below fill it and
+ * pull it back through every in-support pair, recomputing the kernel.
+ * Gradients refer to the training set inserted with sbki_insert_training:
+ * pass the same xyzl to sbki_backward.
+ * ------------------------------------------------------------------------ */
+
+/* Sets G to zero on every allocated block. */
+sbki_status sbki_grad_clear(sbki_map* map);
+
+/* Held-out log-likelihood of labelled points, the Dirichlet mean of Eq.
+ * (variance) used as the predictive probability at the voxel containing each
+ * point: LL = sum_h log(alpha^{y_h} / sum_k alpha^k) (alpha with prior; a
+ * voxel outside every block reads the prior).  xyz [h,3] world, labels [h] in
+ * 0..K (host or device).  If accumulate_grad != 0, dLL/dalpha is added into G
+ * (only on allocated blocks: no pair reaches the others).  *loglik on host. */
+sbki_status sbki_heldout_loglik(sbki_map* map, const float* xyz, const int32_t* labels, int64_t h,
+                                int32_t accumulate_grad, double* loglik);
+
+/* Adds an upstream gradient given per voxel: keys [count,3] int64 voxel
+ * indices, grad_alpha [count,K+1] float32 (host or device).  Rows whose voxel
+ * lies outside every allocated block are skipped and counted in *missed
+ * (nullable): no pair reaches them. */
+sbki_status sbki_grad_add_alpha(sbki_map* map, const int64_t* keys, const float* grad_alpha, int64_t count,
+                                int64_t* missed);
+
+/* Backward pass of Eq. (alpha_kernel) through Eq. (kernel) for the training
+ * set xyzl [p,4] (world x, y, z, label as float; host or device) that was
+ * inserted: with r = d/l and G = G_v^{y_i} per in-support pair,
+ *   grad_sigma0 = sum G f(r),  grad_l = sum G sigma0 f'(r) (-d/l^2),
+ *   grad_xyz[i] = sum_v G sigma0 f'(r) (x_i - c_v)/(l d)   ([p,3], nullable,
+ *   host or device; 0 where d = 0).
+ * grad_l and grad_sigma0 (host, nullable) are summed in FP64 from FP32 pair
+ * terms. */
+sbki_status sbki_backward(sbki_map* map, const float* xyzl, int64_t p, double* grad_l, double* grad_sigma0,
+                          float* grad_xyz);
+
+/* Stateless forms (they create and destroy a map of `params` inside the call,
+ * so they allocate): alpha of a training set at every voxel of the blocks it
+ * reaches (as sbki_export: keys_out [cap,3], alpha_out [cap,K+1], host
+ * memory, sorted by key, count-only when both are NULL), and the gradient of
+ * L with respect to l, sigma0 and the points for dL/dalpha given at voxel
+ * keys.  Errors are reported by sbki_last_error(NULL). */
+sbki_status sbki_forward_alpha(const sbki_params* params, const float* xyzl, int64_t p, int64_t* keys_out,
+                               float* alpha_out, int64_t cap, int64_t* count);
+sbki_status sbki_grad(const sbki_params* params, const float* xyzl, int64_t p, const int64_t* keys,
+                      const float* grad_alpha, int64_t count, double* grad_l, double* grad_sigma0, float* grad_xyz);
 
 /* Message of the last failure on this map (or of the last sbki_create_map
  * failure when map is NULL). */

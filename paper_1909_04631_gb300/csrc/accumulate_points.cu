@@ -4,21 +4,25 @@
 //
 // Candidate voxels come from a static table.  Split the voxel of a point into
 // 3x3x3 parts by the point's sub-voxel position; for each part the table
-// lists every offset d (relative to the point's voxel) whose centre can lie
-// within l of some position in that part, widened by 0.01 voxel on every side
-// (so FP32 rounding of the position cannot pick too small a list).  For
-// l = 3 res a list has at most 154 entries, against ~113 in support.
+// lists every offset (dx, dy, dz) (relative to the point's voxel) whose centre
+// can lie within l of some position in that part, widened by 0.01 voxel on
+// every side (so FP32 rounding of the position cannot pick too small a list).
+// For l = 3 res a list has at most 154 entries, against ~113 in support.
 // Per point the warp
 //   1. forms the compensated offsets E0 = c(v0) - x of the point's own voxel
-//      centre (hi + lo per axis) and, per axis and per offset d, the squared
-//      offset (E0 + d res)^2 and the block / in-block index of voxel v0 + d
-//      (shared memory, one lane per entry); looks up the pool slots of the
-//      blocks the ball can reach (one lane per block);
-//   2. sweeps its part's list, 32 candidates at a time: d^2 is the sum of
-//      three looked-up squares; the FP32 test (re-decided in FP64 inside the
-//      relative band around l^2), the kernel value, and red.global.add.f32
-//      into alpha.  Lists are sorted z, y, x so that neighbouring lanes update
-//      neighbouring voxels.
+//      centre (hi + lo per axis) and fills two per-warp lookup tables in
+//      shared memory: X[dx] = (ex^2, x-part of the voxel address) and
+//      YZ[dy, dz] = (ey^2 + ez^2, y/z-part of the voxel address), where an
+//      address part holds the block-offset digit (base 3 per axis) in its low
+//      byte and the in-block index above it, so the two parts add up to the
+//      full address without carries; and the pointers to class y_i of the
+//      (at most 27) blocks the ball can reach;
+//   2. sweeps its part's list, 32 candidates at a time (fully unrolled for
+//      the common list lengths): a list entry holds the byte offsets of its X
+//      and YZ rows, so d^2 and the address are two shared-memory loads and two
+//      adds; the FP32 test (re-decided in FP64 inside the relative band around
+//      l^2), the kernel value and red.global.add.f32 into alpha.  Padding
+//      entries point at an X row with d^2 = 1e30.
 // Training points arrive sorted by their downsampling cell, so the warps in
 // flight at any moment update a compact region of the map (L2 locality).
 // Blocks allocated by this update are zero-filled before (fresh_fill_kernel).
@@ -27,14 +31,16 @@
 #include <vector>
 
 #include "kernel_value.cuh"
-#include "sbki_internal.cuh"
+#include "point_common.cuh"
 
 namespace sbki {
 namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kAxisMax = 16;  // offsets per axis: 2R + 1 <= 15
+constexpr int kAxisMax = 15;             // offsets per axis: 2R + 1 <= 15
+constexpr int kYZMax = kAxisMax * kAxisMax;
+constexpr float kFar = 1.0e30f;          // d^2 of the padding row
 
 struct PtArgs {
   Geom g;
@@ -44,102 +50,112 @@ struct PtArgs {
   int64_t hash_cap;
   float* alpha;
   int32_t* pairs;
-  const int32_t* ctab;  // [27][tpad] packed (ix | iy << 4 | iz << 8), -1 = none
-  int tpad;             // entries per list (multiple of 32)
-  int R;                // offsets per axis span [-R, R]
+  const uint32_t* ctab;  // [27][tpad] (X byte offset | YZ byte offset << 8 | dy << 19 | dz << 23)
+  int tpad;              // entries per list (multiple of 32)
+  int R;                 // offsets per axis span [-R, R]
+  uint32_t recip_na;     // small_recip(2R + 1)
   DevCounters* dc;
 };
 
-__device__ __forceinline__ int floor_i(float v) { return (int)floorf(v); }
+struct WarpTables {
+  float2 x[kAxisMax + 1];  // (e_x^2, address part as int bits); entry 2R+1 is the padding row
+  float2 yz[kYZMax];
+  float* blk[27];          // alpha + (pool * (K+1) + y_i) * B^3, or null
+  int32_t* cnt[27];        // pair counts of the block (tracking only)
+};
 
-__device__ int32_t find_pool(const PtArgs& a, unsigned long long key) {
-  uint32_t slot = hash_slot(key, a.hash_cap);
-  for (int probe = 0; probe < kMaxProbes; ++probe) {
-    const unsigned long long k = a.hkeys[slot];
-    if (k == key) return a.hvals[slot];
-    if (k == kEmpty) return -1;
-    slot = (uint32_t)((slot + 1) & (uint32_t)(a.hash_cap - 1));
+// One candidate per lane, branch-free except for the (rare, warp-uniform)
+// FP64 re-decision: every lane evaluates the kernel and the reduction is
+// predicated.  Every list entry (padding included) yields a block digit in
+// 0..26, so the block-pointer load is always in range.  Returns 1 for an
+// in-support pair.
+template <bool kTrack>
+__device__ __forceinline__ uint32_t candidate(const PtArgs& a, const WarpTables& t, uint32_t ent, const int v0[3],
+                                              const float4& p) {
+  const Geom& g = a.g;
+  const float2 ex = *reinterpret_cast<const float2*>(reinterpret_cast<const char*>(t.x) + (ent & 0xffu));
+  const float2 eyz = *reinterpret_cast<const float2*>(reinterpret_cast<const char*>(t.yz) + ((ent >> 8) & 0x7ffu));
+  const float d2 = __fadd_rn(ex.x, eyz.x);
+  const int pk = __float_as_int(ex.y) + __float_as_int(eyz.y);
+  bool in = d2 < g.l2_lo;
+  const bool band = !in && d2 < g.l2_hi;
+  if (__any_sync(0xffffffffu, band)) {
+    if (band)
+      in = in_support64_call(v0[0] + (int)((ent & 0xffu) >> 3) - a.R, v0[1] + (int)((ent >> 19) & 15u) - a.R,
+                             v0[2] + (int)((ent >> 23) & 15u) - a.R, p.x, p.y, p.z, g.res64, g.l2_64);
   }
-  return -1;
+  float* base = t.blk[pk & 0xff];
+  const float d = d2 * rsqrtf(fmaxf(d2, 1e-30f));
+  const float u = fmaxf(__fmaf_rn(-d, g.inv_l, 1.0f), 0.0f);
+  const float w = u * u;
+  const bool hit = in && base != nullptr;
+  red_add_if(hit, base + (pk >> 8), g.sigma0 * (w * w * u * kernel_q(w)));
+  if (kTrack) red_add_if(hit, t.cnt[pk & 0xff] + (pk >> 8), 1);
+  return hit ? 1u : 0u;
 }
 
-template <bool kTrack>
-__global__ void __launch_bounds__(kThreads) accumulate_points_kernel(PtArgs a) {
-  __shared__ float s_sq[kWarps][3][kAxisMax];
-  __shared__ int s_pk[kWarps][3][kAxisMax];  // (block index weight) << 16 | in-block index weight
+// kNit > 0: lists of exactly kNit x 32 entries, unrolled; 0: any length
+template <bool kTrack, int kNit>
+__global__ void __launch_bounds__(kThreads, 4) accumulate_points_kernel(PtArgs a) {
+  __shared__ WarpTables s_tab[kWarps];
   const Geom& g = a.g;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-  const int B = g.B, K1B3 = g.K1 * g.B3, R = a.R, naxis = 2 * R + 1;
-  const uint32_t maxis = small_recip(naxis);
-  float(*sq)[kAxisMax] = s_sq[wid];
-  int(*pk)[kAxisMax] = s_pk[wid];
+  const int R = a.R, na = 2 * R + 1;
+  WarpTables& t = s_tab[wid];
   uint32_t npairs = 0;
   if (a.dc->err != 0) return;
   const uint32_t P = a.dc->n_train;
+  if (lane == 0) t.x[na] = make_float2(kFar, __int_as_float(0));
   float4 pnext = gw < P ? a.train[gw] : make_float4(0.f, 0.f, 0.f, 0.f);
   for (uint32_t i = gw; i < P; i += nw) {
     const float4 p = pnext;
     if (i + nw < P) pnext = a.train[i + nw];  // in flight while this point is processed
-    const int label = (int)p.w;
-    const float xs[3] = {p.x, p.y, p.z};
-    int v0[3], part[3], blo[3], nb[3];
-    float hi[3], lo[3];
-#pragma unroll
-    for (int ax = 0; ax < 3; ++ax) {
-      v0[ax] = floor_i(__fmul_rn(xs[ax], g.inv_res));
-      centre_offset0(v0[ax], xs[ax], g, hi[ax], lo[ax]);
-      // sub-voxel position 1/2 - E0/res (accurate anywhere in the map), in thirds
-      const float phi = 0.5f - __fmul_rn(__fadd_rn(hi[ax], lo[ax]), g.inv_res);
-      part[ax] = min(2, max(0, floor_i(phi * 3.0f)));
-      blo[ax] = (v0[ax] - R) >> g.B_shift;
-      nb[ax] = ((v0[ax] + R) >> g.B_shift) - blo[ax] + 1;
+    const int lm = label_of(p.w);  // label + 32 * map
+    const int label = lm & ((1 << kLabelBits) - 1), map = lm >> kLabelBits;
+    const PointFrame f = point_frame(p.x, p.y, p.z, R, g);
+    const uint32_t* tab = a.ctab + f.part * a.tpad;
+    // X rows
+    if (lane < na) {
+      const float e = centre_offset_at(lane - R, f.hi[0], f.lo[0], g);
+      t.x[lane] = make_float2(__fmul_rn(e, e), __int_as_float(xpart(f, lane, R, g)));
     }
-    const int32_t* tab = a.ctab + (part[0] + 3 * part[1] + 9 * part[2]) * a.tpad;
-    // per-axis lookups: lane -> (axis, offset)
-    for (int q = lane; q < 3 * naxis; q += 32) {
-      const int ax = (int)small_div(q, maxis), j = q - ax * naxis, d = j - R;
-      const float h = ax == 0 ? hi[0] : (ax == 1 ? hi[1] : hi[2]);
-      const float l0 = ax == 0 ? lo[0] : (ax == 1 ? lo[1] : lo[2]);
-      const int vv = (ax == 0 ? v0[0] : (ax == 1 ? v0[1] : v0[2])) + d;
-      const int bl = ax == 0 ? blo[0] : (ax == 1 ? blo[1] : blo[2]);
-      const int w = ax == 0 ? 1 : (ax == 1 ? nb[0] : nb[0] * nb[1]);
-      const int stride = ax == 0 ? 1 : (ax == 1 ? B : B * B);
-      const float e = centre_offset_at(d, h, l0, g);
-      sq[ax][j] = __fmul_rn(e, e);
-      pk[ax][j] = (((vv >> g.B_shift) - bl) * w << 16) | ((vv & (B - 1)) * stride);
+    // Y rows in lanes 0..15, Z rows in lanes 16..31, combined into YZ rows by shuffles
+    float sq1 = 0.f;
+    int pk1 = 0;
+    {
+      const int ax = 1 + (lane >> 4), j = min(lane & 15, na - 1);
+      const float e = centre_offset_at(j - R, f.hi[ax], f.lo[ax], g);
+      const int v = f.v0[ax] + j - R, m = g.B - 1;
+      sq1 = __fmul_rn(e, e);
+      pk1 = ax == 1 ? (3 * ((v >> g.B_shift) - f.blo[1])) | ((v & m) << (g.B_shift + 8))
+                    : (9 * ((v >> g.B_shift) - f.blo[2])) | ((v & m) << (2 * g.B_shift + 8));
     }
-    int32_t pool = -1;
-    const int nblk = nb[0] * nb[1] * nb[2];
-    if (lane < nblk) {
-      const uint32_t mx = small_recip(nb[0]), mxy = small_recip(nb[0] * nb[1]);
-      const int cz = (int)small_div(lane, mxy), cxy = lane - cz * nb[0] * nb[1];
-      const int cy = (int)small_div(cxy, mx), cx = cxy - cy * nb[0];
-      pool = find_pool(a, pack_block(blo[0] + cx, blo[1] + cy, blo[2] + cz));
+    for (int q0 = 0; q0 < na * na; q0 += 32) {  // uniform trip count: full-warp shuffles
+      const int q = min(q0 + lane, na * na - 1);
+      const int jy = (int)small_div((uint32_t)q, a.recip_na), jz = q - jy * na;
+      const float sy = __shfl_sync(0xffffffffu, sq1, jy), sz = __shfl_sync(0xffffffffu, sq1, 16 + jz);
+      const int py = __shfl_sync(0xffffffffu, pk1, jy), pz = __shfl_sync(0xffffffffu, pk1, 16 + jz);
+      if (q0 + lane < na * na) t.yz[q] = make_float2(__fadd_rn(sy, sz), __int_as_float(py + pz));
+    }
+    // blocks the ball can reach: digit (bx, by, bz) in base 3
+    if (lane < 27) {
+      const int32_t pool = digit_pool(f, lane, map, a.hkeys, a.hvals, a.hash_cap);
+      t.blk[lane] = pool >= 0 ? a.alpha + ((size_t)pool * g.K1 + label) * g.B3 : nullptr;
+      if (kTrack) t.cnt[lane] = pool >= 0 ? a.pairs + (size_t)pool * g.B3 : nullptr;
     }
     __syncwarp();
-    float* base = a.alpha + (size_t)label * g.B3;
-    for (int k = lane; k < a.tpad; k += 32) {  // uniform trip count: full-warp shuffle below
-      const int ent = __ldg(tab + k);
-      const bool live = ent >= 0;
-      const int ix = ent & 15, iy = (ent >> 4) & 15, iz = (ent >> 8) & 15;
-      const float d2 = live ? __fadd_rn(__fadd_rn(sq[0][ix], sq[1][iy]), sq[2][iz]) : 3.0e38f;
-      const int ps = pk[0][ix] + pk[1][iy] + pk[2][iz];
-      bool in = d2 < g.l2_lo;
-      if (!in && d2 < g.l2_hi)
-        in = in_support64(v0[0] + ix - R, v0[1] + iy - R, v0[2] + iz - R, p.x, p.y, p.z, g);
-      const int32_t pl = __shfl_sync(0xffffffffu, pool, live ? (ps >> 16) : 0);
-      if (in && pl >= 0) {
-        const float d = d2 * rsqrtf(fmaxf(d2, 1e-30f));
-        const float u = __fmul_rn(__fsub_rn(g.l, d), g.inv_l);
-        const int local = ps & 0xffff;
-        atomicAdd(base + (size_t)pl * K1B3 + local, g.sigma0 * kernel_f_poly_u(u));
-        if (kTrack) atomicAdd(a.pairs + (size_t)pl * g.B3 + local, 1);
-      }
-      npairs += (in && pl >= 0) ? 1u : 0u;
+    if (kNit > 0) {
+      uint32_t ent[kNit > 0 ? kNit : 1];
+#pragma unroll
+      for (int it = 0; it < kNit; ++it) ent[it] = __ldg(tab + it * 32 + lane);
+#pragma unroll
+      for (int it = 0; it < kNit; ++it) npairs += candidate<kTrack>(a, t, ent[it], f.v0, p);
+    } else {
+      for (int k = lane; k < a.tpad; k += 32) npairs += candidate<kTrack>(a, t, __ldg(tab + k), f.v0, p);
     }
-    __syncwarp();  // the lookups are rewritten for the next point
+    __syncwarp();  // the tables are rewritten for the next point
   }
   for (int o = 16; o > 0; o >>= 1) npairs += __shfl_down_sync(0xffffffffu, npairs, o);
   if (lane == 0) atomicAdd(&a.dc->pairs, (unsigned long long)npairs);
@@ -194,23 +210,52 @@ cudaError_t build_candidate_tables(MapState& m) {
   for (auto& L : lists)
     for (int32_t e : L)
       for (int a = 0; a < 3; ++a) maxd = std::max(maxd, std::abs(((e >> (4 * a)) & 15) - R));
-  // re-pack with the tight R (the lookups hold 2R + 1 <= 15 entries per axis)
-  const int Rt = maxd;
+  // re-pack with the tight R (the lookups hold 2R + 1 <= 15 entries per axis):
+  // X row jx at byte offset 8 jx, YZ row (jy, jz) at byte offset 8 (jy (2R+1) + jz);
+  // padding entries point at X row 2R + 1 (d^2 = 1e30) and YZ row 0
+  const int Rt = maxd, na = 2 * Rt + 1;
+  if (na > kAxisMax) return cudaErrorInvalidValue;
   const int tpad = (int)((longest + 31) / 32 * 32);
-  std::vector<int32_t> flat((size_t)27 * tpad, -1);
+  std::vector<uint32_t> flat((size_t)27 * tpad, (uint32_t)(8 * na));
   for (int t = 0; t < 27; ++t)
     for (size_t k = 0; k < lists[t].size(); ++k) {
       const int32_t e = lists[t][k];
-      const int dx = (e & 15) - R, dy = ((e >> 4) & 15) - R, dz = ((e >> 8) & 15) - R;
-      flat[(size_t)t * tpad + k] = (dx + Rt) | ((dy + Rt) << 4) | ((dz + Rt) << 8);
+      const uint32_t jx = (uint32_t)((e & 15) - R + Rt), jy = (uint32_t)(((e >> 4) & 15) - R + Rt),
+                     jz = (uint32_t)(((e >> 8) & 15) - R + Rt);
+      flat[(size_t)t * tpad + k] = (8u * jx) | ((8u * (jy * na + jz)) << 8) | (jy << 19) | (jz << 23);
     }
-  if (2 * Rt + 1 > kAxisMax) return cudaErrorInvalidValue;
-  cudaError_t e = cudaMalloc(&m.ctab, sizeof(int32_t) * flat.size());
+  cudaError_t e = cudaMalloc(&m.ctab, sizeof(uint32_t) * flat.size());
   if (e != cudaSuccess) return e;
   m.ctab_pad = tpad;
   m.ctab_R = Rt;
-  return cudaMemcpy(m.ctab, flat.data(), sizeof(int32_t) * flat.size(), cudaMemcpyHostToDevice);
+  return cudaMemcpy(m.ctab, flat.data(), sizeof(uint32_t) * flat.size(), cudaMemcpyHostToDevice);
 }
+
+namespace {
+
+template <bool kTrack, int kNit>
+cudaError_t launch_points(const PtArgs& a, int sm_count, cudaStream_t st) {
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, accumulate_points_kernel<kTrack, kNit>,
+                                                                kThreads, 0);
+  if (e != cudaSuccess) return e;
+  accumulate_points_kernel<kTrack, kNit><<<std::max(1, per_sm) * sm_count, kThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <bool kTrack>
+cudaError_t launch_points_nit(const PtArgs& a, int sm_count, cudaStream_t st) {
+  switch (a.tpad / 32) {  // unrolled sweeps for the common list lengths
+    case 2: return launch_points<kTrack, 2>(a, sm_count, st);
+    case 3: return launch_points<kTrack, 3>(a, sm_count, st);
+    case 4: return launch_points<kTrack, 4>(a, sm_count, st);
+    case 5: return launch_points<kTrack, 5>(a, sm_count, st);
+    case 6: return launch_points<kTrack, 6>(a, sm_count, st);
+    default: return launch_points<kTrack, 0>(a, sm_count, st);
+  }
+}
+
+}  // namespace
 
 cudaError_t launch_accumulate_points(MapState& m) {
   fresh_fill_kernel<<<m.sm_count * 4, 256, 0, m.stream>>>(m.s.fresh, m.hvals, m.alpha, m.pairs, m.g.K1 * m.g.B3,
@@ -226,17 +271,10 @@ cudaError_t launch_accumulate_points(MapState& m) {
   a.ctab = m.ctab;
   a.tpad = m.ctab_pad;
   a.R = m.ctab_R;
+  a.recip_na = ((1u << 20) + (uint32_t)(2 * m.ctab_R + 1) - 1u) / (uint32_t)(2 * m.ctab_R + 1);
   a.dc = m.dc;
-  int per_sm = 0;
-  cudaError_t e;
-  if (m.pairs) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, accumulate_points_kernel<true>, kThreads, 0);
-  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, accumulate_points_kernel<false>, kThreads, 0);
-  if (e != cudaSuccess) return e;
-  const int grid = std::max(1, per_sm) * m.sm_count;
-  if (m.pairs) accumulate_points_kernel<true><<<grid, kThreads, 0, m.stream>>>(a);
-  else accumulate_points_kernel<false><<<grid, kThreads, 0, m.stream>>>(a);
   m.launches += 2;
-  return cudaGetLastError();
+  return m.pairs ? launch_points_nit<true>(a, m.sm_count, m.stream) : launch_points_nit<false>(a, m.sm_count, m.stream);
 }
 
 }  // namespace sbki

@@ -33,14 +33,14 @@ struct TouchArgs {
   uint32_t* touched;
   uint32_t* fresh;
   uint32_t* blist;
-  uint32_t epoch;
   DevCounters* dc;
 };
 
 __device__ __forceinline__ int floor_i(float v) { return (int)floorf(v); }
 
 __device__ void mark_touched(const TouchArgs& a, uint32_t slot) {
-  if (atomicExch(&a.hmark[slot], a.epoch) != a.epoch) {
+  const uint32_t epoch = a.dc->epoch;
+  if (atomicExch(&a.hmark[slot], epoch) != epoch) {
     const uint32_t t = atomicAdd(&a.dc->n_touched, 1u);
     a.touched[t] = slot;
   }
@@ -151,34 +151,40 @@ __device__ void candidate_blocks(const float xs[3], const Geom& g, int blo[3], i
 // point count (used to lay out the per-block point lists).
 __global__ void __launch_bounds__(256) touch_kernel(TouchArgs a) {
   const Geom& g = a.g;
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool active = a.dc->err == 0 && i < a.dc->n_train;
-  float xs[3] = {0.f, 0.f, 0.f};
-  int blo[3] = {0, 0, 0}, bhi[3] = {-1, -1, -1};
-  if (active) {
-    const float4 p = a.train[i];
-    xs[0] = p.x;
-    xs[1] = p.y;
-    xs[2] = p.z;
-    candidate_blocks(xs, g, blo, bhi);
-  }
-  // the warp walks the smallest cube of candidate offsets that covers every lane
-  const int mx = __reduce_max_sync(0xffffffffu, (unsigned)max(0, bhi[0] - blo[0] + 1));
-  const int my = __reduce_max_sync(0xffffffffu, (unsigned)max(0, bhi[1] - blo[1] + 1));
-  const int mz = __reduce_max_sync(0xffffffffu, (unsigned)max(0, bhi[2] - blo[2] + 1));
-  const int nc = mx * my * mz;
-  for (int c = 0; c < nc; ++c) {
-    const int bx = blo[0] + c % mx, by = blo[1] + (c / mx) % my, bz = blo[2] + c / (mx * my);
-    bool hit = bx <= bhi[0] && by <= bhi[1] && bz <= bhi[2];
-    if (hit) {
-      const int K0[3] = {bx << g.B_shift, by << g.B_shift, bz << g.B_shift};
-      hit = touches_block(K0, xs, g);
+  if (a.dc->err != 0) return;
+  const uint32_t P = a.dc->n_train;
+  for (uint32_t base = blockIdx.x * blockDim.x; base < P; base += gridDim.x * blockDim.x) {  // warp-uniform
+    const uint32_t i = base + threadIdx.x;
+    const bool active = i < P;
+    float xs[3] = {0.f, 0.f, 0.f};
+    int blo[3] = {0, 0, 0}, bhi[3] = {-1, -1, -1};
+    int map = 0;
+    if (active) {
+      const float4 p = a.train[i];
+      xs[0] = p.x;
+      xs[1] = p.y;
+      xs[2] = p.z;
+      map = (int)p.w >> kLabelBits;
+      candidate_blocks(xs, g, blo, bhi);
     }
-    const unsigned long long key = hit ? pack_block(bx, by, bz) : kEmpty;
-    const unsigned peers = __match_any_sync(0xffffffffu, key);
-    if (hit && (unsigned)(__ffs(peers) - 1) == (threadIdx.x & 31u)) {
-      const int64_t slot = insert_block(a, key);
-      if (slot >= 0) atomicAdd(&a.hcnt[slot], (uint32_t)__popc(peers));
+    // the warp walks the smallest cube of candidate offsets that covers every lane
+    const int mx = __reduce_max_sync(0xffffffffu, (unsigned)max(0, bhi[0] - blo[0] + 1));
+    const int my = __reduce_max_sync(0xffffffffu, (unsigned)max(0, bhi[1] - blo[1] + 1));
+    const int mz = __reduce_max_sync(0xffffffffu, (unsigned)max(0, bhi[2] - blo[2] + 1));
+    const int nc = mx * my * mz;
+    for (int c = 0; c < nc; ++c) {
+      const int bx = blo[0] + c % mx, by = blo[1] + (c / mx) % my, bz = blo[2] + c / (mx * my);
+      bool hit = bx <= bhi[0] && by <= bhi[1] && bz <= bhi[2];
+      if (hit) {
+        const int K0[3] = {bx << g.B_shift, by << g.B_shift, bz << g.B_shift};
+        hit = touches_block(K0, xs, g);
+      }
+      const unsigned long long key = hit ? pack_block(bx, by, bz, map) : kEmpty;
+      const unsigned peers = __match_any_sync(0xffffffffu, key);
+      if (hit && (unsigned)(__ffs(peers) - 1) == (threadIdx.x & 31u)) {
+        const int64_t slot = insert_block(a, key);
+        if (slot >= 0) atomicAdd(&a.hcnt[slot], (uint32_t)__popc(peers));
+      }
     }
   }
 }
@@ -187,40 +193,46 @@ __global__ void __launch_bounds__(256) touch_kernel(TouchArgs a) {
 // entry of the block's list.
 __global__ void __launch_bounds__(256) bin_fill_kernel(TouchArgs a) {
   const Geom& g = a.g;
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool active = a.dc->err == 0 && i < a.dc->n_train;
-  float xs[3] = {0.f, 0.f, 0.f};
-  int blo[3] = {0, 0, 0}, bhi[3] = {-1, -1, -1};
-  if (active) {
-    const float4 p = a.train[i];
-    xs[0] = p.x;
-    xs[1] = p.y;
-    xs[2] = p.z;
-    candidate_blocks(xs, g, blo, bhi);
-  }
-  const uint32_t lane_lt = (1u << (threadIdx.x & 31u)) - 1u;
-  // the warp walks the smallest cube of candidate offsets that covers every lane
-  const int mx = __reduce_max_sync(0xffffffffu, (unsigned)max(0, bhi[0] - blo[0] + 1));
-  const int my = __reduce_max_sync(0xffffffffu, (unsigned)max(0, bhi[1] - blo[1] + 1));
-  const int mz = __reduce_max_sync(0xffffffffu, (unsigned)max(0, bhi[2] - blo[2] + 1));
-  const int nc = mx * my * mz;
-  for (int c = 0; c < nc; ++c) {
-    const int bx = blo[0] + c % mx, by = blo[1] + (c / mx) % my, bz = blo[2] + c / (mx * my);
-    bool hit = bx <= bhi[0] && by <= bhi[1] && bz <= bhi[2];
-    if (hit) {
-      const int K0[3] = {bx << g.B_shift, by << g.B_shift, bz << g.B_shift};
-      hit = touches_block(K0, xs, g);
+  if (a.dc->err != 0) return;
+  const uint32_t P = a.dc->n_train;
+  for (uint32_t base = blockIdx.x * blockDim.x; base < P; base += gridDim.x * blockDim.x) {  // warp-uniform
+    const uint32_t i = base + threadIdx.x;
+    const bool active = i < P;
+    float xs[3] = {0.f, 0.f, 0.f};
+    int blo[3] = {0, 0, 0}, bhi[3] = {-1, -1, -1};
+    int map = 0;
+    if (active) {
+      const float4 p = a.train[i];
+      xs[0] = p.x;
+      xs[1] = p.y;
+      xs[2] = p.z;
+      map = (int)p.w >> kLabelBits;
+      candidate_blocks(xs, g, blo, bhi);
     }
-    const unsigned long long key = hit ? pack_block(bx, by, bz) : kEmpty;
-    const unsigned peers = __match_any_sync(0xffffffffu, key);
-    const int leader = __ffs(peers) - 1;
-    uint32_t base = 0;
-    if (hit && leader == (int)(threadIdx.x & 31u)) {
-      const int64_t slot = find_block(a, key);
-      base = slot >= 0 ? atomicAdd(&a.hcur[slot], (uint32_t)__popc(peers)) : 0xffffffffu;
+    const uint32_t lane_lt = (1u << (threadIdx.x & 31u)) - 1u;
+    // the warp walks the smallest cube of candidate offsets that covers every lane
+    const int mx = __reduce_max_sync(0xffffffffu, (unsigned)max(0, bhi[0] - blo[0] + 1));
+    const int my = __reduce_max_sync(0xffffffffu, (unsigned)max(0, bhi[1] - blo[1] + 1));
+    const int mz = __reduce_max_sync(0xffffffffu, (unsigned)max(0, bhi[2] - blo[2] + 1));
+    const int nc = mx * my * mz;
+    for (int c = 0; c < nc; ++c) {
+      const int bx = blo[0] + c % mx, by = blo[1] + (c / mx) % my, bz = blo[2] + c / (mx * my);
+      bool hit = bx <= bhi[0] && by <= bhi[1] && bz <= bhi[2];
+      if (hit) {
+        const int K0[3] = {bx << g.B_shift, by << g.B_shift, bz << g.B_shift};
+        hit = touches_block(K0, xs, g);
+      }
+      const unsigned long long key = hit ? pack_block(bx, by, bz, map) : kEmpty;
+      const unsigned peers = __match_any_sync(0xffffffffu, key);
+      const int leader = __ffs(peers) - 1;
+      uint32_t base = 0;
+      if (hit && leader == (int)(threadIdx.x & 31u)) {
+        const int64_t slot = find_block(a, key);
+        base = slot >= 0 ? atomicAdd(&a.hcur[slot], (uint32_t)__popc(peers)) : 0xffffffffu;
+      }
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (hit && base != 0xffffffffu) a.blist[base + __popc(peers & lane_lt)] = i;
     }
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (hit && base != 0xffffffffu) a.blist[base + __popc(peers & lane_lt)] = i;
   }
 }
 
@@ -291,10 +303,9 @@ cudaError_t launch_touch_blocks(MapState& m, const KeyFrame& /*kf*/, int64_t bou
   a.hcnt = m.hcnt;
   a.hcur = m.hcur;
   a.blist = m.blist;
-  a.epoch = m.epoch;
   a.dc = m.dc;
   // bound: the training points never exceed the items of the update
-  const int64_t blocks = std::max<int64_t>(1, (bound + 255) / 256);
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((bound + 255) / 256, (int64_t)m.sm_count * 8));
   touch_kernel<<<(unsigned)blocks, 256, 0, m.stream>>>(a);
   m.launches += 1;
   return cudaGetLastError();
@@ -314,7 +325,6 @@ cudaError_t launch_bin_points(MapState& m, int64_t bound) {
   a.hcnt = m.hcnt;
   a.hcur = m.hcur;
   a.blist = m.blist;
-  a.epoch = m.epoch;
   a.dc = m.dc;
   // touched blocks never exceed 27 per training point nor the hash size
   const int64_t tb = std::min<int64_t>(m.hash_cap, 27 * std::max<int64_t>(bound, 1));
@@ -323,7 +333,7 @@ cudaError_t launch_bin_points(MapState& m, int64_t bound) {
   cudaError_t e = exclusive_scan_u32(m.boff, tb, m.s.scan_tmp, m.stream);
   if (e != cudaSuccess) return e;
   bin_cursor_kernel<<<m.sm_count * 4, 256, 0, m.stream>>>(m.s.touched, m.hcnt, m.hcur, m.boff, m.list_cap, m.dc);
-  const int64_t blocks = std::max<int64_t>(1, (bound + 255) / 256);
+  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((bound + 255) / 256, (int64_t)m.sm_count * 8));
   bin_fill_kernel<<<(unsigned)blocks, 256, 0, m.stream>>>(a);
   m.launches += 1 + 3 + 1 + 1;
   return cudaGetLastError();

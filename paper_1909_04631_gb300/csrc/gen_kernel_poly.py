@@ -10,6 +10,12 @@ Q is approximated by Chebyshev interpolation of degree N at the N+1
 Chebyshev nodes of [0, 1] (values from mpmath at 60 digits), converted to
 monomials in x = 2w - 1 for a Horner evaluation.
 
+The backward pass needs the slope.  In u, f is odd (f = (2 + cos 2 pi u) u/3
+- sin(2 pi u)/(2 pi)), so df/du is even with a fourth-order zero at u = 0:
+    df/dr = -df/du = -u^4 D(u^2),   D(w) = (df/du)(sqrt(w)) / w^2,
+with D analytic on [0, 1] (D(0) = 4 pi^4 / 9, D(1) = 0), interpolated the same
+way (degree ND).
+
 Run:  python gen_kernel_poly.py   (from this directory)
 """
 import os
@@ -19,6 +25,7 @@ import numpy as np
 from numpy.polynomial import chebyshev as Ch
 
 N = 9
+ND = 10
 mp.mp.dps = 60
 
 
@@ -32,31 +39,50 @@ def Q(w):
     return f(1 - u) / u ** 5
 
 
-def coefficients(n=N):
+def dfdu(u):
+    u = mp.mpf(u)
+    return (2 - 2 * mp.cos(2 * mp.pi * u)) / 3 - 2 * mp.pi * u * mp.sin(2 * mp.pi * u) / 3
+
+
+def D(w):
+    u = mp.sqrt(mp.mpf(w))
+    return dfdu(u) / u ** 4
+
+
+def coefficients(fn=Q, n=N):
     k = np.arange(n + 1)
     x = np.cos(np.pi * (k + 0.5) / (n + 1))
-    vals = np.array([float(Q((xi + 1) / 2)) for xi in x])
+    vals = np.array([float(fn((xi + 1) / 2)) for xi in x])
     return Ch.cheb2poly(Ch.chebfit(x, vals, n))
 
 
+def horner(name, c, what):
+    lines = ["// %s" % what,
+             "__device__ __forceinline__ float %s(float w) {" % name,
+             "  const float x = __fmaf_rn(2.0f, w, -1.0f);",
+             "  float acc = %.9ef;" % c[-1]]
+    for a in c[-2::-1]:
+        lines.append("  acc = __fmaf_rn(acc, x, %.9ef);" % a)
+    lines += ["  return acc;", "}", ""]
+    return lines
+
+
 def main():
-    c = coefficients()
     lines = [
         "// Generated by gen_kernel_poly.py - do not edit.",
-        "// Sparse kernel f(r) of Eq. (kernel) as f = u^5 Q(u^2), u = 1 - r, with Q a degree-%d" % N,
-        "// Chebyshev interpolant on w = u^2 in [0, 1], stored as monomials in x = 2w - 1.",
+        "// Sparse kernel f(r) of Eq. (kernel) as f = u^5 Q(u^2) and its slope as",
+        "// df/dr = -u^4 D(u^2), u = 1 - r, with Q and D Chebyshev interpolants on",
+        "// w = u^2 in [0, 1], stored as monomials in x = 2w - 1.",
         "#pragma once",
         "",
         "namespace sbki {",
         "",
         "constexpr int kPolyDegree = %d;" % N,
-        "__device__ __forceinline__ float kernel_q(float w) {",
-        "  const float x = __fmaf_rn(2.0f, w, -1.0f);",
-        "  float acc = %.9ef;" % c[-1],
+        "constexpr int kSlopeDegree = %d;" % ND,
     ]
-    for a in c[-2::-1]:
-        lines.append("  acc = __fmaf_rn(acc, x, %.9ef);" % a)
-    lines += ["  return acc;", "}", "", "}  // namespace sbki", ""]
+    lines += horner("kernel_q", coefficients(Q, N), "Q(w), degree %d" % N)
+    lines += horner("kernel_dq", coefficients(D, ND), "D(w), degree %d" % ND)
+    lines += ["}  // namespace sbki", ""]
     out = os.path.join(os.path.dirname(os.path.abspath(__file__)), "kernel_poly.cuh")
     with open(out, "w") as fh:
         fh.write("\n".join(lines))

@@ -21,23 +21,19 @@ namespace {
 constexpr unsigned long long kValidOne = 1ull << 40;
 constexpr unsigned long long kFreeMask = kValidOne - 1;
 
-struct Pose {
-  double r[9];
-  double t[3];
-  float o[3];
-};
 
 __device__ __forceinline__ int floor_i(float v) { return (int)floorf(v); }
 
-// sort key: [rel tile x | rel tile y | rel tile z | local cell (z,y,x) | label]
+// sort key: [scan | rel tile x | rel tile y | rel tile z | local cell (z,y,x) | label]
 __device__ __forceinline__ unsigned long long make_key(float x, float y, float z, int label, const Geom& g,
-                                                       const KeyFrame& kf, DevCounters* dc) {
+                                                       const KeyFrame& kf, const int32_t org[3], int scan,
+                                                       DevCounters* dc) {
   int gx = floor_i(__fmul_rn(x, g.inv_ds));
   int gy = floor_i(__fmul_rn(y, g.inv_ds));
   int gz = floor_i(__fmul_rn(z, g.inv_ds));
-  int tx = (gx >> kTileShift) - kf.org[0];
-  int ty = (gy >> kTileShift) - kf.org[1];
-  int tz = (gz >> kTileShift) - kf.org[2];
+  int tx = (gx >> kTileShift) - org[0];
+  int ty = (gy >> kTileShift) - org[1];
+  int tz = (gz >> kTileShift) - org[2];
   const int lim = 1 << kf.bits;
   if (tx < 0 || ty < 0 || tz < 0 || tx >= lim || ty >= lim || tz >= lim) {
     set_error(dc, SBKI_ERR_INVALID_ARG);
@@ -47,7 +43,28 @@ __device__ __forceinline__ unsigned long long make_key(float x, float y, float z
                             (unsigned long long)tz;
   unsigned long long local = (unsigned long long)(((gz & (kTileEdge - 1)) << (2 * kTileShift)) |
                                                   ((gy & (kTileEdge - 1)) << kTileShift) | (gx & (kTileEdge - 1)));
-  return (((tile << kLocalBits) | local) << g.label_bits) | (unsigned long long)label;
+  const unsigned long long k = (((tile << kLocalBits) | local) << g.label_bits) | (unsigned long long)label;
+  return kf.scan_bits ? (k | ((unsigned long long)scan << kf.total_bits)) : k;
+}
+__device__ __forceinline__ unsigned long long make_key(float x, float y, float z, int label, const Geom& g,
+                                                       const KeyFrame& kf, DevCounters* dc) {
+  return make_key(x, y, z, label, g, kf, kf.org, 0, dc);
+}
+
+// scan of global point gi: the last s with off[s] <= gi (empty scans are skipped)
+__device__ __forceinline__ int scan_of(const int64_t* off, int ns, int64_t gi) {
+  int lo = 0, hi = ns - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= gi) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// the map index a training point's segment belongs to
+__device__ __forceinline__ int map_of_segment(unsigned long long key, const KeyFrame& kf, const ScanDesc* desc) {
+  return desc[kf.scan_bits ? (int)(key >> kf.total_bits) : 0].map_id;
 }
 
 // number of j >= 1 with fp32(j) * s < r  (the set is a prefix since fp32(j)*s is monotone in j)
@@ -60,13 +77,13 @@ __device__ __forceinline__ uint32_t free_count(float r, float s) {
   return (uint32_t)(j < 0 ? 0 : j);
 }
 
-__global__ void transform_count_kernel(const float* __restrict__ pts, const int32_t* __restrict__ labels, int64_t n,
-                                       Pose pose, Geom g, float4* __restrict__ world,
-                                       unsigned long long* __restrict__ cnt, DevCounters* dc) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const float px = pts[3 * i], py = pts[3 * i + 1], pz = pts[3 * i + 2];
-  const int lab = labels[i];
+// a1 for global point i of scan d
+__device__ __forceinline__ void transform_count_one(const ScanDesc& d, int64_t i, const int64_t* off, const Geom& g,
+                                                    float4* __restrict__ world, unsigned long long* __restrict__ cnt,
+                                                    DevCounters* dc) {
+  const int64_t li = i - d.off;
+  const float px = d.pts[3 * li], py = d.pts[3 * li + 1], pz = d.pts[3 * li + 2];
+  const int lab = d.labels[li];
   if (lab < 1 || lab > g.K1 - 1) set_error(dc, SBKI_ERR_LABEL_RANGE);
   bool ok = isfinite(px) && isfinite(py) && isfinite(pz);
   unsigned long long c = 0;
@@ -79,15 +96,15 @@ __global__ void transform_count_kernel(const float* __restrict__ pts, const int3
       float wc[3];
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
-        double acc = __dmul_rn(pose.r[3 * r], dx);
-        acc = __dadd_rn(acc, __dmul_rn(pose.r[3 * r + 1], dy));
-        acc = __dadd_rn(acc, __dmul_rn(pose.r[3 * r + 2], dz));
-        acc = __dadd_rn(acc, pose.t[r]);
+        double acc = __dmul_rn(d.r[3 * r], dx);
+        acc = __dadd_rn(acc, __dmul_rn(d.r[3 * r + 1], dy));
+        acc = __dadd_rn(acc, __dmul_rn(d.r[3 * r + 2], dz));
+        acc = __dadd_rn(acc, d.t[r]);
         wc[r] = __double2float_rn(acc);
       }
-      const float ex = __fsub_rn(wc[0], pose.o[0]);
-      const float ey = __fsub_rn(wc[1], pose.o[1]);
-      const float ez = __fsub_rn(wc[2], pose.o[2]);
+      const float ex = __fsub_rn(wc[0], d.o[0]);
+      const float ey = __fsub_rn(wc[1], d.o[1]);
+      const float ez = __fsub_rn(wc[2], d.o[2]);
       const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez));
       const float rr = __fsqrt_rn(r2);
       c = kValidOne | (unsigned long long)free_count(rr, g.step);
@@ -98,8 +115,21 @@ __global__ void transform_count_kernel(const float* __restrict__ pts, const int3
   cnt[i] = c;
 }
 
-__global__ void check_counts_kernel(const unsigned long long* cnt, int64_t n, int64_t cap, DevCounters* dc) {
-  const unsigned long long tot = cnt[n];
+// Steps a1 (and the free-sample counts of a2) for every point of every scan
+// of the update; points are numbered globally, scan after scan.
+__global__ void __launch_bounds__(256) transform_count_kernel(const ScanDesc* __restrict__ desc, int ns, Geom g,
+                                                               float4* __restrict__ world,
+                                                               unsigned long long* __restrict__ cnt, DevCounters* dc) {
+  __shared__ int64_t s_off[kMaxScans + 1];
+  for (int t = threadIdx.x; t <= ns; t += blockDim.x) s_off[t] = desc[t].off;
+  __syncthreads();
+  const int64_t total = s_off[ns];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+    transform_count_one(desc[scan_of(s_off, ns, i)], i, s_off, g, world, cnt, dc);
+}
+
+__global__ void check_counts_kernel(const unsigned long long* cnt, int64_t cap, DevCounters* dc) {
+  const unsigned long long tot = cnt[dc->n_points];
   const uint32_t nv = (uint32_t)(tot >> 40);
   const unsigned long long nf = tot & kFreeMask;
   dc->n_valid = nv;
@@ -113,30 +143,44 @@ __global__ void check_counts_kernel(const unsigned long long* cnt, int64_t n, in
   }
 }
 
-// one warp per 32 input points; the warp writes each beam's samples together
+// Step a2 for every scan of the update: one warp per 32 consecutive points
+// (which may belong to different scans); the warp writes each beam's samples
+// together.  Hits go to items [0, hits), free samples after all hits.
 __global__ void __launch_bounds__(256) emit_kernel(const float4* __restrict__ world,
-                                                   const unsigned long long* __restrict__ cnt, int64_t n, Pose pose,
-                                                   Geom g, KeyFrame kf, float4* __restrict__ items,
-                                                   unsigned long long* __restrict__ keys, uint32_t* __restrict__ vals,
-                                                   DevCounters* dc) {
+                                                   const unsigned long long* __restrict__ cnt,
+                                                   const ScanDesc* __restrict__ desc, int ns, Geom g, KeyFrame kf,
+                                                   float4* __restrict__ items, unsigned long long* __restrict__ keys,
+                                                   uint32_t* __restrict__ vals, DevCounters* dc) {
+  __shared__ int64_t s_off[kMaxScans + 1];
+  for (int t = threadIdx.x; t <= ns; t += blockDim.x) s_off[t] = desc[t].off;
+  __syncthreads();
   if (dc->err) return;
+  const int64_t n = s_off[ns];
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const unsigned long long nvalid = cnt[n] >> 40;
-  const float ox = pose.o[0], oy = pose.o[1], oz = pose.o[2];
   for (int64_t base = warp * 32; base < n; base += nwarps * 32) {
     const int64_t i = base + lane;
     uint32_t nfree = 0;
     unsigned long long fpos = 0;
-    float ex = 0.f, ey = 0.f, ez = 0.f, rr = 0.f;
+    float ex = 0.f, ey = 0.f, ez = 0.f, rr = 0.f, ox = 0.f, oy = 0.f, oz = 0.f;
+    int sc = 0, og[3] = {0, 0, 0};
     if (i < n) {
+      sc = scan_of(s_off, ns, i);
+      const ScanDesc& d = desc[sc];
+      ox = d.o[0];
+      oy = d.o[1];
+      oz = d.o[2];
+      og[0] = d.org[0];
+      og[1] = d.org[1];
+      og[2] = d.org[2];
       const unsigned long long c0 = cnt[i], c1 = cnt[i + 1];
       if ((c1 >> 40) != (c0 >> 40)) {  // a kept hit
         const float4 w = world[i];
         const unsigned long long hpos = c0 >> 40;
         items[hpos] = w;
-        keys[hpos] = make_key(w.x, w.y, w.z, (int)w.w, g, kf, dc);
+        keys[hpos] = make_key(w.x, w.y, w.z, (int)w.w, g, kf, og, sc, dc);
         vals[hpos] = (uint32_t)hpos;
         nfree = (uint32_t)((c1 & kFreeMask) - (c0 & kFreeMask));
         fpos = nvalid + (c0 & kFreeMask);
@@ -153,38 +197,48 @@ __global__ void __launch_bounds__(256) emit_kernel(const float4* __restrict__ wo
       const float sy = __shfl_sync(0xffffffffu, ey, src);
       const float sz = __shfl_sync(0xffffffffu, ez, src);
       const float sr = __shfl_sync(0xffffffffu, rr, src);
+      const float qx = __shfl_sync(0xffffffffu, ox, src);
+      const float qy = __shfl_sync(0xffffffffu, oy, src);
+      const float qz = __shfl_sync(0xffffffffu, oz, src);
+      const int32_t sorg[3] = {__shfl_sync(0xffffffffu, og[0], src), __shfl_sync(0xffffffffu, og[1], src),
+                               __shfl_sync(0xffffffffu, og[2], src)};
+      const int ssc = __shfl_sync(0xffffffffu, sc, src);
       const unsigned long long sp = __shfl_sync(0xffffffffu, fpos, src);
       for (uint32_t j = lane + 1; j <= m; j += 32) {
         const float t = __fsub_rn(sr, __fmul_rn((float)j, g.step));
         const float q = __fdiv_rn(t, sr);
-        const float x = __fadd_rn(ox, __fmul_rn(sx, q));
-        const float y = __fadd_rn(oy, __fmul_rn(sy, q));
-        const float z = __fadd_rn(oz, __fmul_rn(sz, q));
+        const float x = __fadd_rn(qx, __fmul_rn(sx, q));
+        const float y = __fadd_rn(qy, __fmul_rn(sy, q));
+        const float z = __fadd_rn(qz, __fmul_rn(sz, q));
         const unsigned long long pos = sp + j - 1;
         items[pos] = make_float4(x, y, z, 0.f);
-        keys[pos] = make_key(x, y, z, 0, g, kf, dc);
+        keys[pos] = make_key(x, y, z, 0, g, kf, sorg, ssc, dc);
         vals[pos] = (uint32_t)pos;
       }
     }
   }
 }
 
-__global__ void seg_flags_kernel(const unsigned long long* __restrict__ keys, int64_t n, uint32_t* __restrict__ flags,
+// segment heads of the sorted items (count read on the device, at most cap)
+__global__ void seg_flags_kernel(const unsigned long long* __restrict__ keys, int64_t cap, uint32_t* __restrict__ flags,
                                  const DevCounters* dc) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n || dc->err) return;
-  flags[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1u : 0u;
+  if (dc->err) return;
+  const int64_t n = min(cap, (int64_t)dc->n_items);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    flags[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1u : 0u;
 }
 
-__global__ void seg_start_kernel(const unsigned long long* __restrict__ keys, int64_t n,
+__global__ void seg_start_kernel(const unsigned long long* __restrict__ keys, int64_t cap,
                                  const uint32_t* __restrict__ segid, uint32_t* __restrict__ seg_start,
                                  DevCounters* dc) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n || dc->err) return;
-  if (i == 0 || keys[i] != keys[i - 1]) seg_start[segid[i]] = (uint32_t)i;
-  if (i == n - 1) {
-    seg_start[segid[n]] = (uint32_t)n;
-    dc->n_train = segid[n];
+  if (dc->err) return;
+  const int64_t n = min(cap, (int64_t)dc->n_items);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (i == 0 || keys[i] != keys[i - 1]) seg_start[segid[i]] = (uint32_t)i;
+    if (i == n - 1) {
+      seg_start[segid[n]] = (uint32_t)n;
+      dc->n_train = segid[n];
+    }
   }
 }
 
@@ -384,17 +438,15 @@ __global__ void __launch_bounds__(256) centroid_kernel(const unsigned long long*
                                                        const uint32_t* __restrict__ perm,
                                                        const float4* __restrict__ items,
                                                        const uint32_t* __restrict__ seg_start, Geom g,
-                                                       float4* __restrict__ train, uint32_t* __restrict__ tflags,
-                                                       uint32_t nbound, uint32_t* __restrict__ huge,
+                                                       float4* __restrict__ train, const ScanDesc* __restrict__ desc,
+                                                       KeyFrame kf, uint32_t* __restrict__ huge,
                                                        uint32_t* __restrict__ mid, DevCounters* dc) {
   if (dc->err) return;
   const uint32_t P = dc->n_train;
   const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t nthreads = gridDim.x * blockDim.x;
-  for (uint32_t s = P + gtid; s < nbound; s += nthreads) tflags[s] = 0u;  // keep the tile-head scan exact
   const int lane = threadIdx.x & 31;
   const uint32_t warp = gtid >> 5, nwarps = nthreads >> 5;
-  const int tshift = kLocalBits + g.label_bits;
   for (uint32_t base = warp * 32; base < P; base += nwarps * 32) {
     const uint32_t s = base + lane;
     const bool valid = s < P;
@@ -433,8 +485,7 @@ __global__ void __launch_bounds__(256) centroid_kernel(const unsigned long long*
       float out[3];
 #pragma unroll
       for (int c = 0; c < 3; ++c) out[c] = finish_axis(ax[c], fit[c], T[c], n, items, perm, a, b, c);
-      train[s] = make_float4(out[0], out[1], out[2], (float)label);
-      tflags[s] = (s == 0 || (k >> tshift) != (keys[seg_start[s - 1]] >> tshift)) ? 1u : 0u;
+      train[s] = make_float4(out[0], out[1], out[2], (float)(label + 32 * map_of_segment(k, kf, desc)));
     }
   }
 }
@@ -446,13 +497,13 @@ __global__ void __launch_bounds__(256) mid_centroid_kernel(const unsigned long l
                                                            const uint32_t* __restrict__ perm,
                                                            const float4* __restrict__ items,
                                                            const uint32_t* __restrict__ seg_start, Geom g,
-                                                           float4* __restrict__ train, uint32_t* __restrict__ tflags,
+                                                           float4* __restrict__ train,
+                                                           const ScanDesc* __restrict__ desc, KeyFrame kf,
                                                            const uint32_t* __restrict__ mid, DevCounters* dc) {
   if (dc->err) return;
   const uint32_t nm = dc->n_mid;
   const int lane = threadIdx.x & 31;
   const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
-  const int tshift = kLocalBits + g.label_bits;
   for (uint32_t j = warp; j < nm; j += nwarps) {
     const uint32_t s = mid[j];
     const uint32_t a = seg_start[s], b = seg_start[s + 1], n = b - a;
@@ -487,8 +538,7 @@ __global__ void __launch_bounds__(256) mid_centroid_kernel(const unsigned long l
       for (int c = 0; c < 3; ++c) out[c] = finish_axis(w[c], fit[c], t[c], n, items, perm, a, b, c);
       const unsigned long long k = keys[a];
       const int label = (int)(k & ((1ull << g.label_bits) - 1));
-      train[s] = make_float4(out[0], out[1], out[2], (float)label);
-      tflags[s] = (s == 0 || (k >> tshift) != (keys[seg_start[s - 1]] >> tshift)) ? 1u : 0u;
+      train[s] = make_float4(out[0], out[1], out[2], (float)(label + 32 * map_of_segment(k, kf, desc)));
     }
   }
 }
@@ -499,14 +549,14 @@ __global__ void __launch_bounds__(256) huge_centroid_kernel(const unsigned long 
                                                             const uint32_t* __restrict__ perm,
                                                             const float4* __restrict__ items,
                                                             const uint32_t* __restrict__ seg_start, Geom g,
-                                                            float4* __restrict__ train, uint32_t* __restrict__ tflags,
+                                                            float4* __restrict__ train,
+                                                            const ScanDesc* __restrict__ desc, KeyFrame kf,
                                                             const uint32_t* __restrict__ huge, DevCounters* dc) {
   __shared__ int s_emin[3][8], s_emax[3][8], s_neg[3][8];
   __shared__ unsigned long long s_lo[3][8], s_hi[3][8];
   if (dc->err) return;
   const uint32_t nh = dc->n_huge;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int tshift = kLocalBits + g.label_bits;
   for (uint32_t h = blockIdx.x; h < nh; h += gridDim.x) {
     const uint32_t s = huge[h];
     const uint32_t a = seg_start[s], b = seg_start[s + 1], n = b - a;
@@ -579,30 +629,9 @@ __global__ void __launch_bounds__(256) huge_centroid_kernel(const unsigned long 
       }
       const unsigned long long k = keys[a];
       const int label = (int)(k & ((1ull << g.label_bits) - 1));
-      train[s] = make_float4(out[0], out[1], out[2], (float)label);
-      tflags[s] = (s == 0 || (k >> tshift) != (keys[seg_start[s - 1]] >> tshift)) ? 1u : 0u;
+      train[s] = make_float4(out[0], out[1], out[2], (float)(label + 32 * map_of_segment(k, kf, desc)));
     }
     __syncthreads();
-  }
-}
-
-// tile list: tile_key[t] (relative packed tile), tile_start[t] (first training point)
-__global__ void tile_list_kernel(const unsigned long long* __restrict__ keys, const uint32_t* __restrict__ seg_start,
-                                 const uint32_t* __restrict__ tid, Geom g, unsigned long long* __restrict__ tile_key,
-                                 uint32_t* __restrict__ tile_start, DevCounters* dc) {
-  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-  const uint32_t P = dc->n_train;
-  if (dc->err || s >= P) return;
-  const int tshift = kLocalBits + g.label_bits;
-  const unsigned long long tk = keys[seg_start[s]] >> tshift;
-  const bool head = (s == 0) || (tk != (keys[seg_start[s - 1]] >> tshift));
-  if (head) {
-    tile_key[tid[s]] = tk;
-    tile_start[tid[s]] = s;
-  }
-  if (s == P - 1) {
-    tile_start[tid[P]] = P;
-    dc->n_tiles = tid[P];
   }
 }
 
@@ -642,78 +671,70 @@ __global__ void train_keys_kernel(const float4* __restrict__ in, int64_t p, Geom
   vals[i] = (uint32_t)i;
 }
 
-// every point is its own segment; gather into tile order and flag tile heads
-__global__ void train_gather_kernel(const float4* __restrict__ in, const unsigned long long* __restrict__ keys,
-                                    const uint32_t* __restrict__ perm, int64_t p, Geom g,
-                                    float4* __restrict__ train, uint32_t* __restrict__ seg_start,
-                                    uint32_t* __restrict__ tflags, DevCounters* dc) {
+// every point is its own segment; gather into tile order, tag the map index
+__global__ void train_gather_kernel(const float4* __restrict__ in, const uint32_t* __restrict__ perm, int64_t p,
+                                    int map_id, float4* __restrict__ train, uint32_t* __restrict__ seg_start,
+                                    DevCounters* dc) {
   int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= p || dc->err) return;
-  train[s] = in[perm[s]];
+  float4 v = in[perm[s]];
+  v.w = __fadd_rn(v.w, (float)(32 * map_id));  // exact: label < 32, map < 64
+  train[s] = v;
   seg_start[s] = (uint32_t)s;
-  const int tshift = kLocalBits + g.label_bits;
-  tflags[s] = (s == 0 || (keys[s] >> tshift) != (keys[s - 1] >> tshift)) ? 1u : 0u;
   if (s == p - 1) {
     seg_start[p] = (uint32_t)p;
     dc->n_train = (uint32_t)p;
   }
 }
 
-Pose make_pose(const double T[16]) {
-  Pose p;
-  for (int r = 0; r < 3; ++r) {
-    for (int c = 0; c < 3; ++c) p.r[3 * r + c] = T[4 * r + c];
-    p.t[r] = T[4 * r + 3];
-    p.o[r] = (float)T[4 * r + 3];
-  }
-  return p;
-}
-
 inline unsigned grid_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
 }  // namespace
 
-cudaError_t launch_transform_count(MapState& m, const float* pts, const int32_t* labels, int64_t n,
-                                   const double* /*unused*/, const double pose[16], const KeyFrame& /*kf*/) {
-  Pose P = make_pose(pose);
-  transform_count_kernel<<<grid_for(n, 256), 256, 0, m.stream>>>(pts, labels, n, P, m.g, m.s.world, m.s.cnt, m.dc);
+// Steps a1-a2 count for the ns scans described in m.s.desc; total_n bounds the
+// point count, which the kernels read on the device (dc->n_points, desc[ns].off).
+cudaError_t launch_transform_count(MapState& m, int ns, int64_t total_n) {
+  const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(total_n, 256), (int64_t)m.sm_count * 16));
+  transform_count_kernel<<<blocks, 256, 0, m.stream>>>(m.s.desc, ns, m.g, m.s.world, m.s.cnt, m.dc);
   m.launches += 1 + 3 + 1;  // transform, scan, check
-  cudaError_t e = exclusive_scan_u64(m.s.cnt, n, m.s.scan_tmp, m.stream);
+  cudaError_t e = exclusive_scan_u64(m.s.cnt, total_n, m.s.scan_tmp, m.stream, &m.dc->n_points);
   if (e != cudaSuccess) return e;
-  check_counts_kernel<<<1, 1, 0, m.stream>>>(m.s.cnt, n, m.s.s_cap, m.dc);
+  check_counts_kernel<<<1, 1, 0, m.stream>>>(m.s.cnt, m.s.s_cap, m.dc);
   return cudaGetLastError();
 }
 
-cudaError_t launch_emit(MapState& m, int64_t n, const double pose[16], const KeyFrame& kf) {
-  Pose P = make_pose(pose);
-  int64_t warps = (n + 31) / 32;
+cudaError_t launch_emit(MapState& m, int ns, int64_t total_n, const KeyFrame& kf) {
+  const int64_t warps = (total_n + 31) / 32;
   unsigned blocks = (unsigned)std::min<int64_t>((warps + 7) / 8, (int64_t)m.sm_count * 16);
   if (blocks == 0) blocks = 1;
-  emit_kernel<<<blocks, 256, 0, m.stream>>>(m.s.world, m.s.cnt, n, P, m.g, kf, m.s.items, m.s.keys, m.s.vals, m.dc);
+  emit_kernel<<<blocks, 256, 0, m.stream>>>(m.s.world, m.s.cnt, m.s.desc, ns, m.g, kf, m.s.items, m.s.keys, m.s.vals,
+                                            m.dc);
   m.launches += 1;
   return cudaGetLastError();
 }
 
-// Sorts the items and reduces each (cell, label) segment to its centroid; builds the tile list.
-// Host-known item count nitems (read back after the count step).
+// Sorts the items and reduces each (scan, cell, label) segment to its centroid.
+// nitems: host-known bound on the item count (the count itself is read on the device).
 cudaError_t launch_downsample_n(MapState& m, const KeyFrame& kf, int64_t nitems) {
   Scratch& s = m.s;
-  m.launches += 5 * ((kf.total_bits + 7) / 8) + 1 + 3 + 1 + 3;  // sort, segments, centroids
-  cudaError_t e = radix_sort_pairs(s.keys, s.vals, s.keys2, s.vals2, &m.dc->n_items, nitems, kf.total_bits, s.hist,
-                                   s.scan_tmp, m.dc, m.stream);
+  const int bits = kf.total_bits + kf.scan_bits;
+  m.launches += 1 + (bits + 7) / 8 + 1 + 3 + 1 + 3;  // sort, segments, centroids
+  cudaError_t e = radix_sort_pairs(s.keys, s.vals, s.keys2, s.vals2, &m.dc->n_items, nitems, bits, s.hist,
+                                   m.sm_count, m.dc, m.stream);
   if (e != cudaSuccess) return e;
-  seg_flags_kernel<<<grid_for(nitems, 256), 256, 0, m.stream>>>(s.keys, nitems, s.flags, m.dc);
-  e = exclusive_scan_u32(s.flags, nitems, s.scan_tmp, m.stream);
+  const unsigned sblocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(nitems, 256), (int64_t)m.sm_count * 16));
+  seg_flags_kernel<<<sblocks, 256, 0, m.stream>>>(s.keys, nitems, s.flags, m.dc);
+  e = exclusive_scan_u32(s.flags, nitems, s.scan_tmp, m.stream, &m.dc->n_items);
   if (e != cudaSuccess) return e;
-  seg_start_kernel<<<grid_for(nitems, 256), 256, 0, m.stream>>>(s.keys, nitems, s.flags, s.seg_start, m.dc);
+  seg_start_kernel<<<sblocks, 256, 0, m.stream>>>(s.keys, nitems, s.flags, s.seg_start, m.dc);
   {
     const unsigned cblocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((nitems + 255) / 256, (int64_t)m.sm_count * 16));
-    centroid_kernel<<<cblocks, 256, 0, m.stream>>>(s.keys, s.vals, s.items, s.seg_start, m.g, s.train, s.tflags,
-                                                   (uint32_t)nitems, s.huge, s.mid, m.dc);
+    centroid_kernel<<<cblocks, 256, 0, m.stream>>>(s.keys, s.vals, s.items, s.seg_start, m.g, s.train, s.desc, kf,
+                                                   s.huge, s.mid, m.dc);
     mid_centroid_kernel<<<(unsigned)m.sm_count * 8, 256, 0, m.stream>>>(s.keys, s.vals, s.items, s.seg_start, m.g,
-                                                                        s.train, s.tflags, s.mid, m.dc);
+                                                                        s.train, s.desc, kf, s.mid, m.dc);
     huge_centroid_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(nitems / kHuge + 1, 1024)), 256, 0,
-                           m.stream>>>(s.keys, s.vals, s.items, s.seg_start, m.g, s.train, s.tflags, s.huge, m.dc);
+                           m.stream>>>(s.keys, s.vals, s.items, s.seg_start, m.g, s.train, s.desc, kf, s.huge, m.dc);
   }
   return cudaGetLastError();
 }
@@ -726,13 +747,13 @@ cudaError_t launch_train_bbox(MapState& m, const float4* in, int64_t p, int* bbo
 
 cudaError_t launch_train_prepare(MapState& m, const float4* in, int64_t p, const KeyFrame& kf) {
   Scratch& s = m.s;
-  m.launches += 1 + 5 * ((kf.total_bits + 7) / 8) + 1;
+  m.launches += 1 + 1 + (kf.total_bits + 7) / 8 + 1;
   train_keys_kernel<<<grid_for(p, 256), 256, 0, m.stream>>>(in, p, m.g, kf, s.keys, s.vals, m.dc);
   cudaError_t e = radix_sort_pairs(s.keys, s.vals, s.keys2, s.vals2, &m.dc->n_items, p, kf.total_bits, s.hist,
-                                   s.scan_tmp, m.dc, m.stream);
+                                   m.sm_count, m.dc, m.stream);
   if (e != cudaSuccess) return e;
-  train_gather_kernel<<<grid_for(p, 256), 256, 0, m.stream>>>(in, s.keys, s.vals, p, m.g, s.train, s.seg_start,
-                                                               s.tflags, m.dc);
+  train_gather_kernel<<<grid_for(p, 256), 256, 0, m.stream>>>(in, s.vals, p, m.active_map, s.train, s.seg_start,
+                                                               m.dc);
   return cudaGetLastError();
 }
 

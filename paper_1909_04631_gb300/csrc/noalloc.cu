@@ -9,13 +9,13 @@
 // may synchronise the whole device).  Such a caller passes device buffers for
 // the inputs and the output; every intermediate buffer of the computation
 // (transformed points, sample counts, items, radix-sort keys and values,
-// segment and tile tables, scan partials, device counters) lives in one
+// segment tables, scan partials, the scan descriptor, device counters) lives in one
 // file-scope device array of fixed size, so calling this allocates nothing.
 //
 // Limits: at most kMaxPoints input points and kMaxItems hits + free samples
 // per call; larger inputs are rejected with SBKI_ERR_INVALID_ARG (points) or
 // SBKI_ERR_CAPACITY (items, known only after counting on the device).  The
-// array (kScratchBytes, about 9.4 MB) is reserved on every device that loads
+// array (kScratchBytes, about 8.9 MB) is reserved on every device that loads
 // the library, for the life of the process.  All calls share it and it keeps
 // the last call's contents; the device counters are cleared at the start of
 // each call, every other buffer is written before it is read.  Calls whose
@@ -47,14 +47,14 @@ constexpr size_t kOffVals2 = align256(kOffVals + 4 * kMaxItems);
 constexpr size_t kOffFlags = align256(kOffVals2 + 4 * kMaxItems);
 constexpr size_t kOffSeg = align256(kOffFlags + 4 * (kMaxItems + 1));
 constexpr size_t kOffTrain = align256(kOffSeg + 4 * (kMaxItems + 1));
-constexpr size_t kOffTflags = align256(kOffTrain + 16 * kMaxItems);
-constexpr size_t kOffMid = align256(kOffTflags + 4 * (kMaxItems + 1));
+constexpr size_t kOffMid = align256(kOffTrain + 16 * kMaxItems);
 constexpr size_t kOffHuge = align256(kOffMid + 4 * (kMaxItems / 16 + 2));
-constexpr size_t kHistEntries = 256 * ((kMaxItems + 4095) / 4096) + 1;
+constexpr size_t kHistEntries = (size_t)sbki::radix_work_entries(kMaxItems);
 constexpr size_t kOffHist = align256(kOffHuge + 4 * (kMaxItems / 1024 + 2));
 constexpr size_t kOffScanTmp = align256(kOffHist + 4 * kHistEntries);
 constexpr size_t kScanTmpBytes = 8 * ((kMaxItems + 2) / 2048 + 64);  // partial sums of the largest scan
-constexpr size_t kScratchBytes = align256(kOffScanTmp + kScanTmpBytes);
+constexpr size_t kOffDesc = align256(kOffScanTmp + kScanTmpBytes);
+constexpr size_t kScratchBytes = align256(kOffDesc + 2 * sizeof(sbki::ScanDesc));
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -151,12 +151,12 @@ sbki_status run(const sbki_params* params, const float* points, const int32_t* l
   s.flags = reinterpret_cast<uint32_t*>(base + kOffFlags);
   s.seg_start = reinterpret_cast<uint32_t*>(base + kOffSeg);
   s.train = reinterpret_cast<float4*>(base + kOffTrain);
-  s.tflags = reinterpret_cast<uint32_t*>(base + kOffTflags);
   s.mid = reinterpret_cast<uint32_t*>(base + kOffMid);
   s.huge = reinterpret_cast<uint32_t*>(base + kOffHuge);
   s.hist = reinterpret_cast<uint32_t*>(base + kOffHist);
   s.hist_cap = (int64_t)kHistEntries;
   s.scan_tmp = base + kOffScanTmp;
+  s.desc = reinterpret_cast<ScanDesc*>(base + kOffDesc);
   s.s_cap = kMaxItems;
 
   int prev = -1;
@@ -171,8 +171,23 @@ sbki_status run(const sbki_params* params, const float* points, const int32_t* l
 
   // the counters must start at zero; every other buffer is written before it is read
   CKN(cudaMemsetAsync(m.dc, 0, sizeof(DevCounters), m.stream));
+  const uint32_t np = (uint32_t)n;
+  CKN(cudaMemcpyAsync(&m.dc->n_points, &np, sizeof(np), cudaMemcpyHostToDevice, m.stream));
   const KeyFrame kf = frame_of_scan(m, pose);
-  CKN(launch_transform_count(m, points, labels, n, nullptr, pose, kf));
+  ScanDesc hd[2];  // this scan, then the end marker holding the point count
+  memset(hd, 0, sizeof(hd));
+  hd[0].pts = points;
+  hd[0].labels = labels;
+  hd[0].n = n;
+  for (int r = 0; r < 3; ++r) {
+    for (int c = 0; c < 3; ++c) hd[0].r[3 * r + c] = pose[4 * r + c];
+    hd[0].t[r] = pose[4 * r + 3];
+    hd[0].o[r] = (float)pose[4 * r + 3];
+    hd[0].org[r] = kf.org[r];
+  }
+  hd[1].off = n;
+  CKN(cudaMemcpyAsync(s.desc, hd, sizeof(hd), cudaMemcpyHostToDevice, m.stream));
+  CKN(launch_transform_count(m, 1, n));
   DevCounters h;
   CKN(cudaMemcpyAsync(&h, m.dc, sizeof(h), cudaMemcpyDeviceToHost, m.stream));
   CKN(cudaStreamSynchronize(m.stream));
@@ -182,7 +197,7 @@ sbki_status run(const sbki_params* params, const float* points, const int32_t* l
   if (h.err != 0) return fail((sbki_status)h.err, "training set without allocation: device error");
   const int64_t nitems = h.n_items;
   if (nitems > 0) {
-    CKN(launch_emit(m, n, pose, kf));
+    CKN(launch_emit(m, 1, n, kf));
     CKN(launch_downsample_n(m, kf, nitems));
     CKN(cudaMemcpyAsync(&h, m.dc, sizeof(h), cudaMemcpyDeviceToHost, m.stream));
     CKN(cudaStreamSynchronize(m.stream));

@@ -26,6 +26,7 @@ struct QueryArgs {
   int32_t* label;
   float* p_occ;
   int32_t* state;
+  int map;
 };
 
 __device__ int32_t lookup_block(const QueryArgs& a, unsigned long long key) {
@@ -55,7 +56,7 @@ __global__ void __launch_bounds__(256) query_kernel(QueryArgs a) {
   int32_t pool = -1;
   int local = 0;
   if (inside) {
-    pool = lookup_block(a, pack_block(v[0] >> g.B_shift, v[1] >> g.B_shift, v[2] >> g.B_shift));
+    pool = lookup_block(a, pack_block(v[0] >> g.B_shift, v[1] >> g.B_shift, v[2] >> g.B_shift, a.map));
     const int m = g.B - 1;
     local = (((v[2] & m) << g.B_shift) + (v[1] & m)) * g.B + (v[0] & m);
   }
@@ -115,6 +116,7 @@ cudaError_t launch_query(const MapState& m, const float* xyz, int64_t q, float* 
   a.label = label;
   a.p_occ = p_occ;
   a.state = state;
+  a.map = m.active_map;
   query_kernel<<<(unsigned)((q + 255) / 256), 256, 0, m.stream>>>(a);
   return cudaGetLastError();
 }

@@ -84,7 +84,8 @@ cudaError_t dalloc(T** p, size_t count) {
   return cudaMalloc((void**)p, sizeof(T) * count);
 }
 
-__global__ void begin_kernel(DevCounters* dc, uint32_t epoch) {
+__global__ void begin_kernel(DevCounters* dc, uint32_t epoch, uint32_t n_points) {
+  dc->n_points = n_points;
   dc->pairs = 0;
   dc->touched_voxels = 0;
   dc->n_free = 0;
@@ -100,6 +101,27 @@ __global__ void begin_kernel(DevCounters* dc, uint32_t epoch) {
   dc->work_next = 0;
   dc->epoch = epoch;
   dc->n_blocks_before = dc->n_blocks;
+}
+
+// begin_kernel for a batched update recorded in a graph: the epoch advances on
+// the device and the point count comes from the scan descriptors
+__global__ void batch_begin_kernel(DevCounters* dc, const ScanDesc* desc, int ns) {
+  dc->pairs = 0;
+  dc->touched_voxels = 0;
+  dc->n_free = 0;
+  dc->err = 0;
+  dc->n_valid = 0;
+  dc->n_items = 0;
+  dc->n_train = 0;
+  dc->n_tiles = 0;
+  dc->n_touched = 0;
+  dc->n_new = 0;
+  dc->n_huge = 0;
+  dc->n_mid = 0;
+  dc->work_next = 0;
+  dc->epoch = dc->epoch + 1;
+  dc->n_blocks_before = dc->n_blocks;
+  dc->n_points = (uint32_t)desc[ns].off;
 }
 
 __global__ void bbox_init_kernel(int* bbox) {
@@ -128,6 +150,8 @@ sbki_status check_params(const sbki_params* p) {
     return fail(nullptr, SBKI_ERR_INVALID_ARG, "length_scale must be <= 0.75 * block_edge * res");
   if (p->pool_blocks < 1 || p->pool_blocks > (1ll << 28))
     return fail(nullptr, SBKI_ERR_INVALID_ARG, "pool_blocks must be in 1..2^28");
+  if (p->num_maps < 1 || p->num_maps > kMaxMaps)
+    return fail(nullptr, SBKI_ERR_INVALID_ARG, "num_maps must be in 1..%d", kMaxMaps);
   if (p->accumulate_mode != 0 && p->accumulate_mode != 1)
     return fail(nullptr, SBKI_ERR_INVALID_ARG, "accumulate_mode must be 0 (point-major) or 1 (block-major)");
   if (p->sample_capacity < 1 || p->sample_capacity > (1ll << 27))
@@ -187,7 +211,24 @@ KeyFrame scan_frame(const MapState& m, const double T[16]) {
     kf.org[a] = (int32_t)(floor_div64(gcell, kTileEdge) - half);
   }
   kf.total_bits = 3 * kf.bits + kLocalBits + m.g.label_bits;
+  kf.scan_bits = 0;
   return kf;
+}
+
+// Descriptor of one scan (device point and label pointers).
+void fill_desc(ScanDesc& d, const float* pts, const int32_t* labels, int64_t n, int64_t off, const double T[16],
+               const KeyFrame& kf, int map) {
+  d.pts = pts;
+  d.labels = labels;
+  d.n = n;
+  d.off = off;
+  for (int r = 0; r < 3; ++r) {
+    for (int c = 0; c < 3; ++c) d.r[3 * r + c] = T[4 * r + c];
+    d.t[r] = T[4 * r + 3];
+    d.o[r] = (float)T[4 * r + 3];
+    d.org[r] = kf.org[r];
+  }
+  d.map_id = map;
 }
 
 cudaError_t free_scratch_points(Scratch& s) {
@@ -214,6 +255,7 @@ sbki_status ensure_point_capacity(MapState& m, int64_t n) {
   CK(&m, dalloc(&s.world, cap));
   CK(&m, dalloc(&s.cnt, cap + 1));
   s.n_cap = cap;  // scan partials are sized at creation for 2^27 entries
+  m.scratch_gen += 1;  // recorded graphs name the old buffers
   return SBKI_OK;
 }
 
@@ -258,7 +300,7 @@ void fill_stats(const MapState& m, int64_t n, sbki_stats* st) {
 // Steps a1-a3 on device; leaves the training set in s.train.  On return
 // *nitems holds the number of hits + free samples (0 on a pending error).
 sbki_status run_ingest(MapState& m, const float* points, const int32_t* labels, int64_t n, const double T[16],
-                       KeyFrame& kf, int64_t* nitems) {
+                       KeyFrame& kf, int64_t* nitems, int map) {
   *nitems = 0;
   for (int i = 0; i < 16; ++i)
     if (!std::isfinite(T[i])) return fail(&m, SBKI_ERR_INVALID_ARG, "sensor_pose has a non-finite entry");
@@ -281,16 +323,20 @@ sbki_status run_ingest(MapState& m, const float* points, const int32_t* labels, 
   }
   m.epoch += 1;
   if (m.profiling) CK(&m, cudaEventRecord(m.ev[0], m.stream));
-  begin_kernel<<<1, 1, 0, m.stream>>>(m.dc, m.epoch);
+  begin_kernel<<<1, 1, 0, m.stream>>>(m.dc, m.epoch, (uint32_t)n);
   m.launches += 1;
   kf = scan_frame(m, T);
-  CK(&m, launch_transform_count(m, dpts, dlab, n, nullptr, T, kf));
+  fill_desc(m.hdesc[0], dpts, dlab, n, 0, T, kf, map);
+  m.hdesc[1] = ScanDesc{};
+  m.hdesc[1].off = n;
+  CK(&m, cudaMemcpyAsync(m.s.desc, m.hdesc, 2 * sizeof(ScanDesc), cudaMemcpyHostToDevice, m.stream));
+  CK(&m, launch_transform_count(m, 1, n));
   st = read_counters(m);
   if (st != SBKI_OK) return st;
   if (m.hc->err != 0) return status_from_device(m);
   *nitems = m.hc->n_items;
   if (*nitems == 0) return SBKI_OK;
-  CK(&m, launch_emit(m, n, T, kf));
+  CK(&m, launch_emit(m, 1, n, kf));
   CK(&m, launch_downsample_n(m, kf, *nitems));
   return SBKI_OK;
 }
@@ -340,7 +386,7 @@ sbki_status insert_scan_impl(sbki_map* map, const float* points, const int32_t* 
   }
   KeyFrame kf;
   int64_t nitems = 0;
-  sbki_status st = run_ingest(m, points, labels, n, pose, kf, &nitems);
+  sbki_status st = run_ingest(m, points, labels, n, pose, kf, &nitems, m.active_map);
   if (st != SBKI_OK) {
     fill_stats(m, n, &m.last_stats);
     if (stats) *stats = m.last_stats;
@@ -392,6 +438,7 @@ sbki_status sbki_default_params(sbki_params* p) {
   p->track_pairs = 0;
   p->device = 0;
   p->accumulate_mode = 0;
+  p->num_maps = 1;
   p->cuda_stream = nullptr;
   return SBKI_OK;
 }
@@ -452,9 +499,6 @@ sbki_status sbki_create_map(const sbki_params* params, sbki_map** out) {
   if ((ce = dalloc(&s.flags, S + 1)) != cudaSuccess) return bail("flags", ce);
   if ((ce = dalloc(&s.seg_start, S + 1)) != cudaSuccess) return bail("seg_start", ce);
   if ((ce = dalloc(&s.train, S)) != cudaSuccess) return bail("train", ce);
-  if ((ce = dalloc(&s.tflags, S + 1)) != cudaSuccess) return bail("tflags", ce);
-  if ((ce = dalloc(&s.tile_key, S)) != cudaSuccess) return bail("tile keys", ce);
-  if ((ce = dalloc(&s.tile_start, S + 1)) != cudaSuccess) return bail("tile starts", ce);
   s.hist_cap = radix_hist_entries(S);
   if ((ce = dalloc(&s.hist, s.hist_cap)) != cudaSuccess) return bail("histogram", ce);
   const int64_t scan_n = std::max<int64_t>(std::max<int64_t>(s.hist_cap, S + 1), (int64_t)1 << 27);
@@ -463,6 +507,9 @@ sbki_status sbki_create_map(const sbki_params* params, sbki_map** out) {
   if ((ce = dalloc(&s.bbox, 8)) != cudaSuccess) return bail("bbox", ce);
   if ((ce = dalloc(&s.huge, S / 1024 + 2)) != cudaSuccess) return bail("huge cells", ce);
   if ((ce = dalloc(&s.mid, S / 16 + 2)) != cudaSuccess) return bail("long cells", ce);
+  if ((ce = dalloc(&s.desc, kMaxScans + 1)) != cudaSuccess) return bail("scan descriptors", ce);
+  if ((ce = cudaMallocHost((void**)&m.hdesc, sizeof(ScanDesc) * (kMaxScans + 1))) != cudaSuccess)
+    return bail("host scan descriptors", ce);
   if ((ce = dalloc(&s.fresh, m.hash_cap)) != cudaSuccess) return bail("fresh list", ce);
   if ((ce = cudaMemsetAsync(m.hkeys, 0xff, sizeof(unsigned long long) * m.hash_cap, m.stream)) != cudaSuccess)
     return bail("hash init", ce);
@@ -486,13 +533,17 @@ void sbki_destroy_map(sbki_map* map) {
   {
     DeviceGuard dg(m.device);
     if (m.stream || m.dc) cudaStreamSynchronize(m.stream);
-    void* ptrs[] = {m.ctab, m.hkeys, m.hvals, m.hmark, m.hcnt, m.hcur, m.boff, m.blist, m.alpha, m.pool_keys, m.pairs, m.dc, m.s.items, m.s.keys, m.s.keys2,
-                    m.s.vals, m.s.vals2, m.s.flags, m.s.seg_start, m.s.train, m.s.tflags, m.s.tile_key,
-                    m.s.tile_start, m.s.hist, m.s.scan_tmp, m.s.touched, m.s.fresh, m.s.bbox, m.s.huge, m.s.mid};
+    void* ptrs[] = {m.gpool, m.dacc, m.ctab, m.hkeys, m.hvals, m.hmark, m.hcnt, m.hcur, m.boff, m.blist, m.alpha, m.pool_keys, m.pairs, m.dc, m.s.items, m.s.keys, m.s.keys2,
+                    m.s.vals, m.s.vals2, m.s.flags, m.s.seg_start, m.s.train, m.s.hist, m.s.scan_tmp, m.s.touched, m.s.fresh, m.s.bbox, m.s.huge, m.s.mid,
+                    m.s.desc};
     for (void* p : ptrs)
       if (p) cudaFree(p);
     free_scratch_points(m.s);
     if (m.hc) cudaFreeHost(m.hc);
+    if (m.hdesc) cudaFreeHost(m.hdesc);
+    for (int i = 0; i <= kMaxScans; ++i)
+      if (m.batch_exec[i]) cudaGraphExecDestroy(m.batch_exec[i]);
+    if (m.rec_stream) cudaStreamDestroy(m.rec_stream);
     for (int i = 0; i < 4; ++i)
       if (m.ev[i]) cudaEventDestroy(m.ev[i]);
   }
@@ -502,6 +553,136 @@ void sbki_destroy_map(sbki_map* map) {
 sbki_status sbki_insert_scan(sbki_map* map, const float* points, const int32_t* labels, int64_t n,
                              const double sensor_pose[16], sbki_stats* stats) {
   return insert_scan_impl(map, points, labels, n, sensor_pose, true, stats);
+}
+
+sbki_status sbki_select_map(sbki_map* map, int32_t map_id) {
+  if (!map) return fail(nullptr, SBKI_ERR_INVALID_ARG, "map is NULL");
+  MapState& m = map->st;
+  if (map_id < 0 || map_id >= m.prm.num_maps)
+    return fail(&m, SBKI_ERR_INVALID_ARG, "map_id %d outside 0..%d", map_id, m.prm.num_maps - 1);
+  m.active_map = map_id;
+  return SBKI_OK;
+}
+
+sbki_status sbki_insert_batch(sbki_map* map, const sbki_scan* scans, int32_t count, sbki_stats* stats) {
+  if (!map) return fail(nullptr, SBKI_ERR_INVALID_ARG, "map is NULL");
+  MapState& m = map->st;
+  if (!scans || count < 1 || count > kMaxScans)
+    return fail(&m, SBKI_ERR_INVALID_ARG, "need 1 <= count <= %d scans", kMaxScans);
+  int64_t total = 0;
+  for (int i = 0; i < count; ++i) {
+    const sbki_scan& sc = scans[i];
+    if (sc.n < 0 || (sc.n > 0 && (!sc.points || !sc.labels)))
+      return fail(&m, SBKI_ERR_INVALID_ARG, "scan %d: need n >= 0 and points/labels for n > 0", i);
+    if (sc.map_id < 0 || sc.map_id >= m.prm.num_maps)
+      return fail(&m, SBKI_ERR_INVALID_ARG, "scan %d: map_id %d outside 0..%d", i, sc.map_id, m.prm.num_maps - 1);
+    for (int k = 0; k < 16; ++k)
+      if (!std::isfinite(sc.pose[k])) return fail(&m, SBKI_ERR_INVALID_ARG, "scan %d: non-finite pose", i);
+    for (int a = 0; a < 3; ++a)
+      if ((std::fabs(sc.pose[4 * a + 3]) + m.prm.max_range) / m.prm.res > (double)(kKeyLimit - 1024))
+        return fail(&m, SBKI_ERR_INVALID_ARG, "scan %d: sensor origin too far from the map origin", i);
+    total += sc.n;
+  }
+  if (total > (1ll << 26)) return fail(&m, SBKI_ERR_INVALID_ARG, "too many points in one batch");
+  DeviceGuard dg(m.device);
+  if (total == 0) {
+    if (stats) {
+      *stats = sbki_stats{};
+      stats->total_blocks = m.host_blocks;
+    }
+    return SBKI_OK;
+  }
+  sbki_status st = ensure_point_capacity(m, total);
+  if (st != SBKI_OK) return st;
+  // descriptors; host inputs are staged into the map's point buffers (outside the recording)
+  KeyFrame kf = scan_frame(m, scans[0].pose);
+  kf.scan_bits = count > 1 ? ceil_log2(count) : 0;
+  if (kf.total_bits + kf.scan_bits > 64) return fail(&m, SBKI_ERR_INVALID_ARG, "batch keys do not fit 64 bits");
+  int64_t off = 0;
+  for (int i = 0; i < count; ++i) {
+    const sbki_scan& sc = scans[i];
+    const float* dp = sc.points;
+    const int32_t* dl = sc.labels;
+    if (sc.n > 0 && !is_device_ptr(sc.points)) {
+      CK(&m, cudaMemcpyAsync(m.s.pts + 3 * off, sc.points, sizeof(float) * 3 * sc.n, cudaMemcpyHostToDevice,
+                             m.stream));
+      dp = m.s.pts + 3 * off;
+    }
+    if (sc.n > 0 && !is_device_ptr(sc.labels)) {
+      CK(&m, cudaMemcpyAsync(m.s.labels + off, sc.labels, sizeof(int32_t) * sc.n, cudaMemcpyHostToDevice, m.stream));
+      dl = m.s.labels + off;
+    }
+    fill_desc(m.hdesc[i], dp, dl, sc.n, off, sc.pose, scan_frame(m, sc.pose), sc.map_id);
+    off += sc.n;
+  }
+  m.hdesc[count] = ScanDesc{};
+  m.hdesc[count].off = total;
+  CK(&m, cudaMemcpyAsync(m.s.desc, m.hdesc, sizeof(ScanDesc) * (count + 1), cudaMemcpyHostToDevice, m.stream));
+  // the stage sequence, recorded once per scan count (every size it depends on is read on the device)
+  if (!m.batch_exec[count] || m.batch_gen[count] != m.scratch_gen) {
+    if (m.batch_exec[count]) {
+      cudaGraphExecDestroy(m.batch_exec[count]);
+      m.batch_exec[count] = nullptr;
+    }
+    // recorded on a private stream (the legacy default stream cannot be captured),
+    // launched on the map's stream
+    if (!m.rec_stream) CK(&m, cudaStreamCreateWithFlags(&m.rec_stream, cudaStreamNonBlocking));
+    const bool prof = m.profiling;
+    const int64_t l0 = m.launches;
+    const cudaStream_t user_stream = m.stream;
+    m.profiling = false;
+    m.stream = m.rec_stream;
+    {
+      const cudaError_t be = cudaStreamBeginCapture(m.stream, cudaStreamCaptureModeThreadLocal);
+      if (be != cudaSuccess) {
+        m.stream = user_stream;
+        m.profiling = prof;
+        return fail(&m, SBKI_ERR_CUDA, "recording the batched update failed: %s", cudaGetErrorString(be));
+      }
+    }
+    batch_begin_kernel<<<1, 1, 0, m.stream>>>(m.dc, m.s.desc, count);
+    m.launches += 1;
+    cudaError_t ce = launch_transform_count(m, count, m.s.n_cap);
+    if (ce == cudaSuccess) ce = launch_emit(m, count, m.s.n_cap, kf);
+    if (ce == cudaSuccess) ce = launch_downsample_n(m, kf, m.s.s_cap);
+    sbki_status ust = SBKI_OK;
+    if (ce == cudaSuccess) ust = run_update(m, kf, m.s.s_cap);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(m.stream, &graph);
+    m.stream = user_stream;
+    m.profiling = prof;
+    if (ce != cudaSuccess || ee != cudaSuccess || ust != SBKI_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      return fail(&m, SBKI_ERR_CUDA, "recording the batched update failed: %s",
+                  cudaGetErrorString(ce != cudaSuccess ? ce : ee));
+    }
+    ce = cudaGraphInstantiate(&m.batch_exec[count], graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) {
+      m.batch_exec[count] = nullptr;
+      return fail(&m, SBKI_ERR_CUDA, "instantiating the batched update failed: %s", cudaGetErrorString(ce));
+    }
+    m.batch_kernels[count] = m.launches - l0;
+    m.launches = l0;
+    m.batch_gen[count] = m.scratch_gen;
+  }
+  m.epoch += 1;  // the recording advances the device epoch
+  if (m.profiling) CK(&m, cudaEventRecord(m.ev[0], m.stream));
+  CK(&m, cudaGraphLaunch(m.batch_exec[count], m.stream));
+  m.launches += m.batch_kernels[count];
+  if (m.profiling) {
+    CK(&m, cudaEventRecord(m.ev[1], m.stream));
+    CK(&m, cudaEventRecord(m.ev[2], m.stream));
+    CK(&m, cudaEventRecord(m.ev[3], m.stream));
+  }
+  st = read_counters(m);
+  if (st != SBKI_OK) return st;
+  if (m.hc->err == 0) profile_collect(m);
+  m.host_blocks = m.hc->n_blocks;
+  fill_stats(m, total, &m.last_stats);
+  if (stats) *stats = m.last_stats;
+  return status_from_device(m);
 }
 
 sbki_status sbki_insert_scan_async(sbki_map* map, const float* points, const int32_t* labels, int64_t n,
@@ -543,7 +724,7 @@ sbki_status sbki_training_set(sbki_map* map, const float* points, const int32_t*
   if (n == 0) return SBKI_OK;
   KeyFrame kf;
   int64_t nitems = 0;
-  sbki_status st = run_ingest(m, points, labels, n, sensor_pose, kf, &nitems);
+  sbki_status st = run_ingest(m, points, labels, n, sensor_pose, kf, &nitems, 0);  // labels only in the output
   if (st != SBKI_OK) return st;
   st = read_counters(m);
   if (st != SBKI_OK) return st;
@@ -580,7 +761,7 @@ sbki_status sbki_insert_training(sbki_map* map, const float* xyzl, int64_t p, sb
   }
   m.epoch += 1;
   if (m.profiling) CK(&m, cudaEventRecord(m.ev[0], m.stream));
-  begin_kernel<<<1, 1, 0, m.stream>>>(m.dc, m.epoch);
+  begin_kernel<<<1, 1, 0, m.stream>>>(m.dc, m.epoch, 0u);
   m.launches += 1;
   int* bbox = m.s.bbox;
   sbki_status st = SBKI_OK;
@@ -680,7 +861,20 @@ sbki_status sbki_voxel_count(const sbki_map* cmap, int64_t* count) {
   DeviceGuard dg(m.device);
   sbki_status st = read_counters(m);
   if (st != SBKI_OK) return st;
-  *count = (int64_t)m.hc->n_blocks * m.g.B3;
+  const int64_t nb = m.hc->n_blocks;
+  if (m.prm.num_maps == 1) {
+    *count = nb * m.g.B3;
+    return SBKI_OK;
+  }
+  std::vector<unsigned long long> bkeys((size_t)nb);
+  if (nb > 0) {
+    CK(&m, cudaMemcpyAsync(bkeys.data(), m.pool_keys, sizeof(unsigned long long) * nb, cudaMemcpyDeviceToHost,
+                           m.stream));
+    CK(&m, cudaStreamSynchronize(m.stream));
+  }
+  int64_t mine = 0;
+  for (unsigned long long k : bkeys) mine += map_of_block(k) == m.active_map ? 1 : 0;
+  *count = mine * m.g.B3;
   return SBKI_OK;
 }
 
@@ -694,16 +888,23 @@ sbki_status sbki_export(const sbki_map* cmap, int64_t* keys, float* alpha, int32
   if (st != SBKI_OK) return st;
   const int64_t nb = m.hc->n_blocks;
   const int B = m.g.B, B3 = m.g.B3, K1 = m.g.K1;
-  *count = nb * B3;
-  if (!keys && !alpha && !pairs) return SBKI_OK;
-  if (cap < *count) return fail(&m, SBKI_ERR_CAPACITY, "export needs %lld rows, cap %lld", (long long)*count,
-                                (long long)cap);
   std::vector<unsigned long long> bkeys((size_t)nb);
-  std::vector<float> a((size_t)nb * K1 * B3);
-  std::vector<int32_t> pc(m.pairs ? (size_t)nb * B3 : 0);
   if (nb > 0) {
     CK(&m, cudaMemcpyAsync(bkeys.data(), m.pool_keys, sizeof(unsigned long long) * nb, cudaMemcpyDeviceToHost,
                            m.stream));
+    CK(&m, cudaStreamSynchronize(m.stream));
+  }
+  std::vector<int64_t> mine;  // pool blocks of the selected map
+  mine.reserve((size_t)nb);
+  for (int64_t b = 0; b < nb; ++b)
+    if (map_of_block(bkeys[(size_t)b]) == m.active_map) mine.push_back(b);
+  *count = (int64_t)mine.size() * B3;
+  if (!keys && !alpha && !pairs) return SBKI_OK;
+  if (cap < *count) return fail(&m, SBKI_ERR_CAPACITY, "export needs %lld rows, cap %lld", (long long)*count,
+                                (long long)cap);
+  std::vector<float> a((size_t)nb * K1 * B3);
+  std::vector<int32_t> pc(m.pairs ? (size_t)nb * B3 : 0);
+  if (nb > 0) {
     CK(&m, cudaMemcpyAsync(a.data(), m.alpha, sizeof(float) * a.size(), cudaMemcpyDeviceToHost, m.stream));
     if (m.pairs)
       CK(&m, cudaMemcpyAsync(pc.data(), m.pairs, sizeof(int32_t) * pc.size(), cudaMemcpyDeviceToHost, m.stream));
@@ -713,12 +914,13 @@ sbki_status sbki_export(const sbki_map* cmap, int64_t* keys, float* alpha, int32
     int32_t k[3];
     int64_t src;  // pool block * B3 + local
   };
-  std::vector<Row> rows((size_t)nb * B3);
-  for (int64_t b = 0; b < nb; ++b) {
+  std::vector<Row> rows(mine.size() * B3);
+  for (size_t mb = 0; mb < mine.size(); ++mb) {
+    const int64_t b = mine[mb];
     int32_t bx, by, bz;
     unpack_block(bkeys[(size_t)b], bx, by, bz);
     for (int li = 0; li < B3; ++li) {
-      Row& r = rows[(size_t)(b * B3 + li)];
+      Row& r = rows[mb * B3 + li];
       r.k[0] = bx * B + li % B;
       r.k[1] = by * B + (li / B) % B;
       r.k[2] = bz * B + li / (B * B);
@@ -760,6 +962,188 @@ sbki_status sbki_profile_read(const sbki_map* map, sbki_profile_data* out) {
   *out = map->st.prof;
   out->launches = map->st.launches;
   return SBKI_OK;
+}
+
+// ---------------------------------------------------------------- differentiable form
+
+}  // extern "C"
+
+namespace {
+
+// The gradient buffer (pool-shaped, like alpha) and the device accumulators, on first use.
+sbki_status ensure_grad(MapState& m) {
+  if (m.gpool) return SBKI_OK;
+  CK(&m, dalloc(&m.gpool, (size_t)m.pool_blocks * m.g.K1 * m.g.B3));
+  CK(&m, dalloc(&m.dacc, 4));
+  CK(&m, cudaMemsetAsync(m.gpool, 0, sizeof(float) * (size_t)m.pool_blocks * m.g.K1 * m.g.B3, m.stream));
+  return SBKI_OK;
+}
+
+// A device copy of a host or device input; `tmp` receives an allocation to free (or null).
+template <typename T>
+sbki_status device_input(MapState& m, const T* src, size_t count, const T** dst, void** tmp) {
+  *tmp = nullptr;
+  if (is_device_ptr(src)) {
+    *dst = src;
+    return SBKI_OK;
+  }
+  CK(&m, cudaMalloc(tmp, sizeof(T) * std::max<size_t>(count, 1)));
+  CK(&m, cudaMemcpyAsync(*tmp, src, sizeof(T) * count, cudaMemcpyHostToDevice, m.stream));
+  *dst = static_cast<const T*>(*tmp);
+  return SBKI_OK;
+}
+
+struct TmpFree {
+  void* p[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaStream_t st = nullptr;
+  ~TmpFree() {
+    bool any = false;
+    for (void* q : p) any = any || q;
+    if (!any) return;
+    cudaStreamSynchronize(st);
+    for (void* q : p)
+      if (q) cudaFree(q);
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+sbki_status sbki_grad_clear(sbki_map* map) {
+  if (!map) return fail(nullptr, SBKI_ERR_INVALID_ARG, "map is NULL");
+  MapState& m = map->st;
+  DeviceGuard dg(m.device);
+  sbki_status st = ensure_grad(m);
+  if (st != SBKI_OK) return st;
+  st = read_counters(m);
+  if (st != SBKI_OK) return st;
+  CK(&m, cudaMemsetAsync(m.gpool, 0, sizeof(float) * (size_t)m.hc->n_blocks * m.g.K1 * m.g.B3, m.stream));
+  return SBKI_OK;
+}
+
+sbki_status sbki_heldout_loglik(sbki_map* map, const float* xyz, const int32_t* labels, int64_t h,
+                                int32_t accumulate_grad, double* loglik) {
+  if (!map) return fail(nullptr, SBKI_ERR_INVALID_ARG, "map is NULL");
+  MapState& m = map->st;
+  if (h < 0 || (h > 0 && (!xyz || !labels)) || !loglik) return fail(&m, SBKI_ERR_INVALID_ARG, "bad arguments");
+  DeviceGuard dg(m.device);
+  sbki_status st = ensure_grad(m);
+  if (st != SBKI_OK) return st;
+  *loglik = 0.0;
+  if (h == 0) return SBKI_OK;
+  TmpFree tf;
+  tf.st = m.stream;
+  const float* dx = nullptr;
+  const int32_t* dl = nullptr;
+  if ((st = device_input(m, xyz, (size_t)h * 3, &dx, &tf.p[0])) != SBKI_OK) return st;
+  if ((st = device_input(m, labels, (size_t)h, &dl, &tf.p[1])) != SBKI_OK) return st;
+  CK(&m, cudaMemsetAsync(m.dacc, 0, sizeof(double), m.stream));
+  CK(&m, cudaMemsetAsync(&m.dc->err, 0, sizeof(int32_t), m.stream));
+  CK(&m, launch_heldout(m, dx, dl, h, accumulate_grad ? m.gpool : nullptr, m.dacc));
+  m.launches += 1;
+  CK(&m, cudaMemcpyAsync(loglik, m.dacc, sizeof(double), cudaMemcpyDeviceToHost, m.stream));
+  st = read_counters(m);
+  if (st != SBKI_OK) return st;
+  if (m.hc->err == SBKI_ERR_LABEL_RANGE) {
+    CK(&m, cudaMemsetAsync(&m.dc->err, 0, sizeof(int32_t), m.stream));
+    return fail(&m, SBKI_ERR_LABEL_RANGE, "a held-out label is outside 0..K");
+  }
+  return status_from_device(m);
+}
+
+sbki_status sbki_grad_add_alpha(sbki_map* map, const int64_t* keys, const float* grad_alpha, int64_t count,
+                                int64_t* missed) {
+  if (!map) return fail(nullptr, SBKI_ERR_INVALID_ARG, "map is NULL");
+  MapState& m = map->st;
+  if (count < 0 || (count > 0 && (!keys || !grad_alpha))) return fail(&m, SBKI_ERR_INVALID_ARG, "bad arguments");
+  DeviceGuard dg(m.device);
+  sbki_status st = ensure_grad(m);
+  if (st != SBKI_OK) return st;
+  if (missed) *missed = 0;
+  if (count == 0) return SBKI_OK;
+  TmpFree tf;
+  tf.st = m.stream;
+  const int64_t* dk = nullptr;
+  const float* dg2 = nullptr;
+  if ((st = device_input(m, keys, (size_t)count * 3, &dk, &tf.p[0])) != SBKI_OK) return st;
+  if ((st = device_input(m, grad_alpha, (size_t)count * m.g.K1, &dg2, &tf.p[1])) != SBKI_OK) return st;
+  unsigned long long* dmiss = reinterpret_cast<unsigned long long*>(m.dacc + 3);
+  CK(&m, cudaMemsetAsync(dmiss, 0, sizeof(unsigned long long), m.stream));
+  CK(&m, launch_grad_scatter(m, dk, dg2, count, m.gpool, dmiss));
+  m.launches += 1;
+  unsigned long long hm = 0;
+  CK(&m, cudaMemcpyAsync(&hm, dmiss, sizeof(hm), cudaMemcpyDeviceToHost, m.stream));
+  CK(&m, cudaStreamSynchronize(m.stream));
+  if (missed) *missed = (int64_t)hm;
+  return SBKI_OK;
+}
+
+sbki_status sbki_backward(sbki_map* map, const float* xyzl, int64_t p, double* grad_l, double* grad_sigma0,
+                          float* grad_xyz) {
+  if (!map) return fail(nullptr, SBKI_ERR_INVALID_ARG, "map is NULL");
+  MapState& m = map->st;
+  if (p < 0 || (p > 0 && !xyzl)) return fail(&m, SBKI_ERR_INVALID_ARG, "bad arguments");
+  DeviceGuard dg(m.device);
+  sbki_status st = ensure_grad(m);
+  if (st != SBKI_OK) return st;
+  TmpFree tf;
+  tf.st = m.stream;
+  const float* dxyzl = nullptr;
+  if ((st = device_input(m, xyzl, (size_t)p * 4, &dxyzl, &tf.p[0])) != SBKI_OK) return st;
+  if (p > 0 && (reinterpret_cast<uintptr_t>(dxyzl) & 15u) != 0) {
+    CK(&m, cudaMalloc(&tf.p[1], sizeof(float4) * (size_t)p));
+    CK(&m, cudaMemcpyAsync(tf.p[1], dxyzl, sizeof(float4) * (size_t)p, cudaMemcpyDeviceToDevice, m.stream));
+    dxyzl = static_cast<const float*>(tf.p[1]);
+  }
+  float* dgx = grad_xyz;
+  if (grad_xyz && !is_device_ptr(grad_xyz)) {
+    CK(&m, cudaMalloc(&tf.p[2], sizeof(float) * 3 * std::max<int64_t>(p, 1)));
+    dgx = static_cast<float*>(tf.p[2]);
+  }
+  CK(&m, cudaMemsetAsync(m.dacc + 1, 0, 2 * sizeof(double), m.stream));
+  CK(&m, launch_backward(m, reinterpret_cast<const float4*>(dxyzl), p, m.gpool, m.dacc + 1, dgx));
+  m.launches += 1;
+  double acc[2] = {0.0, 0.0};
+  CK(&m, cudaMemcpyAsync(acc, m.dacc + 1, sizeof(acc), cudaMemcpyDeviceToHost, m.stream));
+  if (grad_xyz && dgx != grad_xyz && p > 0)
+    CK(&m, cudaMemcpyAsync(grad_xyz, dgx, sizeof(float) * 3 * p, cudaMemcpyDeviceToHost, m.stream));
+  st = read_counters(m);
+  if (st != SBKI_OK) return st;
+  if (m.hc->err != 0) return status_from_device(m);
+  const double l = m.prm.length_scale;
+  if (grad_sigma0) *grad_sigma0 = acc[0];
+  if (grad_l) *grad_l = m.prm.sigma0 * acc[1] / (l * l);
+  return SBKI_OK;
+}
+
+sbki_status sbki_forward_alpha(const sbki_params* params, const float* xyzl, int64_t p, int64_t* keys_out,
+                               float* alpha_out, int64_t cap, int64_t* count) {
+  if (!params || !count || p < 0 || (p > 0 && !xyzl)) return fail(nullptr, SBKI_ERR_INVALID_ARG, "bad arguments");
+  sbki_map* map = nullptr;
+  sbki_status st = sbki_create_map(params, &map);
+  if (st != SBKI_OK) return st;
+  st = sbki_insert_training(map, xyzl, p, nullptr);
+  if (st == SBKI_OK) st = sbki_export(map, keys_out, alpha_out, nullptr, cap, count);
+  if (st != SBKI_OK) snprintf(g_create_error, sizeof(g_create_error), "%s", map->st.last_error);
+  sbki_destroy_map(map);
+  return st;
+}
+
+sbki_status sbki_grad(const sbki_params* params, const float* xyzl, int64_t p, const int64_t* keys,
+                      const float* grad_alpha, int64_t count, double* grad_l, double* grad_sigma0, float* grad_xyz) {
+  if (!params || p < 0 || (p > 0 && !xyzl) || count < 0 || (count > 0 && (!keys || !grad_alpha)))
+    return fail(nullptr, SBKI_ERR_INVALID_ARG, "bad arguments");
+  sbki_map* map = nullptr;
+  sbki_status st = sbki_create_map(params, &map);
+  if (st != SBKI_OK) return st;
+  st = sbki_insert_training(map, xyzl, p, nullptr);
+  if (st == SBKI_OK) st = sbki_grad_clear(map);
+  if (st == SBKI_OK) st = sbki_grad_add_alpha(map, keys, grad_alpha, count, nullptr);
+  if (st == SBKI_OK) st = sbki_backward(map, xyzl, p, grad_l, grad_sigma0, grad_xyz);
+  if (st != SBKI_OK) snprintf(g_create_error, sizeof(g_create_error), "%s", map->st.last_error);
+  sbki_destroy_map(map);
+  return st;
 }
 
 const char* sbki_last_error(const sbki_map* map) { return map ? map->st.last_error : g_create_error; }

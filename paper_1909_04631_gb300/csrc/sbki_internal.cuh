@@ -11,8 +11,12 @@ namespace sbki {
 // ---------------------------------------------------------------- limits
 constexpr int kMaxClasses = 32;          // K+1 <= 32 (shared-memory alpha tile)
 constexpr int32_t kKeyLimit = 1 << 20;   // |voxel index| < kKeyLimit on every axis
-constexpr int kKeyBits = 21;             // bits per axis in a packed block key
-constexpr unsigned long long kEmpty = ~0ull;
+constexpr int kKeyBits = 19;             // bits per axis of a block coordinate in a packed key
+constexpr int kMapShift = 3 * kKeyBits;  // map index above the coordinates in a packed key
+constexpr int kMaxMaps = 64;             // independent maps in one handle (map index < 2^6)
+constexpr int kMaxScans = 64;            // scans of one batched update
+constexpr int kLabelBits = 5;            // a training point's float label word = label + 32 * map
+constexpr unsigned long long kEmpty = ~0ull;  // never a key: the map field's top bit is always 0
 constexpr int kMaxProbes = 4096;         // hash probe bound (then SBKI_ERR_CAPACITY)
 constexpr int kTileShift = 3;            // training-point tiles are 8^3 ds cells
 constexpr int kTileEdge = 1 << kTileShift;
@@ -39,6 +43,7 @@ struct DevCounters {
   uint32_t n_list;                    // (training point, touched block) pairs, this scan
   uint32_t n_huge;                    // downsampling cells summed by a whole CTA, this scan
   uint32_t n_mid;                     // downsampling cells summed by a warp, this scan
+  uint32_t n_points;                  // input points of the update (all scans)
 };
 
 // ---------------------------------------------------------------- geometry constants
@@ -63,7 +68,22 @@ struct Geom {
 struct KeyFrame {
   int32_t org[3];   // origin tile (ds-tile index) minus half range
   int bits;         // bits per axis of a relative tile index
-  int total_bits;   // bits of a full sort key
+  int total_bits;   // bits of a scan-local sort key (the scan index, if any, sits above)
+  int scan_bits;    // bits of the scan index in a batched update (0: one scan)
+};
+
+// One scan of an update, in device memory (read by the ingest kernels, so a
+// batch of scans needs no per-scan launch arguments).  Entry [count].off holds
+// the total point count.
+struct ScanDesc {
+  const float* pts;       // [n,3] sensor frame (device)
+  const int32_t* labels;  // [n] 1..K (device)
+  int64_t n;
+  int64_t off;            // first global point index of the scan
+  double r[9], t[3];      // world_from_sensor
+  float o[3];             // fp32 sensor origin
+  int32_t org[3];         // key-frame origin tile
+  int32_t map_id;         // target map of the handle
 };
 
 // ---------------------------------------------------------------- scratch of one map
@@ -83,9 +103,6 @@ struct Scratch {
   uint32_t* flags = nullptr;      // [s_cap+1] segment heads, scanned
   uint32_t* seg_start = nullptr;  // [s_cap+1]
   float4* train = nullptr;        // [s_cap] training points (xyz, label bits), tile-sorted
-  uint32_t* tflags = nullptr;     // [s_cap+1] tile heads, scanned
-  unsigned long long* tile_key = nullptr;  // [s_cap] relative packed tile index
-  uint32_t* tile_start = nullptr; // [s_cap+1]
   int64_t s_cap = 0;
   // radix sort / scan temporaries
   uint32_t* hist = nullptr;       // [256 * sort_ctas + 1]
@@ -97,6 +114,7 @@ struct Scratch {
   int* bbox = nullptr;            // [6] tile bounding box of a given training set
   uint32_t* huge = nullptr;       // [s_cap / 1024 + 2] very long downsampling cells
   uint32_t* mid = nullptr;        // [s_cap / 16 + 2] long downsampling cells
+  ScanDesc* desc = nullptr;       // [kMaxScans + 1] scans of the current update
 };
 
 // ---------------------------------------------------------------- the map
@@ -129,7 +147,16 @@ struct MapState {
   sbki_status sticky = SBKI_OK;
   int64_t launches = 0;                 // kernels launched on this map
   int acc_mode = 0;                     // 0: point-major (global reductions), 1: block-major (shared tile)
-  int32_t* ctab = nullptr;              // point-major candidate lists [27][ctab_pad]
+  int active_map = 0;                   // map index the single-map calls act on
+  cudaStream_t rec_stream = nullptr;    // private stream the batched update is recorded on
+  cudaGraphExec_t batch_exec[kMaxScans + 1] = {};  // recorded batched updates, by scan count
+  int64_t batch_kernels[kMaxScans + 1] = {};       // kernels in each recording
+  uint64_t batch_gen[kMaxScans + 1] = {};          // scratch generation each recording used
+  uint64_t scratch_gen = 1;             // advances when scratch buffers move
+  ScanDesc* hdesc = nullptr;            // pinned host staging of s.desc
+  uint32_t* ctab = nullptr;             // point-major candidate lists [27][ctab_pad]
+  float* gpool = nullptr;               // dL/dalpha [pool_blocks][K1][B3] (differentiable form, on first use)
+  double* dacc = nullptr;               // [4]: held-out LL, sum G f, sum G u^4 D d, keys missed (as u64)
   int ctab_pad = 0, ctab_R = 0;
   bool profiling = false;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -139,9 +166,11 @@ struct MapState {
 };
 
 // ---------------------------------------------------------------- device helpers
-__host__ __device__ inline unsigned long long pack_block(int32_t bx, int32_t by, int32_t bz) {
+// Block key: map index (6 bits, top bit of its 7-bit field always 0), then
+// x, y, z block coordinates offset by 2^18 (19 bits each; |block| < 2^18).
+__host__ __device__ inline unsigned long long pack_block(int32_t bx, int32_t by, int32_t bz, int32_t map) {
   const unsigned long long off = 1ull << (kKeyBits - 1);
-  return (((unsigned long long)(bx + (int64_t)off)) << (2 * kKeyBits)) |
+  return ((unsigned long long)map << kMapShift) | (((unsigned long long)(bx + (int64_t)off)) << (2 * kKeyBits)) |
          (((unsigned long long)(by + (int64_t)off)) << kKeyBits) | ((unsigned long long)(bz + (int64_t)off));
 }
 __host__ __device__ inline void unpack_block(unsigned long long k, int32_t& bx, int32_t& by, int32_t& bz) {
@@ -151,6 +180,7 @@ __host__ __device__ inline void unpack_block(unsigned long long k, int32_t& bx, 
   by = (int32_t)((int64_t)((k >> kKeyBits) & m) - off);
   bz = (int32_t)((int64_t)(k & m) - off);
 }
+__host__ __device__ inline int32_t map_of_block(unsigned long long k) { return (int32_t)(k >> kMapShift); }
 __device__ __forceinline__ uint32_t hash_slot(unsigned long long k, int64_t cap) {
   k ^= k >> 33;
   k *= 0xff51afd7ed558ccdull;
@@ -177,8 +207,12 @@ __device__ __forceinline__ uint32_t small_div(uint32_t x, uint32_t m) { return (
 // exactly as the plain definition states: c = (v + 0.5)*res64, e = c - x,
 // d^2 = (ex^2 + ey^2) + ez^2 < l^2.  Round-to-nearest intrinsics keep the
 // compiler from contracting or reordering any of it.
+// (float)K for |K| < 2^22, exactly, without a conversion instruction
+__device__ __forceinline__ float small_int_to_float(int K) {
+  return __fsub_rn(__int_as_float(0x4B400000 + K), 12582912.0f);
+}
 __device__ __forceinline__ void centre_offset0(int K, float x, const Geom& g, float& hi, float& lo) {
-  const float c0 = (float)K + 0.5f;  // exact: |K| < 2^22
+  const float c0 = __fadd_rn(small_int_to_float(K), 0.5f);  // exact: |K| < 2^22
   const float p_hi = __fmul_rn(c0, g.res);
   const float p_lo = __fmaf_rn(c0, g.res_lo, __fmaf_rn(c0, g.res, -p_hi));
   const float s = __fsub_rn(p_hi, x);
@@ -189,7 +223,7 @@ __device__ __forceinline__ void centre_offset0(int K, float x, const Geom& g, fl
 }
 // c_{K+d} - x = E0 + d res, rounded once (d a small integer)
 __device__ __forceinline__ float centre_offset_at(int d, float hi, float lo, const Geom& g) {
-  const float fd = (float)d;
+  const float fd = small_int_to_float(d);
   return __fadd_rn(__fmaf_rn(fd, g.res, hi), __fmaf_rn(fd, g.res_lo, lo));
 }
 __device__ __forceinline__ bool in_support64(int vx, int vy, int vz, float x, float y, float z, const Geom& g) {
@@ -199,6 +233,16 @@ __device__ __forceinline__ bool in_support64(int vx, int vy, int vz, float x, fl
   const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
   return d2 < g.l2_64;
 }
+// The same test as a call: the FP64 conversions stay inside the (rare) band
+// path instead of being hoisted into the caller's loop.
+static __device__ __noinline__ bool in_support64_call(int vx, int vy, int vz, float x, float y, float z, double res64,
+                                               double l2_64) {
+  const double ex = __dsub_rn(__dmul_rn(__dadd_rn((double)vx, 0.5), res64), (double)x);
+  const double ey = __dsub_rn(__dmul_rn(__dadd_rn((double)vy, 0.5), res64), (double)y);
+  const double ez = __dsub_rn(__dmul_rn(__dadd_rn((double)vz, 0.5), res64), (double)z);
+  const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
+  return d2 < l2_64;
+}
 
 // ---------------------------------------------------------------- shared host helpers (sbki_api.cu)
 sbki_status validate_params(const sbki_params* p);
@@ -207,22 +251,31 @@ KeyFrame frame_of_scan(const MapState& m, const double T[16]);
 void set_global_error(const char* msg);
 
 // ---------------------------------------------------------------- launchers (one per .cu)
-// scan.cu: exclusive prefix sums in place over n+1 entries (entry n receives the total)
-cudaError_t exclusive_scan_u32(uint32_t* data, int64_t n, void* tmp, cudaStream_t st);
-cudaError_t exclusive_scan_u64(unsigned long long* data, int64_t n, void* tmp, cudaStream_t st);
+// scan.cu: exclusive prefix sums in place over n+1 entries (entry n receives the total);
+// with n_dev the count is min(n, *n_dev), read on the device (n bounds the launch)
+cudaError_t exclusive_scan_u32(uint32_t* data, int64_t n, void* tmp, cudaStream_t st, const uint32_t* n_dev = nullptr);
+cudaError_t exclusive_scan_u64(unsigned long long* data, int64_t n, void* tmp, cudaStream_t st,
+                               const uint32_t* n_dev = nullptr);
 int64_t scan_tmp_bytes(int64_t n);
 
-// radix_sort.cu: stable LSD sort of (keys, vals) over bits [0, bits); count read
-// from *n_dev; capacity cap bounds the launch; result in (keys, vals).
-cudaError_t radix_sort_pairs(unsigned long long* keys, uint32_t* vals, unsigned long long* keys_alt,
-                             uint32_t* vals_alt, const uint32_t* n_dev, int64_t cap, int bits, uint32_t* hist,
-                             void* scan_tmp, DevCounters* dc, cudaStream_t st);
+// radix_sort.cu: stable LSD sort of (keys, vals) over bits [0, bits) (at most
+// 8 passes of 8 bits); count read from *n_dev, cap >= count bounds the work
+// area; the pointer pairs are swapped as passes go, so on return (keys, vals)
+// name the buffers that hold the result.  hist: radix_work_entries(cap) words.
+constexpr int64_t kRadixTile = 4096;  // items per tile of one pass
+constexpr int kMaxPasses = 8;
+constexpr int64_t radix_work_entries(int64_t cap) {
+  return 2 * 256 * ((cap + kRadixTile - 1) / kRadixTile) + kMaxPasses * 256 + kMaxPasses;
+}
+cudaError_t radix_sort_pairs(unsigned long long*& keys, uint32_t*& vals, unsigned long long*& keys_alt,
+                             uint32_t*& vals_alt, const uint32_t* n_dev, int64_t cap, int bits, uint32_t* hist,
+                             int sm_count, DevCounters* dc, cudaStream_t st);
 int64_t radix_hist_entries(int64_t cap);
 
 // ingest.cu
-cudaError_t launch_transform_count(MapState& m, const float* pts, const int32_t* labels, int64_t n,
-                                   const double* pose_dev_or_null, const double pose[16], const KeyFrame& kf);
-cudaError_t launch_emit(MapState& m, int64_t n, const double pose[16], const KeyFrame& kf);
+// ingest of the ns scans described in m.s.desc (ns + 1 entries, the last holding the total)
+cudaError_t launch_transform_count(MapState& m, int ns, int64_t total_n);
+cudaError_t launch_emit(MapState& m, int ns, int64_t total_n, const KeyFrame& kf);
 cudaError_t launch_downsample_n(MapState& m, const KeyFrame& kf, int64_t nitems);
 cudaError_t launch_train_bbox(MapState& m, const float4* in, int64_t p, int* bbox_dev);
 cudaError_t launch_train_prepare(MapState& m, const float4* in, int64_t p, const KeyFrame& kf);
@@ -236,6 +289,14 @@ cudaError_t launch_bin_points(MapState& m, int64_t bound);
 cudaError_t launch_accumulate(MapState& m, const KeyFrame& kf);
 cudaError_t launch_accumulate_points(MapState& m);
 cudaError_t build_candidate_tables(MapState& m);
+// backward.cu: held-out log-likelihood (+ dLL/dalpha into grad), upstream gradient at voxel keys,
+// and the backward pass through Eq. (kernel) into acc_dev[0..1] and grad_xyz
+cudaError_t launch_heldout(const MapState& m, const float* xyz, const int32_t* labels, int64_t h, float* grad,
+                           double* ll_dev);
+cudaError_t launch_grad_scatter(const MapState& m, const int64_t* keys, const float* grad, int64_t count, float* gpool,
+                                unsigned long long* missed_dev);
+cudaError_t launch_backward(const MapState& m, const float4* xyzl, int64_t p, const float* gpool, double* acc_dev,
+                            float* grad_xyz);
 size_t accumulate_smem_bytes(const Geom& g);
 
 // readoff.cu

@@ -35,11 +35,19 @@ __device__ T block_exclusive_scan(T v, T* warp_tot, T* total) {
   return warp_tot[warp] + inc - v;
 }
 
+// element count: the launch bound n, or the device count *n_dev (<= n) when given
+__device__ __forceinline__ int64_t count_of(int64_t n, const uint32_t* n_dev) {
+  return n_dev ? min(n, (int64_t)*n_dev) : n;
+}
+
 template <typename T>
-__global__ void __launch_bounds__(kThreads) scan_reduce(const T* __restrict__ data, int64_t n, T* partial) {
+__global__ void __launch_bounds__(kThreads) scan_reduce(const T* __restrict__ data, int64_t cap, T* partial,
+                                                        const uint32_t* n_dev) {
   __shared__ T warp_tot[kThreads / 32];
   __shared__ T total;
+  const int64_t n = count_of(cap, n_dev);
   const int64_t base = (int64_t)blockIdx.x * kTile;
+  if (base >= n) return;  // uniform over the CTA
   T s = 0;
   for (int i = threadIdx.x; i < kTile; i += kThreads) {
     int64_t idx = base + i;
@@ -51,9 +59,11 @@ __global__ void __launch_bounds__(kThreads) scan_reduce(const T* __restrict__ da
 
 // single CTA: exclusive scan of the tile totals, grand total to data[n]
 template <typename T>
-__global__ void __launch_bounds__(kThreads) scan_partials(T* partial, int64_t nparts, T* data, int64_t n) {
+__global__ void __launch_bounds__(kThreads) scan_partials(T* partial, T* data, int64_t cap, const uint32_t* n_dev) {
   __shared__ T warp_tot[kThreads / 32];
   __shared__ T total;
+  const int64_t n = count_of(cap, n_dev);
+  const int64_t nparts = (n + kTile - 1) / kTile;
   T carry = 0;
   for (int64_t base = 0; base < nparts; base += kThreads) {
     int64_t i = base + threadIdx.x;
@@ -67,11 +77,14 @@ __global__ void __launch_bounds__(kThreads) scan_partials(T* partial, int64_t np
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) scan_down(T* data, int64_t n, const T* __restrict__ partial) {
+__global__ void __launch_bounds__(kThreads) scan_down(T* data, int64_t cap, const T* __restrict__ partial,
+                                                      const uint32_t* n_dev) {
   __shared__ T tile[kTile];
   __shared__ T warp_tot[kThreads / 32];
   __shared__ T total;
+  const int64_t n = count_of(cap, n_dev);
   const int64_t base = (int64_t)blockIdx.x * kTile;
+  if (base >= n) return;  // uniform over the CTA
   for (int i = threadIdx.x; i < kTile; i += kThreads) {
     int64_t idx = base + i;
     tile[i] = idx < n ? data[idx] : T(0);
@@ -98,15 +111,15 @@ __global__ void __launch_bounds__(kThreads) scan_down(T* data, int64_t n, const 
 }
 
 template <typename T>
-cudaError_t scan_impl(T* data, int64_t n, void* tmp, cudaStream_t st) {
+cudaError_t scan_impl(T* data, int64_t n, void* tmp, cudaStream_t st, const uint32_t* n_dev) {
   if (n <= 0) {
     return cudaMemsetAsync(data, 0, sizeof(T), st);
   }
   int64_t tiles = (n + kTile - 1) / kTile;
   T* partial = (T*)tmp;
-  scan_reduce<T><<<(unsigned)tiles, kThreads, 0, st>>>(data, n, partial);
-  scan_partials<T><<<1, kThreads, 0, st>>>(partial, tiles, data, n);
-  scan_down<T><<<(unsigned)tiles, kThreads, 0, st>>>(data, n, partial);
+  scan_reduce<T><<<(unsigned)tiles, kThreads, 0, st>>>(data, n, partial, n_dev);
+  scan_partials<T><<<1, kThreads, 0, st>>>(partial, data, n, n_dev);
+  scan_down<T><<<(unsigned)tiles, kThreads, 0, st>>>(data, n, partial, n_dev);
   return cudaGetLastError();
 }
 
@@ -114,11 +127,11 @@ cudaError_t scan_impl(T* data, int64_t n, void* tmp, cudaStream_t st) {
 
 int64_t scan_tmp_bytes(int64_t n) { return ((n + kTile - 1) / kTile + 1) * (int64_t)sizeof(unsigned long long); }
 
-cudaError_t exclusive_scan_u32(uint32_t* data, int64_t n, void* tmp, cudaStream_t st) {
-  return scan_impl<uint32_t>(data, n, tmp, st);
+cudaError_t exclusive_scan_u32(uint32_t* data, int64_t n, void* tmp, cudaStream_t st, const uint32_t* n_dev) {
+  return scan_impl<uint32_t>(data, n, tmp, st, n_dev);
 }
-cudaError_t exclusive_scan_u64(unsigned long long* data, int64_t n, void* tmp, cudaStream_t st) {
-  return scan_impl<unsigned long long>(data, n, tmp, st);
+cudaError_t exclusive_scan_u64(unsigned long long* data, int64_t n, void* tmp, cudaStream_t st, const uint32_t* n_dev) {
+  return scan_impl<unsigned long long>(data, n, tmp, st, n_dev);
 }
 
 }  // namespace sbki

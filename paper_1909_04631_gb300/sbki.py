@@ -23,7 +23,8 @@ STATUS_NAMES = {0: "ok", 1: "invalid argument", 2: "label out of range", 3: "cap
 EXPORTED = ["sbki_default_params", "sbki_create_map", "sbki_destroy_map", "sbki_insert_scan",
             "sbki_insert_scan_async", "sbki_sync", "sbki_training_set", "sbki_insert_training", "sbki_query_probs",
             "sbki_voxel_count", "sbki_export", "sbki_profile", "sbki_profile_read", "sbki_kernel_values", "sbki_last_error", "sbki_status_string",
-            "sbki_training_set_noalloc"]
+            "sbki_training_set_noalloc", "sbki_grad_clear", "sbki_heldout_loglik", "sbki_grad_add_alpha",
+            "sbki_backward", "sbki_forward_alpha", "sbki_grad", "sbki_insert_batch", "sbki_select_map"]
 
 
 class SbkiError(RuntimeError):
@@ -37,8 +38,13 @@ class Params(C.Structure):
                                           "min_range", "max_range", "free_thresh", "occ_thresh")] + \
                [("num_classes", C.c_int32), ("block_edge", C.c_int32), ("pool_blocks", C.c_int64),
                 ("sample_capacity", C.c_int64), ("track_pairs", C.c_int32), ("device", C.c_int32),
-                ("accumulate_mode", C.c_int32),
+                ("accumulate_mode", C.c_int32), ("num_maps", C.c_int32),
                 ("cuda_stream", C.c_void_p)]
+
+
+class Scan(C.Structure):
+    _fields_ = [("points", C.c_void_p), ("labels", C.c_void_p), ("n", C.c_int64), ("pose", C.c_double * 16),
+                ("map_id", C.c_int32)]
 
 
 class ProfileData(C.Structure):
@@ -89,6 +95,14 @@ def load(build_if_missing: bool = True):
         L.sbki_insert_training.argtypes = [vp, vp, i64, P(Stats)]
         L.sbki_training_set_noalloc.argtypes = [P(Params), vp, vp, i64, vp, vp, i64, P(i64)]
         L.sbki_query_probs.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp]
+        L.sbki_insert_batch.argtypes = [vp, vp, i32, P(Stats)]
+        L.sbki_select_map.argtypes = [vp, i32]
+        L.sbki_grad_clear.argtypes = [vp]
+        L.sbki_heldout_loglik.argtypes = [vp, vp, vp, i64, i32, P(C.c_double)]
+        L.sbki_grad_add_alpha.argtypes = [vp, vp, vp, i64, P(i64)]
+        L.sbki_backward.argtypes = [vp, vp, i64, P(C.c_double), P(C.c_double), vp]
+        L.sbki_forward_alpha.argtypes = [P(Params), vp, i64, vp, vp, i64, P(i64)]
+        L.sbki_grad.argtypes = [P(Params), vp, i64, vp, vp, i64, P(C.c_double), P(C.c_double), vp]
         L.sbki_voxel_count.argtypes = [vp, P(i64)]
         L.sbki_export.argtypes = [vp, vp, vp, vp, i64, P(i64)]
         L.sbki_last_error.argtypes = [vp]
@@ -103,7 +117,9 @@ def load(build_if_missing: bool = True):
         L.sbki_status_string.restype = C.c_char_p
         for f in ("sbki_default_params", "sbki_create_map", "sbki_insert_scan", "sbki_insert_scan_async", "sbki_sync",
                   "sbki_training_set", "sbki_insert_training", "sbki_query_probs", "sbki_voxel_count",
-                  "sbki_export", "sbki_training_set_noalloc"):
+                  "sbki_export", "sbki_training_set_noalloc", "sbki_grad_clear", "sbki_heldout_loglik",
+                  "sbki_grad_add_alpha", "sbki_backward", "sbki_forward_alpha", "sbki_grad", "sbki_insert_batch",
+                  "sbki_select_map"):
             getattr(L, f).restype = C.c_int
         _lib = L
         return L
@@ -136,6 +152,52 @@ def training_set_noalloc(params: Params, points, labels, pose, out):
     if st != OK:
         raise SbkiError(st, L.sbki_last_error(None).decode())
     return cnt.value
+
+
+def _as_i64(x, tail):
+    if hasattr(x, "data_ptr"):
+        import torch
+        return x.to(torch.int64).contiguous()
+    return np.ascontiguousarray(x, dtype=np.int64).reshape(-1, tail)
+
+
+def forward_alpha(params: Params, xyzl):
+    """(keys int64 [n,3], alpha float32 [n,K+1]) of a training set xyzl [p,4] at every
+    voxel of the blocks it reaches (a map is created and destroyed inside)."""
+    L = load()
+    x = _as(xyzl, np.float32, 4)
+    xp, keep = _ptr(x)
+    cnt = C.c_int64()
+    st = L.sbki_forward_alpha(C.byref(params), xp, x.shape[0], None, None, 0, C.byref(cnt))
+    if st != OK:
+        raise SbkiError(st, L.sbki_last_error(None).decode())
+    n = cnt.value
+    K1 = params.num_classes + 1
+    keys = np.empty((max(n, 1), 3), np.int64)
+    alpha = np.empty((max(n, 1), K1), np.float32)
+    st = L.sbki_forward_alpha(C.byref(params), xp, x.shape[0], keys.ctypes.data_as(C.c_void_p),
+                              alpha.ctypes.data_as(C.c_void_p), n, C.byref(cnt))
+    if st != OK:
+        raise SbkiError(st, L.sbki_last_error(None).decode())
+    return keys[:cnt.value], alpha[:cnt.value]
+
+
+def grad(params: Params, xyzl, keys, grad_alpha):
+    """(dL/dl, dL/dsigma0, dL/dxyz [p,3]) for dL/dalpha given at voxel keys."""
+    L = load()
+    x = _as(xyzl, np.float32, 4)
+    k = _as_i64(keys, 3)
+    gvals = _as(grad_alpha, np.float32, params.num_classes + 1)
+    xp, k1 = _ptr(x)
+    kp, k2 = _ptr(k)
+    gp, k3 = _ptr(gvals)
+    gx = np.empty((max(x.shape[0], 1), 3), np.float32)
+    gl, gs = C.c_double(), C.c_double()
+    st = L.sbki_grad(C.byref(params), xp, x.shape[0], kp, gp, k.shape[0], C.byref(gl), C.byref(gs),
+                     gx.ctypes.data_as(C.c_void_p))
+    if st != OK:
+        raise SbkiError(st, L.sbki_last_error(None).decode())
+    return gl.value, gs.value, gx[:x.shape[0]]
 
 
 def kernel_values(r, method=0):
@@ -308,6 +370,80 @@ class Map:
         c = C.c_int64()
         self._check(self._L.sbki_voxel_count(self._h, C.byref(c)))
         return c.value
+
+    # ------------------------------------------------- several maps, batched updates
+    def select(self, map_id):
+        """Make map `map_id` of the handle the one single-map calls act on."""
+        self._check(self._L.sbki_select_map(self._h, int(map_id)))
+        self.active = int(map_id)
+
+    def insert_batch(self, scans):
+        """One batched update: scans is a list of dict(points, labels, pose, map_id)
+        (numpy arrays or torch tensors); returns the batch's total stats."""
+        arr = (Scan * len(scans))()
+        keep = []
+        for i, sc in enumerate(scans):
+            pts = _as(sc["points"], np.float32, 3)
+            lab = _as(sc["labels"], np.int32)
+            pp, k1 = _ptr(pts)
+            lp, k2 = _ptr(lab)
+            keep += [pts, lab, k1, k2]
+            arr[i].points = pp
+            arr[i].labels = lp
+            arr[i].n = pts.shape[0]
+            T = np.ascontiguousarray(sc["pose"], dtype=np.float64).reshape(16)
+            for k in range(16):
+                arr[i].pose[k] = float(T[k])
+            arr[i].map_id = int(sc.get("map_id", 0))
+        s = Stats()
+        self._check(self._L.sbki_insert_batch(self._h, arr, len(scans), C.byref(s)))
+        return s.as_dict()
+
+    # ------------------------------------------------- differentiable form
+    def grad_clear(self):
+        """Zero the map's gradient buffer dL/dalpha."""
+        self._check(self._L.sbki_grad_clear(self._h))
+
+    def heldout_loglik(self, xyz, labels, grad=False):
+        """Held-out log-likelihood of world points with labels 0..K; with grad=True
+        dLL/dalpha is added into the map's gradient buffer."""
+        x = _as(xyz, np.float32, 3)
+        lab = _as(labels, np.int32)
+        xp, k1 = _ptr(x)
+        lp, k2 = _ptr(lab)
+        ll = C.c_double()
+        self._check(self._L.sbki_heldout_loglik(self._h, xp, lp, x.shape[0], int(bool(grad)), C.byref(ll)))
+        return ll.value
+
+    def grad_add_alpha(self, keys, grad_alpha):
+        """Add dL/dalpha given at voxel keys [n,3]; returns the rows no block holds."""
+        k = _as_i64(keys, 3)
+        gvals = _as(grad_alpha, np.float32, self.K1)
+        kp, k1 = _ptr(k)
+        gp, k2 = _ptr(gvals)
+        missed = C.c_int64()
+        self._check(self._L.sbki_grad_add_alpha(self._h, kp, gp, k.shape[0], C.byref(missed)))
+        return missed.value
+
+    def backward(self, xyzl, grad_xyz=True):
+        """(dL/dl, dL/dsigma0, dL/dxyz [p,3] or None) for the inserted training set
+        xyzl [p,4] (x, y, z, label); dL/dxyz is a CUDA tensor when xyzl is one."""
+        x = _as(xyzl, np.float32, 4)
+        p = x.shape[0]
+        xp, keep = _ptr(x)
+        gx = None
+        if grad_xyz:
+            if hasattr(x, "data_ptr") and getattr(x, "is_cuda", False):
+                import torch
+                gx = torch.empty((p, 3), dtype=torch.float32, device=x.device)
+            else:
+                gx = np.empty((max(p, 1), 3), np.float32)
+        gxp, keep2 = _ptr(gx)
+        gl, gs = C.c_double(), C.c_double()
+        self._check(self._L.sbki_backward(self._h, xp, p, C.byref(gl), C.byref(gs), gxp))
+        if gx is not None and not hasattr(gx, "data_ptr"):
+            gx = gx[:p]
+        return gl.value, gs.value, gx
 
     def export(self, pairs=False):
         """(keys int64 [n,3], alpha float32 [n,K+1], pairs int32 [n] or None), sorted by key."""

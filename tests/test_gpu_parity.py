@@ -313,3 +313,4 @@ def test_device_kernel_forms_match_fp64(sb, orc):
     assert np.max(np.abs(ft - ref)) < 3e-7
     assert np.max(np.abs(fp - ft)) < 3e-7
     assert np.all(sb.sbki.kernel_values(np.array([1.0, 1.5, 7.0], np.float32), 0) == 0.0)
+
