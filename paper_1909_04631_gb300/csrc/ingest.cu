@@ -12,6 +12,7 @@
 // The centroid of a cell is, per axis, the exact mean of its members'
 // coordinates rounded once to FP32 (see the centroid kernels).
 #include <algorithm>
+#include <climits>
 
 #include "sbki_internal.cuh"
 
@@ -34,13 +35,12 @@ __device__ __forceinline__ unsigned long long make_key(float x, float y, float z
   int tx = (gx >> kTileShift) - org[0];
   int ty = (gy >> kTileShift) - org[1];
   int tz = (gz >> kTileShift) - org[2];
-  const int lim = 1 << kf.bits;
-  if (tx < 0 || ty < 0 || tz < 0 || tx >= lim || ty >= lim || tz >= lim) {
+  if (tx < 0 || ty < 0 || tz < 0 || tx >= (1 << kf.bits[0]) || ty >= (1 << kf.bits[1]) || tz >= (1 << kf.bits[2])) {
     set_error(dc, SBKI_ERR_INVALID_ARG);
     tx = ty = tz = 0;
   }
-  unsigned long long tile = ((unsigned long long)tx << (2 * kf.bits)) | ((unsigned long long)ty << kf.bits) |
-                            (unsigned long long)tz;
+  const unsigned long long tile = ((unsigned long long)tx << (kf.bits[1] + kf.bits[2])) |
+                                  ((unsigned long long)ty << kf.bits[2]) | (unsigned long long)tz;
   unsigned long long local = (unsigned long long)(((gz & (kTileEdge - 1)) << (2 * kTileShift)) |
                                                   ((gy & (kTileEdge - 1)) << kTileShift) | (gx & (kTileEdge - 1)));
   const unsigned long long k = (((tile << kLocalBits) | local) << g.label_bits) | (unsigned long long)label;
@@ -80,7 +80,7 @@ __device__ __forceinline__ uint32_t free_count(float r, float s) {
 // a1 for global point i of scan d
 __device__ __forceinline__ void transform_count_one(const ScanDesc& d, int64_t i, const int64_t* off, const Geom& g,
                                                     float4* __restrict__ world, unsigned long long* __restrict__ cnt,
-                                                    DevCounters* dc) {
+                                                    DevCounters* dc, int tlo[3], int thi[3]) {
   const int64_t li = i - d.off;
   const float px = d.pts[3 * li], py = d.pts[3 * li + 1], pz = d.pts[3 * li + 2];
   const int lab = d.labels[li];
@@ -109,6 +109,12 @@ __device__ __forceinline__ void transform_count_one(const ScanDesc& d, int64_t i
       const float rr = __fsqrt_rn(r2);
       c = kValidOne | (unsigned long long)free_count(rr, g.step);
       w = make_float4(wc[0], wc[1], wc[2], (float)lab);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int t = floor_i(__fmul_rn(wc[a], g.inv_ds)) >> kTileShift;
+        tlo[a] = min(tlo[a], t);
+        thi[a] = max(thi[a], t);
+      }
     }
   }
   world[i] = w;
@@ -124,8 +130,18 @@ __global__ void __launch_bounds__(256) transform_count_kernel(const ScanDesc* __
   for (int t = threadIdx.x; t <= ns; t += blockDim.x) s_off[t] = desc[t].off;
   __syncthreads();
   const int64_t total = s_off[ns];
+  int tlo[3] = {INT_MAX, INT_MAX, INT_MAX}, thi[3] = {INT_MIN, INT_MIN, INT_MIN};
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
-    transform_count_one(desc[scan_of(s_off, ns, i)], i, s_off, g, world, cnt, dc);
+    transform_count_one(desc[scan_of(s_off, ns, i)], i, s_off, g, world, cnt, dc, tlo, thi);
+  // tile bounding box of the kept hits: one atomic per warp and bound
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int lo = __reduce_min_sync(0xffffffffu, tlo[a]), hi = __reduce_max_sync(0xffffffffu, thi[a]);
+    if ((threadIdx.x & 31) == 0 && lo <= hi) {
+      atomicMin(&dc->tbox[a], lo);
+      atomicMax(&dc->tbox[3 + a], hi);
+    }
+  }
 }
 
 __global__ void check_counts_kernel(const unsigned long long* cnt, int64_t cap, DevCounters* dc) {
@@ -415,6 +431,46 @@ __device__ float finish_axis(const AxisAcc& s, bool fits, U128 T, uint32_t n, co
   return wide_mean(items, perm, a, b, ax);
 }
 
+// Single-pass form for an axis whose first member x0 has |x0| >= 2.5 ds: every
+// member of the cell lies within ds (plus rounding) of x0, so it has x0's sign
+// and its last mantissa bit's exponent is within [e0 - 1, e0 + 1] (e0: x0's);
+// in units of 2^E, E = e0 - 1, every |x| is an integer below 2^26 and a 64-bit
+// sum is exact for fewer than 2^32 members.  Cells near a coordinate plane
+// (|x0| < 2.5 ds) take the two-pass AxisAcc path.
+struct FastAxis {
+  bool on, neg;
+  int E;
+  unsigned long long T;
+  __device__ void init(float x0, float lim) {
+    unsigned m;
+    int e;
+    on = fabsf(x0) >= lim && decompose(x0, m, e);
+    neg = x0 < 0.0f;
+    E = on ? e - 1 : 0;
+    T = 0ull;
+  }
+  __device__ void add(float v) {
+    unsigned m;
+    int e;
+    decompose(v, m, e);  // v != 0: |v| > ds
+    T += (unsigned long long)m << (e - E);
+  }
+  __device__ float finish(uint32_t n) const {
+    U128 t;
+    t.lo = T;
+    t.hi = 0ull;
+    float f = 0.0f;
+    round_mean(t, n, E, f);
+    return neg ? -f : f;
+  }
+};
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 __device__ __forceinline__ U128 warp_sum_u128(U128 t) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -455,26 +511,35 @@ __global__ void __launch_bounds__(256) centroid_kernel(const unsigned long long*
     const bool is_huge = valid && n > kHuge;
     if (is_huge) huge[atomicAdd(&dc->n_huge, 1u)] = s;
     AxisAcc ax[3];
+    FastAxis fa[3];
     U128 T[3];
-    bool fit[3];
+    bool fit[3] = {false, false, false};
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       ax[c].init();
       T[c].lo = T[c].hi = 0ull;
     }
     if (valid && n <= kShort) {
-      for (uint32_t i = a; i < b; ++i) {
-        const float4 p = items[perm[i]];
+      const float4 p0 = items[perm[a]];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) ax[c].see(axis_of(p, c));
+      for (int c = 0; c < 3; ++c) fa[c].init(axis_of(p0, c), g.fast_lim);
+      for (uint32_t i = a; i < b; ++i) {
+        const float4 p = i == a ? p0 : items[perm[i]];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          if (fa[c].on) fa[c].add(axis_of(p, c));
+          else ax[c].see(axis_of(p, c));
+        }
       }
+      if (!fa[0].on || !fa[1].on || !fa[2].on) {  // a cell next to a coordinate plane
 #pragma unroll
-      for (int c = 0; c < 3; ++c) fit[c] = ax[c].fits(n);
-      for (uint32_t i = a; i < b; ++i) {
-        const float4 p = items[perm[i]];
+        for (int c = 0; c < 3; ++c) fit[c] = !fa[c].on && ax[c].fits(n);
+        for (uint32_t i = a; i < b; ++i) {
+          const float4 p = items[perm[i]];
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-          if (fit[c]) ax[c].add(T[c], axis_of(p, c));
+          for (int c = 0; c < 3; ++c)
+            if (fit[c]) ax[c].add(T[c], axis_of(p, c));
+        }
       }
     }
     const bool is_mid = valid && n > kShort && !is_huge;
@@ -484,7 +549,8 @@ __global__ void __launch_bounds__(256) centroid_kernel(const unsigned long long*
       const int label = (int)(k & ((1ull << g.label_bits) - 1));
       float out[3];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) out[c] = finish_axis(ax[c], fit[c], T[c], n, items, perm, a, b, c);
+      for (int c = 0; c < 3; ++c)
+        out[c] = fa[c].on ? fa[c].finish(n) : finish_axis(ax[c], fit[c], T[c], n, items, perm, a, b, c);
       train[s] = make_float4(out[0], out[1], out[2], (float)(label + 32 * map_of_segment(k, kf, desc)));
     }
   }
@@ -508,34 +574,47 @@ __global__ void __launch_bounds__(256) mid_centroid_kernel(const unsigned long l
     const uint32_t s = mid[j];
     const uint32_t a = seg_start[s], b = seg_start[s + 1], n = b - a;
     AxisAcc w[3];
+    FastAxis fa[3];
     U128 t[3];
+    const float4 p0 = items[perm[a]];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       w[c].init();
       t[c].lo = t[c].hi = 0ull;
+      fa[c].init(axis_of(p0, c), g.fast_lim);
     }
+    const bool slow = !fa[0].on || !fa[1].on || !fa[2].on;  // warp-uniform
     for (uint32_t i = a + lane; i < b; i += 32) {
       const float4 p = items[perm[i]];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) w[c].see(axis_of(p, c));
-    }
-    bool fit[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      warp_range(w[c]);
-      fit[c] = w[c].fits(n);
-    }
-    for (uint32_t i = a + lane; i < b; i += 32) {
-      const float4 p = items[perm[i]];
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-        if (fit[c]) w[c].add(t[c], axis_of(p, c));
+      for (int c = 0; c < 3; ++c) {
+        if (fa[c].on) fa[c].add(axis_of(p, c));
+        else w[c].see(axis_of(p, c));
+      }
     }
 #pragma unroll
-    for (int c = 0; c < 3; ++c) t[c] = warp_sum_u128(t[c]);
+    for (int c = 0; c < 3; ++c)
+      if (fa[c].on) fa[c].T = warp_sum_u64(fa[c].T);
+    bool fit[3] = {false, false, false};
+    if (slow) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        warp_range(w[c]);
+        fit[c] = !fa[c].on && w[c].fits(n);
+      }
+      for (uint32_t i = a + lane; i < b; i += 32) {
+        const float4 p = items[perm[i]];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          if (fit[c]) w[c].add(t[c], axis_of(p, c));
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) t[c] = warp_sum_u128(t[c]);
+    }
     if (lane == 0) {
       float out[3];
-      for (int c = 0; c < 3; ++c) out[c] = finish_axis(w[c], fit[c], t[c], n, items, perm, a, b, c);
+      for (int c = 0; c < 3; ++c)
+        out[c] = fa[c].on ? fa[c].finish(n) : finish_axis(w[c], fit[c], t[c], n, items, perm, a, b, c);
       const unsigned long long k = keys[a];
       const int label = (int)(k & ((1ull << g.label_bits) - 1));
       train[s] = make_float4(out[0], out[1], out[2], (float)(label + 32 * map_of_segment(k, kf, desc)));
@@ -561,61 +640,88 @@ __global__ void __launch_bounds__(256) huge_centroid_kernel(const unsigned long 
     const uint32_t s = huge[h];
     const uint32_t a = seg_start[s], b = seg_start[s + 1], n = b - a;
     AxisAcc w[3];
+    FastAxis fa[3];
+    const float4 p0 = items[perm[a]];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) w[c].init();
-    for (uint32_t i = a + threadIdx.x; i < b; i += 256) {
-      const float4 p = items[perm[i]];
+    for (int c = 0; c < 3; ++c) {
+      w[c].init();
+      fa[c].init(axis_of(p0, c), g.fast_lim);
+    }
+    const bool slow = !fa[0].on || !fa[1].on || !fa[2].on;  // CTA-uniform
+    {
+      uint32_t i = a + threadIdx.x;
+      for (; i + 768 < b; i += 1024) {  // four independent gathers in flight
+        const float4 ps[4] = {items[perm[i]], items[perm[i + 256]], items[perm[i + 512]], items[perm[i + 768]]};
 #pragma unroll
-      for (int c = 0; c < 3; ++c) w[c].see(axis_of(p, c));
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            if (fa[c].on) fa[c].add(axis_of(ps[u], c));
+            else w[c].see(axis_of(ps[u], c));
+          }
+      }
+      for (; i < b; i += 256) {
+        const float4 p = items[perm[i]];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          if (fa[c].on) fa[c].add(axis_of(p, c));
+          else w[c].see(axis_of(p, c));
+        }
+      }
     }
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      warp_range(w[c]);
-      if (lane == 0) {
-        s_emin[c][warp] = w[c].emin;
-        s_emax[c][warp] = w[c].emax;
-        s_neg[c][warp] = w[c].neg ? 1 : 0;
+      if (fa[c].on) {
+        const unsigned long long tsum = warp_sum_u64(fa[c].T);
+        if (lane == 0) {
+          s_lo[c][warp] = tsum;
+          s_hi[c][warp] = 0ull;
+        }
       }
     }
-    __syncthreads();
-    bool fit[3];
+    bool fit[3] = {false, false, false};
+    if (slow) {  // an axis next to a coordinate plane: range first, then the 128-bit sums
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      int mn = 1 << 20, mx = -(1 << 20), ng = 0;
-      for (int k = 0; k < 8; ++k) {
-        mn = min(mn, s_emin[c][k]);
-        mx = max(mx, s_emax[c][k]);
-        ng |= s_neg[c][k];
+      for (int c = 0; c < 3; ++c) {
+        warp_range(w[c]);
+        if (lane == 0) {
+          s_emin[c][warp] = w[c].emin;
+          s_emax[c][warp] = w[c].emax;
+          s_neg[c][warp] = w[c].neg ? 1 : 0;
+        }
       }
-      w[c].emin = mn;
-      w[c].emax = mx;
-      w[c].neg = ng != 0;
-      fit[c] = w[c].fits(n);
-    }
-    U128 t[3];
+      __syncthreads();
 #pragma unroll
-    for (int c = 0; c < 3; ++c) t[c].lo = t[c].hi = 0ull;
-    uint32_t i = a + threadIdx.x;
-    for (; i + 768 < b; i += 1024) {  // four independent gathers in flight
-      const float4 ps[4] = {items[perm[i]], items[perm[i + 256]], items[perm[i + 512]], items[perm[i + 768]]};
+      for (int c = 0; c < 3; ++c) {
+        int mn = 1 << 20, mx = -(1 << 20), ng = 0;
+        for (int k = 0; k < 8; ++k) {
+          mn = min(mn, s_emin[c][k]);
+          mx = max(mx, s_emax[c][k]);
+          ng |= s_neg[c][k];
+        }
+        w[c].emin = mn;
+        w[c].emax = mx;
+        w[c].neg = ng != 0;
+        fit[c] = !fa[c].on && w[c].fits(n);
+      }
+      U128 t[3];
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int c = 0; c < 3; ++c) t[c].lo = t[c].hi = 0ull;
+      for (uint32_t i = a + threadIdx.x; i < b; i += 256) {
+        const float4 p = items[perm[i]];
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-          if (fit[c]) w[c].add(t[c], axis_of(ps[u], c));
-    }
-    for (; i < b; i += 256) {
-      const float4 p = items[perm[i]];
+          if (fit[c]) w[c].add(t[c], axis_of(p, c));
+      }
 #pragma unroll
-      for (int c = 0; c < 3; ++c)
-        if (fit[c]) w[c].add(t[c], axis_of(p, c));
-    }
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      t[c] = warp_sum_u128(t[c]);
-      if (lane == 0) {
-        s_lo[c][warp] = t[c].lo;
-        s_hi[c][warp] = t[c].hi;
+      for (int c = 0; c < 3; ++c) {
+        if (!fa[c].on) {
+          t[c] = warp_sum_u128(t[c]);
+          if (lane == 0) {
+            s_lo[c][warp] = t[c].lo;
+            s_hi[c][warp] = t[c].hi;
+          }
+        }
       }
     }
     __syncthreads();
@@ -625,7 +731,12 @@ __global__ void __launch_bounds__(256) huge_centroid_kernel(const unsigned long 
         U128 tt;
         tt.lo = tt.hi = 0ull;
         for (int k = 0; k < 8; ++k) u128_add(tt, s_lo[c][k], s_hi[c][k]);
-        out[c] = finish_axis(w[c], fit[c], tt, n, items, perm, a, b, c);
+        if (fa[c].on) {
+          fa[c].T = tt.lo;
+          out[c] = fa[c].finish(n);
+        } else {
+          out[c] = finish_axis(w[c], fit[c], tt, n, items, perm, a, b, c);
+        }
       }
       const unsigned long long k = keys[a];
       const int label = (int)(k & ((1ull << g.label_bits) - 1));

@@ -33,7 +33,7 @@ constexpr uint32_t kAgg = 1u << 30;   // word holds this tile's count of the dig
 constexpr uint32_t kPre = 2u << 30;   // word holds the count through this tile
 constexpr uint32_t kValue = kAgg - 1u;
 constexpr int kMaxSpin = 1 << 20;     // polls of unpublished status words before giving up
-constexpr int kWindow = 8;            // predecessors read at once in the look-back
+constexpr int kWindow = 16;           // predecessors read at once in the look-back
 
 // layout of the work area (uint32): [2][ntiles][256] status (ping-pong by pass),
 // [kMaxPasses][256] global digit counts, [kMaxPasses] tile counters

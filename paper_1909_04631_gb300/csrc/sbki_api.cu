@@ -101,6 +101,10 @@ __global__ void begin_kernel(DevCounters* dc, uint32_t epoch, uint32_t n_points)
   dc->work_next = 0;
   dc->epoch = epoch;
   dc->n_blocks_before = dc->n_blocks;
+  for (int a = 0; a < 3; ++a) {
+    dc->tbox[a] = INT_MAX;
+    dc->tbox[3 + a] = INT_MIN;
+  }
 }
 
 // begin_kernel for a batched update recorded in a graph: the epoch advances on
@@ -122,6 +126,10 @@ __global__ void batch_begin_kernel(DevCounters* dc, const ScanDesc* desc, int ns
   dc->epoch = dc->epoch + 1;
   dc->n_blocks_before = dc->n_blocks;
   dc->n_points = (uint32_t)desc[ns].off;
+  for (int a = 0; a < 3; ++a) {
+    dc->tbox[a] = INT_MAX;
+    dc->tbox[3 + a] = INT_MIN;
+  }
 }
 
 __global__ void bbox_init_kernel(int* bbox) {
@@ -185,6 +193,7 @@ Geom make_geom(const sbki_params& p) {
   g.l2_hi = (float)(p.length_scale * p.length_scale * (1.0 + band));
   g.sigma0 = (float)p.sigma0;
   g.step = (float)p.free_step;
+  g.fast_lim = (float)(2.5 * ds);
   g.res64 = p.res;
   g.l64 = p.length_scale;
   g.l2_64 = p.length_scale * p.length_scale;
@@ -203,16 +212,30 @@ KeyFrame scan_frame(const MapState& m, const double T[16]) {
   KeyFrame kf;
   const double ds = m.prm.ds_res > 0 ? m.prm.ds_res : m.prm.res;
   const int64_t half = (int64_t)std::ceil((m.prm.max_range + 2.0 * ds) / (kTileEdge * ds)) + 2;
-  kf.bits = ceil_log2(2 * half + 1);
+  kf.bits[0] = kf.bits[1] = kf.bits[2] = ceil_log2(2 * half + 1);
   for (int a = 0; a < 3; ++a) {
     const float o = (float)T[4 * a + 3];
     const float q = o * m.g.inv_ds;
     const int64_t gcell = (int64_t)std::floor(q);
     kf.org[a] = (int32_t)(floor_div64(gcell, kTileEdge) - half);
   }
-  kf.total_bits = 3 * kf.bits + kLocalBits + m.g.label_bits;
+  kf.total_bits = kf.bits[0] + kf.bits[1] + kf.bits[2] + kLocalBits + m.g.label_bits;
   kf.scan_bits = 0;
   return kf;
+}
+
+// Key frame of one scan fitted to its tile bounding box (kept hits and the
+// sensor origin, one tile of margin: every free sample lies on a segment
+// between the origin and a hit), so the sort covers fewer key bits.
+void tighten_frame(const MapState& m, const double T[16], KeyFrame& kf) {
+  const int32_t* tb = m.hc->tbox;
+  for (int a = 0; a < 3; ++a) {
+    const int64_t ot = floor_div64((int64_t)std::floor((float)T[4 * a + 3] * m.g.inv_ds), kTileEdge);
+    const int64_t lo = std::min<int64_t>(tb[a], ot) - 1, hi = std::max<int64_t>(tb[3 + a], ot) + 1;
+    kf.org[a] = (int32_t)lo;
+    kf.bits[a] = std::max(1, ceil_log2(hi - lo + 1));
+  }
+  kf.total_bits = kf.bits[0] + kf.bits[1] + kf.bits[2] + kLocalBits + m.g.label_bits;
 }
 
 // Descriptor of one scan (device point and label pointers).
@@ -336,6 +359,11 @@ sbki_status run_ingest(MapState& m, const float* points, const int32_t* labels, 
   if (m.hc->err != 0) return status_from_device(m);
   *nitems = m.hc->n_items;
   if (*nitems == 0) return SBKI_OK;
+  tighten_frame(m, T, kf);
+  m.hdesc[0].org[0] = kf.org[0];
+  m.hdesc[0].org[1] = kf.org[1];
+  m.hdesc[0].org[2] = kf.org[2];
+  CK(&m, cudaMemcpyAsync(m.s.desc, m.hdesc, sizeof(ScanDesc), cudaMemcpyHostToDevice, m.stream));
   CK(&m, launch_emit(m, 1, n, kf));
   CK(&m, launch_downsample_n(m, kf, *nitems));
   return SBKI_OK;
@@ -779,8 +807,8 @@ sbki_status sbki_insert_training(sbki_map* map, const float* xyzl, int64_t p, sb
     kf.org[a] = hb[a];
     ext = std::max<int64_t>(ext, (int64_t)hb[3 + a] - hb[a] + 1);
   }
-  kf.bits = std::max(1, ceil_log2(ext));
-  kf.total_bits = 3 * kf.bits + kLocalBits + m.g.label_bits;
+  kf.bits[0] = kf.bits[1] = kf.bits[2] = std::max(1, ceil_log2(ext));
+  kf.total_bits = kf.bits[0] + kf.bits[1] + kf.bits[2] + kLocalBits + m.g.label_bits;
   if (kf.total_bits > 64) return fail(&m, SBKI_ERR_INVALID_ARG, "training set spans too large a region");
   set_items_kernel<<<1, 1, 0, m.stream>>>(m.dc, (uint32_t)p);
   m.launches += 1;

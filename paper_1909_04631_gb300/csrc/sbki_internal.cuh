@@ -44,6 +44,7 @@ struct DevCounters {
   uint32_t n_huge;                    // downsampling cells summed by a whole CTA, this scan
   uint32_t n_mid;                     // downsampling cells summed by a warp, this scan
   uint32_t n_points;                  // input points of the update (all scans)
+  int32_t tbox[6];                    // ds-tile bounding box of the kept hits (min xyz, max xyz)
 };
 
 // ---------------------------------------------------------------- geometry constants
@@ -58,6 +59,7 @@ struct Geom {
   float l2_lo, l2_hi;      // l2 (1 -/+ band): outside, the fp32 test decides
   float sigma0;
   float step;              // fp32(free_step)
+  float fast_lim;          // 2.5 ds: cells with |x| above it take the single-pass exact mean
   double res64, l64, l2_64, min_range, max_range;
   int K1;                  // classes incl. free
   int B, B_shift, B3;      // block edge (power of two), log2, B^3
@@ -66,8 +68,8 @@ struct Geom {
 
 // Per-scan key frame: training-point tiles are packed relative to an origin tile.
 struct KeyFrame {
-  int32_t org[3];   // origin tile (ds-tile index) minus half range
-  int bits;         // bits per axis of a relative tile index
+  int32_t org[3];   // lowest tile (ds-tile index) of the region
+  int bits[3];      // bits of a relative tile index, per axis
   int total_bits;   // bits of a scan-local sort key (the scan index, if any, sits above)
   int scan_bits;    // bits of the scan index in a batched update (0: one scan)
 };

@@ -314,3 +314,29 @@ def test_device_kernel_forms_match_fp64(sb, orc):
     assert np.max(np.abs(fp - ft)) < 3e-7
     assert np.all(sb.sbki.kernel_values(np.array([1.0, 1.5, 7.0], np.float32), 0) == 0.0)
 
+
+
+# ------------------------------------------------------------ depth-camera workload
+
+def test_depth_frame_parity(sb, orc):
+    """A 640 x 480 depth frame of the room sequence (0.05 m voxels, l = 0.15 m,
+    11 classes): the whole frame's training set bit-exact; the map of a thinned
+    frame (every 7th pixel) and of two consecutive thinned frames against the
+    oracle (keys, pair counts exact, alpha within 1e-5)."""
+    frames = list(scenes.room_sequence(2))
+    prm = dict(scenes.ROOM_PARAMS)
+    m = _gpu_map(sb, prm, sample_capacity=1 << 24)  # 8.8M hits + free samples in the full frame
+    f0 = frames[0]
+    gx, gl = m.training_set(f0["points"], f0["labels"], f0["pose"])
+    ox, ol, _ = orc.training_set(orc.params(**prm), f0["points"], f0["labels"], f0["pose"])
+    gx, gl = _sorted_train(gx, gl)
+    ox, ol = _sorted_train(ox, ol)
+    np.testing.assert_array_equal(gl, ol)
+    np.testing.assert_array_equal(gx, ox)
+    om = orc.OracleMap(orc.params(**prm))
+    for f in frames:
+        pts, lab = f["points"][::7], f["labels"][::7]
+        st = m.insert_scan(pts, lab, f["pose"])
+        ost = om.insert_scan(pts, lab, f["pose"])
+        assert st["train_points"] == ost["train"]
+        _assert_export_equal(m, om)
