@@ -208,6 +208,58 @@ def _gen_diff(n_scans):
     return list(scenes.small_region_lidar_sequence(n_scans))
 
 
+def _gen_single():
+    return scenes.small_region_scan(0)
+
+
+def _gen_depth(n_frames):
+    return list(scenes.room_sequence(n_frames))
+
+
+def other_workloads(sb, torch, dev, stream, single, frames):
+    """The single-scan workload (fresh map per update) and the depth-camera
+    sequence (one map), device inputs, CUDA events."""
+    out = {}
+    p = sb.default_params(**scenes.SMALL_SCENE_PARAMS, pool_blocks=1 << 14, sample_capacity=1 << 22,
+                          device=dev.index)
+    pts, lab = torch.from_numpy(single["points"]).to(dev), torch.from_numpy(single["labels"]).to(dev)
+    maps = [sb.Map(p, stream=stream) for _ in range(12)]
+    times, st = [], None
+    for k, m in enumerate(maps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = m.insert_scan(pts, lab, single["pose"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if k >= 2:
+            times.append(e0.elapsed_time(e1))
+        m.close()
+    ms = float(np.median(times))
+    out["single_scan"] = {"workload": "one 100x100-ray scan of the 20x20x4 m region into a fresh map",
+                          "hits": st["hits"], "pairs": st["pairs"], "ms_per_scan": ms, "scans_per_s": 1e3 / ms,
+                          "pairs_per_s": st["pairs"] / (ms / 1e3)}
+    q = sb.default_params(**scenes.ROOM_PARAMS, pool_blocks=1 << 17, sample_capacity=1 << 24, device=dev.index)
+    dp = [torch.from_numpy(f["points"]).to(dev) for f in frames]
+    dl = [torch.from_numpy(f["labels"]).to(dev) for f in frames]
+    with sb.Map(q, stream=stream) as m:
+        for i in range(2):
+            m.insert_scan(dp[i], dl[i], frames[i]["pose"])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pairs = 0
+        for i in range(2, len(frames)):
+            pairs += m.insert_scan(dp[i], dl[i], frames[i]["pose"])["pairs"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / (len(frames) - 2)
+    out["depth_camera"] = {"workload": "640x480 depth frames of the room sequence (0.05 m voxels, l = 0.15 m, 11 classes)",
+                           "frames": len(frames) - 2, "ms_per_frame": ms, "frames_per_s": 1e3 / ms,
+                           "pairs_per_s": pairs / (len(frames) - 2) / (ms / 1e3)}
+    return out
+
+
 def batched_form(sb, torch, dev, stream, scans, reps):
     """Independent maps, one scan each: one batched update (recorded graph)
     against one sbki_insert_scan per scan, on the same GPU (device inputs)."""
@@ -230,7 +282,10 @@ def batched_form(sb, torch, dev, stream, scans, reps):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1) / reps
 
+    from paper_1909_04631_gb300 import autotune
+    tuned = autotune.autotune(p, batch, reps=2, stream=stream)
     seq = sb.Map(p, stream=stream)
+    seq.set_tuning(**tuned["tuning"])
 
     def run_seq():
         for i in range(n):
@@ -240,6 +295,7 @@ def batched_form(sb, torch, dev, stream, scans, reps):
     ms_seq = timed(run_seq)
     seq.close()
     bat = sb.Map(p, stream=stream)
+    bat.set_tuning(**tuned["tuning"])
     st = {}
 
     def run_batch():
@@ -253,7 +309,10 @@ def batched_form(sb, torch, dev, stream, scans, reps):
             "train_points": st.get("train_points"), "pairs": st.get("pairs"), "reps": reps,
             "sequential_ms": ms_seq, "batched_ms": ms_batch, "sequential_scans_per_s": n / (ms_seq / 1e3),
             "batched_scans_per_s": n / (ms_batch / 1e3), "speedup": ms_seq / ms_batch,
-            "batched_kernels_per_update": launches // (reps + 1)}
+            "batched_kernels_per_update": launches // (reps + 1), "tuning": tuned["tuning"],
+            "tuning_trials": len(tuned["trials"]),
+            "untuned_batched_ms": next((ms for t, ms in tuned["trials"] if t == dict(
+                accumulate_ctas_per_sm=0, accumulate_chunk=8, touch_ctas_per_sm=8, ingest_ctas_per_sm=16)), None)}
 
 
 def differentiable_form(sb, torch, dev, stream, scans, reps):
@@ -342,10 +401,12 @@ def run_ours(args, rank, world, local_rank):
     forms_input = None
     if rank == 0 and not args.no_forms:
         ctx = mp.get_context("spawn")
-        with ctx.Pool(2) as pool:
+        with ctx.Pool(4) as pool:
             fb = pool.apply_async(_gen_batch, (32,))
             fd = pool.apply_async(_gen_diff, (20,))
-            forms_input = (fb.get(), fd.get())
+            fs = pool.apply_async(_gen_single)
+            fr = pool.apply_async(_gen_depth, (12,))
+            forms_input = (fb.get(), fd.get(), fs.get(), fr.get())
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # the oracle on a bounded sample: 12 azimuth sectors of 45 degrees (scan 0
@@ -486,6 +547,7 @@ def run_ours(args, rank, world, local_rank):
     if forms_input is not None:
         line["batched"] = batched_form(sb, torch, dev, stream, forms_input[0], reps=5)
         line["differentiable"] = differentiable_form(sb, torch, dev, stream, forms_input[1], reps=3)
+        line["other_workloads"] = other_workloads(sb, torch, dev, stream, forms_input[2], forms_input[3])
     print(json.dumps(line), flush=True)
     return 0
 

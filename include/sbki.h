@@ -136,7 +136,7 @@ sbki_status sbki_training_set(sbki_map* map, const float* points, const int32_t*
  *   points [n,3] float32 and labels [n] int32 (1..K): DEVICE memory of
  *     params->device; xyzl_out [cap,4] float32: DEVICE memory, written as for
  *     sbki_training_set; *count (host) receives the number of points.
- * Every intermediate buffer lives in one fixed device array of about 8.9 MB
+ * Every intermediate buffer lives in one fixed device array of about 11 MB
  * that each GPU loading the library holds until the process exits; nothing
  * is allocated per call (no cudaMalloc, cudaFree or allocating library call).
  * Limits: n <= 16384 points (else SBKI_ERR_INVALID_ARG before any GPU work)
@@ -175,6 +175,21 @@ typedef struct sbki_scan {
  * Synchronises the stream once, at the end; stats are totals over the batch
  * (touched_voxels 0).  On any error no map changes. */
 sbki_status sbki_insert_batch(sbki_map* map, const sbki_scan* scans, int32_t count, sbki_stats* stats);
+
+/* Launch shapes of the update's kernels (all persistent grids): CTAs per SM
+ * for the accumulation (0 = as many as fit), training points per warp chunk
+ * in the accumulation (1..64), CTAs per SM for the touched-block pass and for
+ * the ingest kernels (transform, samples, segments, centroids).  Results do
+ * not depend on them; speed does.  sbki_set_tuning drops the recorded
+ * batched updates (they are recorded again with the new shapes). */
+typedef struct sbki_tuning {
+  int32_t accumulate_ctas_per_sm;
+  int32_t accumulate_chunk;
+  int32_t touch_ctas_per_sm;
+  int32_t ingest_ctas_per_sm;
+} sbki_tuning;
+sbki_status sbki_get_tuning(const sbki_map* map, sbki_tuning* out);
+sbki_status sbki_set_tuning(sbki_map* map, const sbki_tuning* tuning);
 
 /* Selects the map of the handle (0..num_maps-1) that sbki_insert_scan,
  * sbki_insert_scan_async, sbki_insert_training, sbki_query_probs,

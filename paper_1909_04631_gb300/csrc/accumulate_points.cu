@@ -3,11 +3,12 @@
 // centre within l, with one global floating-point reduction per pair.
 //
 // Candidate voxels come from a static table.  Split the voxel of a point into
-// 3x3x3 parts by the point's sub-voxel position; for each part the table
+// 8x8x8 parts by the point's sub-voxel position; for each part the table
 // lists every offset (dx, dy, dz) (relative to the point's voxel) whose centre
-// can lie within l of some position in that part, widened by 0.01 voxel on
+// can lie within l of some position in that part, widened by 0.001 voxel on
 // every side (so FP32 rounding of the position cannot pick too small a list).
-// For l = 3 res a list has at most 154 entries, against ~113 in support.
+// For l = 3 res a list has at most 136 entries (94 % of them at most 128, four
+// sweeps of 32), against ~113 in support.
 // Per point the warp
 //   1. forms the compensated offsets E0 = c(v0) - x of the point's own voxel
 //      centre (hi + lo per axis) and fills two per-warp lookup tables in
@@ -27,6 +28,7 @@
 // flight at any moment update a compact region of the map (L2 locality).
 // Blocks allocated by this update are zero-filled before (fresh_fill_kernel).
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <vector>
 
@@ -50,10 +52,12 @@ struct PtArgs {
   int64_t hash_cap;
   float* alpha;
   int32_t* pairs;
-  const uint32_t* ctab;  // [27][tpad] (X byte offset | YZ byte offset << 8 | dy << 19 | dz << 23)
+  const uint32_t* ctab;  // [kParts^3][tpad] (X byte offset | YZ byte offset << 8 | dy << 19 | dz << 23)
+  const int32_t* clen;   // [kParts^3] entries of each list
   int tpad;              // entries per list (multiple of 32)
   int R;                 // offsets per axis span [-R, R]
   uint32_t recip_na;     // small_recip(2R + 1)
+  int chunk;             // consecutive training points per warp (fast set-up form)
   DevCounters* dc;
 };
 
@@ -116,6 +120,7 @@ __global__ void __launch_bounds__(kThreads, 4) accumulate_points_kernel(PtArgs a
     const int label = lm & ((1 << kLabelBits) - 1), map = lm >> kLabelBits;
     const PointFrame f = point_frame(p.x, p.y, p.z, R, g);
     const uint32_t* tab = a.ctab + f.part * a.tpad;
+    const int len = __ldg(a.clen + f.part);
     // X rows
     if (lane < na) {
       const float e = centre_offset_at(lane - R, f.hi[0], f.lo[0], g);
@@ -149,13 +154,109 @@ __global__ void __launch_bounds__(kThreads, 4) accumulate_points_kernel(PtArgs a
     if (kNit > 0) {
       uint32_t ent[kNit > 0 ? kNit : 1];
 #pragma unroll
-      for (int it = 0; it < kNit; ++it) ent[it] = __ldg(tab + it * 32 + lane);
+      for (int it = 0; it < kNit; ++it) ent[it] = it * 32 < len ? __ldg(tab + it * 32 + lane) : 0u;
 #pragma unroll
-      for (int it = 0; it < kNit; ++it) npairs += candidate<kTrack>(a, t, ent[it], f.v0, p);
+      for (int it = 0; it < kNit; ++it)
+        if (it * 32 < len) npairs += candidate<kTrack>(a, t, ent[it], f.v0, p);  // warp-uniform
     } else {
-      for (int k = lane; k < a.tpad; k += 32) npairs += candidate<kTrack>(a, t, __ldg(tab + k), f.v0, p);
+      for (int k = lane; k - lane < len; k += 32) npairs += candidate<kTrack>(a, t, __ldg(tab + k), f.v0, p);
     }
     __syncwarp();  // the tables are rewritten for the next point
+  }
+  for (int o = 16; o > 0; o >>= 1) npairs += __shfl_down_sync(0xffffffffu, npairs, o);
+  if (lane == 0) atomicAdd(&a.dc->pairs, (unsigned long long)npairs);
+}
+
+// The same update with a cheaper per-point set-up, for 2R + 1 <= 8 (l up to
+// about 3 voxels): lanes 0-7, 8-15 and 16-23 each take one axis, form that
+// axis's compensated offsets and address parts for offsets -R..R themselves,
+// and hand the sub-voxel part and block of each axis to the warp by shuffles;
+// Y and Z rows combine into YZ rows by shuffles.  A warp takes kChunk
+// consecutive training points (sorted by tile, so mostly one block) and keeps
+// the pool slots of the 27 blocks around the last point's block, looking them
+// up again only when the block (or map) changes.
+
+template <bool kTrack, int kNit>
+__global__ void __launch_bounds__(kThreads, 4) accumulate_points_fast_kernel(PtArgs a) {
+  __shared__ WarpTables s_tab[kWarps];
+  const Geom& g = a.g;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  const int R = a.R, na = 2 * R + 1, m = g.B - 1;
+  WarpTables& t = s_tab[wid];
+  uint32_t npairs = 0;
+  if (a.dc->err != 0) return;
+  const uint32_t P = a.dc->n_train;
+  if (lane == 0) t.x[na] = make_float2(kFar, __int_as_float(0));
+  const int ax = min(lane >> 3, 2), j = lane & 7;  // this lane's axis and offset index
+  const int axshift = ax == 0 ? 0 : (ax == 1 ? g.B_shift : 2 * g.B_shift);
+  const int dmul = ax == 0 ? 1 : (ax == 1 ? 3 : 9);
+  int cb[3] = {INT_MIN, INT_MIN, INT_MIN}, cmap = -1;  // block and map the cached slots belong to
+  int32_t pool = -1;                                   // lanes 0..26: slot of block digit `lane`
+  const uint32_t chunk = (uint32_t)a.chunk;
+  for (uint32_t c = gw; c * chunk < P; c += nw) {
+    for (uint32_t k = 0; k < chunk; ++k) {
+      const uint32_t i = c * chunk + k;
+      if (i >= P) break;  // warp-uniform
+      const float4 p = a.train[i];
+      const int lm = label_of(p.w);
+      const int label = lm & ((1 << kLabelBits) - 1), map = lm >> kLabelBits;
+      // this lane's axis
+      const float xa = ax == 0 ? p.x : (ax == 1 ? p.y : p.z);
+      const int v0 = floor_small(__fmul_rn(xa, g.inv_res));
+      float hi, lo;
+      centre_offset0(v0, xa, g, hi, lo);
+      const float phi = 0.5f - __fmul_rn(__fadd_rn(hi, lo), g.inv_res);
+      const int pt = min(kParts - 1, max(0, floor_small(phi * (float)kParts)));
+      const int b0 = v0 >> g.B_shift;
+      const float e = centre_offset_at(j - R, hi, lo, g);
+      const int v = v0 + j - R;
+      const float sq = __fmul_rn(e, e);
+      const int pk = dmul * ((v >> g.B_shift) - (b0 - 1)) | ((v & m) << (axshift + 8));
+      if (lane < 8 && j < na) t.x[j] = make_float2(sq, __int_as_float(pk));
+      const int part = __shfl_sync(0xffffffffu, pt, 0) +
+                       kParts * (__shfl_sync(0xffffffffu, pt, 8) + kParts * __shfl_sync(0xffffffffu, pt, 16));
+      const int bx = __shfl_sync(0xffffffffu, b0, 0), by = __shfl_sync(0xffffffffu, b0, 8),
+                bz = __shfl_sync(0xffffffffu, b0, 16);
+      const int v0s[3] = {__shfl_sync(0xffffffffu, v0, 0), __shfl_sync(0xffffffffu, v0, 8),
+                          __shfl_sync(0xffffffffu, v0, 16)};
+      for (int q0 = 0; q0 < na * na; q0 += 32) {  // uniform trip count: full-warp shuffles
+        const int q = min(q0 + lane, na * na - 1);
+        const int jy = (int)small_div((uint32_t)q, a.recip_na), jz = q - jy * na;
+        const float sy = __shfl_sync(0xffffffffu, sq, 8 + jy), sz = __shfl_sync(0xffffffffu, sq, 16 + jz);
+        const int py = __shfl_sync(0xffffffffu, pk, 8 + jy), pz = __shfl_sync(0xffffffffu, pk, 16 + jz);
+        if (q0 + lane < na * na) t.yz[q] = make_float2(__fadd_rn(sy, sz), __int_as_float(py + pz));
+      }
+      if (bx != cb[0] || by != cb[1] || bz != cb[2] || map != cmap) {  // warp-uniform
+        cb[0] = bx;
+        cb[1] = by;
+        cb[2] = bz;
+        cmap = map;
+        pool = -1;
+        if (lane < 27)
+          pool = find_pool_slot(a.hkeys, a.hvals, a.hash_cap,
+                                pack_block(bx - 1 + lane % 3, by - 1 + (lane / 3) % 3, bz - 1 + lane / 9, map));
+      }
+      if (lane < 27) {
+        t.blk[lane] = pool >= 0 ? a.alpha + ((size_t)pool * g.K1 + label) * g.B3 : nullptr;
+        if (kTrack) t.cnt[lane] = pool >= 0 ? a.pairs + (size_t)pool * g.B3 : nullptr;
+      }
+      __syncwarp();
+      const uint32_t* tab = a.ctab + part * a.tpad;
+      const int len = __ldg(a.clen + part);
+      if (kNit > 0) {
+        uint32_t ent[kNit > 0 ? kNit : 1];
+#pragma unroll
+        for (int it = 0; it < kNit; ++it) ent[it] = it * 32 < len ? __ldg(tab + it * 32 + lane) : 0u;
+#pragma unroll
+        for (int it = 0; it < kNit; ++it)
+          if (it * 32 < len) npairs += candidate<kTrack>(a, t, ent[it], v0s, p);  // warp-uniform
+      } else {
+        for (int q = lane; q - lane < len; q += 32) npairs += candidate<kTrack>(a, t, __ldg(tab + q), v0s, p);
+      }
+      __syncwarp();  // the tables are rewritten for the next point
+    }
   }
   for (int o = 16; o > 0; o >>= 1) npairs += __shfl_down_sync(0xffffffffu, npairs, o);
   if (lane == 0) atomicAdd(&a.dc->pairs, (unsigned long long)npairs);
@@ -184,21 +285,25 @@ double min_axis_distance(int d, double lo, double hi) {
 
 }  // namespace
 
-// Candidate lists of the 27 sub-voxel parts (host, once per map).
+// Candidate lists of the kParts^3 sub-voxel parts (host, once per map).  The
+// parts are widened by delta = 1e-3 voxel, far above the FP32 error of the
+// sub-voxel position (~1e-6 voxel), so a point's list always holds its ball.
 cudaError_t build_candidate_tables(MapState& m) {
-  const double lr = m.prm.length_scale / m.prm.res, delta = 0.01;
+  const double lr = m.prm.length_scale / m.prm.res, delta = 1e-3;
   const int R = (int)std::ceil(lr + 0.5 + delta);
-  std::vector<std::vector<int32_t>> lists(27);
+  constexpr int kLists = kParts * kParts * kParts;
+  std::vector<std::vector<int32_t>> lists(kLists);
   size_t longest = 0;
-  for (int t = 0; t < 27; ++t) {
-    const int pt[3] = {t % 3, (t / 3) % 3, t / 9};
+  for (int t = 0; t < kLists; ++t) {
+    const int pt[3] = {t % kParts, (t / kParts) % kParts, t / (kParts * kParts)};
     for (int dz = -R; dz <= R; ++dz)
       for (int dy = -R; dy <= R; ++dy)
         for (int dx = -R; dx <= R; ++dx) {
           const int d[3] = {dx, dy, dz};
           double m2 = 0.0;
           for (int a = 0; a < 3; ++a) {
-            const double md = min_axis_distance(d[a], pt[a] / 3.0 - delta, (pt[a] + 1) / 3.0 + delta);
+            const double md =
+                min_axis_distance(d[a], (double)pt[a] / kParts - delta, (double)(pt[a] + 1) / kParts + delta);
             m2 += md * md;
           }
           if (m2 < lr * lr * (1.0 + 1e-5))
@@ -216,8 +321,10 @@ cudaError_t build_candidate_tables(MapState& m) {
   const int Rt = maxd, na = 2 * Rt + 1;
   if (na > kAxisMax) return cudaErrorInvalidValue;
   const int tpad = (int)((longest + 31) / 32 * 32);
-  std::vector<uint32_t> flat((size_t)27 * tpad, (uint32_t)(8 * na));
-  for (int t = 0; t < 27; ++t)
+  std::vector<uint32_t> flat((size_t)kLists * tpad, (uint32_t)(8 * na));
+  std::vector<int32_t> len(kLists);
+  for (int t = 0; t < kLists; ++t) len[t] = (int32_t)lists[t].size();
+  for (int t = 0; t < kLists; ++t)
     for (size_t k = 0; k < lists[t].size(); ++k) {
       const int32_t e = lists[t][k];
       const uint32_t jx = (uint32_t)((e & 15) - R + Rt), jy = (uint32_t)(((e >> 4) & 15) - R + Rt),
@@ -226,32 +333,46 @@ cudaError_t build_candidate_tables(MapState& m) {
     }
   cudaError_t e = cudaMalloc(&m.ctab, sizeof(uint32_t) * flat.size());
   if (e != cudaSuccess) return e;
+  e = cudaMalloc(&m.clen, sizeof(int32_t) * len.size());
+  if (e != cudaSuccess) return e;
   m.ctab_pad = tpad;
   m.ctab_R = Rt;
+  e = cudaMemcpy(m.clen, len.data(), sizeof(int32_t) * len.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
   return cudaMemcpy(m.ctab, flat.data(), sizeof(uint32_t) * flat.size(), cudaMemcpyHostToDevice);
 }
 
 namespace {
 
+// ctas_per_sm: 0 = as many as fit
 template <bool kTrack, int kNit>
-cudaError_t launch_points(const PtArgs& a, int sm_count, cudaStream_t st) {
+cudaError_t launch_points(const PtArgs& a, int sm_count, int ctas_per_sm, cudaStream_t st) {
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, accumulate_points_kernel<kTrack, kNit>,
-                                                                kThreads, 0);
-  if (e != cudaSuccess) return e;
-  accumulate_points_kernel<kTrack, kNit><<<std::max(1, per_sm) * sm_count, kThreads, 0, st>>>(a);
+  cudaError_t e;
+  if (2 * a.R + 1 <= 8) {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, accumulate_points_fast_kernel<kTrack, kNit>, kThreads,
+                                                      0);
+    if (e != cudaSuccess) return e;
+    if (ctas_per_sm > 0) per_sm = std::min(per_sm, ctas_per_sm);
+    accumulate_points_fast_kernel<kTrack, kNit><<<std::max(1, per_sm) * sm_count, kThreads, 0, st>>>(a);
+  } else {
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, accumulate_points_kernel<kTrack, kNit>, kThreads, 0);
+    if (e != cudaSuccess) return e;
+    if (ctas_per_sm > 0) per_sm = std::min(per_sm, ctas_per_sm);
+    accumulate_points_kernel<kTrack, kNit><<<std::max(1, per_sm) * sm_count, kThreads, 0, st>>>(a);
+  }
   return cudaGetLastError();
 }
 
 template <bool kTrack>
-cudaError_t launch_points_nit(const PtArgs& a, int sm_count, cudaStream_t st) {
+cudaError_t launch_points_nit(const PtArgs& a, int sm_count, int ctas_per_sm, cudaStream_t st) {
   switch (a.tpad / 32) {  // unrolled sweeps for the common list lengths
-    case 2: return launch_points<kTrack, 2>(a, sm_count, st);
-    case 3: return launch_points<kTrack, 3>(a, sm_count, st);
-    case 4: return launch_points<kTrack, 4>(a, sm_count, st);
-    case 5: return launch_points<kTrack, 5>(a, sm_count, st);
-    case 6: return launch_points<kTrack, 6>(a, sm_count, st);
-    default: return launch_points<kTrack, 0>(a, sm_count, st);
+    case 2: return launch_points<kTrack, 2>(a, sm_count, ctas_per_sm, st);
+    case 3: return launch_points<kTrack, 3>(a, sm_count, ctas_per_sm, st);
+    case 4: return launch_points<kTrack, 4>(a, sm_count, ctas_per_sm, st);
+    case 5: return launch_points<kTrack, 5>(a, sm_count, ctas_per_sm, st);
+    case 6: return launch_points<kTrack, 6>(a, sm_count, ctas_per_sm, st);
+    default: return launch_points<kTrack, 0>(a, sm_count, ctas_per_sm, st);
   }
 }
 
@@ -269,12 +390,16 @@ cudaError_t launch_accumulate_points(MapState& m) {
   a.alpha = m.alpha;
   a.pairs = m.pairs;
   a.ctab = m.ctab;
+  a.clen = m.clen;
   a.tpad = m.ctab_pad;
   a.R = m.ctab_R;
   a.recip_na = ((1u << 20) + (uint32_t)(2 * m.ctab_R + 1) - 1u) / (uint32_t)(2 * m.ctab_R + 1);
+  a.chunk = std::max(1, std::min(64, m.tune.accumulate_chunk));
   a.dc = m.dc;
   m.launches += 2;
-  return m.pairs ? launch_points_nit<true>(a, m.sm_count, m.stream) : launch_points_nit<false>(a, m.sm_count, m.stream);
+  const int cps = m.tune.accumulate_ctas_per_sm;
+  return m.pairs ? launch_points_nit<true>(a, m.sm_count, cps, m.stream)
+                 : launch_points_nit<false>(a, m.sm_count, cps, m.stream);
 }
 
 }  // namespace sbki

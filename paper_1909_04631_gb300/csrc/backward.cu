@@ -128,6 +128,7 @@ struct BwdArgs {
   int64_t hash_cap;
   const float* gpool;  // dL/dalpha, [pool][K1][B3]
   const uint32_t* ctab;
+  const int32_t* clen;
   int tpad, R;
   uint32_t recip_na;
   double* acc;         // [2]: sum G f, sum G u^4 D d
@@ -177,7 +178,8 @@ __global__ void __launch_bounds__(kThreads, 3) backward_kernel(BwdArgs a) {
     }
     __syncwarp();
     float sf = 0.f, sl = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
-    for (int k = lane; k < a.tpad; k += 32) {
+    const int len = __ldg(a.clen + f.part);
+    for (int k = lane; k - lane < len; k += 32) {  // warp-uniform trip count
       const uint32_t ent = __ldg(tab + k);
       const float4 ex = *reinterpret_cast<const float4*>(reinterpret_cast<const char*>(t.x) + 2u * (ent & 0xffu));
       const float4 eyz =
@@ -279,6 +281,7 @@ cudaError_t launch_backward(const MapState& m, const float4* xyzl, int64_t p, co
   a.hash_cap = m.hash_cap;
   a.gpool = gpool;
   a.ctab = m.ctab;
+  a.clen = m.clen;
   a.tpad = m.ctab_pad;
   a.R = m.ctab_R;
   a.recip_na = ((1u << 20) + (uint32_t)(2 * m.ctab_R + 1) - 1u) / (uint32_t)(2 * m.ctab_R + 1);

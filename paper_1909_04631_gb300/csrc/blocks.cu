@@ -305,7 +305,8 @@ cudaError_t launch_touch_blocks(MapState& m, const KeyFrame& /*kf*/, int64_t bou
   a.blist = m.blist;
   a.dc = m.dc;
   // bound: the training points never exceed the items of the update
-  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((bound + 255) / 256, (int64_t)m.sm_count * 8));
+  const int64_t blocks =
+      std::max<int64_t>(1, std::min<int64_t>((bound + 255) / 256, (int64_t)m.sm_count * m.tune.touch_ctas_per_sm));
   touch_kernel<<<(unsigned)blocks, 256, 0, m.stream>>>(a);
   m.launches += 1;
   return cudaGetLastError();
@@ -333,7 +334,8 @@ cudaError_t launch_bin_points(MapState& m, int64_t bound) {
   cudaError_t e = exclusive_scan_u32(m.boff, tb, m.s.scan_tmp, m.stream);
   if (e != cudaSuccess) return e;
   bin_cursor_kernel<<<m.sm_count * 4, 256, 0, m.stream>>>(m.s.touched, m.hcnt, m.hcur, m.boff, m.list_cap, m.dc);
-  const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>((bound + 255) / 256, (int64_t)m.sm_count * 8));
+  const int64_t blocks =
+      std::max<int64_t>(1, std::min<int64_t>((bound + 255) / 256, (int64_t)m.sm_count * m.tune.touch_ctas_per_sm));
   bin_fill_kernel<<<(unsigned)blocks, 256, 0, m.stream>>>(a);
   m.launches += 1 + 3 + 1 + 1;
   return cudaGetLastError();

@@ -281,6 +281,11 @@ struct U128 {
 
 __device__ __forceinline__ float axis_of(const float4& p, int ax) { return ax == 0 ? p.x : (ax == 1 ? p.y : p.z); }
 
+// member i of the sorted order: items already in sorted order (perm null) or gathered through perm
+__device__ __forceinline__ float4 item_at(const float4* __restrict__ items, const uint32_t* __restrict__ perm, uint32_t i) {
+  return perm ? items[perm[i]] : items[i];
+}
+
 // |v| = m 2^e (m < 2^24 integer); returns false for zero
 __device__ __forceinline__ bool decompose(float v, unsigned& m, int& e) {
   const unsigned b = __float_as_uint(v) & 0x7fffffffu;
@@ -382,7 +387,7 @@ __device__ float wide_mean(const float4* __restrict__ items, const uint32_t* __r
   for (int i = 0; i < 16; ++i) w[i] = 0u;
   bool neg = false;
   for (uint32_t i = a; i < b; ++i) {
-    const float v = axis_of(items[perm[i]], ax);
+    const float v = axis_of(item_at(items, perm, i), ax);
     unsigned m;
     int e;
     if (!decompose(v, m, e)) continue;
@@ -520,11 +525,11 @@ __global__ void __launch_bounds__(256) centroid_kernel(const unsigned long long*
       T[c].lo = T[c].hi = 0ull;
     }
     if (valid && n <= kShort) {
-      const float4 p0 = items[perm[a]];
+      const float4 p0 = item_at(items, perm, a);
 #pragma unroll
       for (int c = 0; c < 3; ++c) fa[c].init(axis_of(p0, c), g.fast_lim);
       for (uint32_t i = a; i < b; ++i) {
-        const float4 p = i == a ? p0 : items[perm[i]];
+        const float4 p = i == a ? p0 : item_at(items, perm, i);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           if (fa[c].on) fa[c].add(axis_of(p, c));
@@ -535,7 +540,7 @@ __global__ void __launch_bounds__(256) centroid_kernel(const unsigned long long*
 #pragma unroll
         for (int c = 0; c < 3; ++c) fit[c] = !fa[c].on && ax[c].fits(n);
         for (uint32_t i = a; i < b; ++i) {
-          const float4 p = items[perm[i]];
+          const float4 p = item_at(items, perm, i);
 #pragma unroll
           for (int c = 0; c < 3; ++c)
             if (fit[c]) ax[c].add(T[c], axis_of(p, c));
@@ -576,7 +581,7 @@ __global__ void __launch_bounds__(256) mid_centroid_kernel(const unsigned long l
     AxisAcc w[3];
     FastAxis fa[3];
     U128 t[3];
-    const float4 p0 = items[perm[a]];
+    const float4 p0 = item_at(items, perm, a);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       w[c].init();
@@ -585,7 +590,7 @@ __global__ void __launch_bounds__(256) mid_centroid_kernel(const unsigned long l
     }
     const bool slow = !fa[0].on || !fa[1].on || !fa[2].on;  // warp-uniform
     for (uint32_t i = a + lane; i < b; i += 32) {
-      const float4 p = items[perm[i]];
+      const float4 p = item_at(items, perm, i);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         if (fa[c].on) fa[c].add(axis_of(p, c));
@@ -603,7 +608,7 @@ __global__ void __launch_bounds__(256) mid_centroid_kernel(const unsigned long l
         fit[c] = !fa[c].on && w[c].fits(n);
       }
       for (uint32_t i = a + lane; i < b; i += 32) {
-        const float4 p = items[perm[i]];
+        const float4 p = item_at(items, perm, i);
 #pragma unroll
         for (int c = 0; c < 3; ++c)
           if (fit[c]) w[c].add(t[c], axis_of(p, c));
@@ -641,7 +646,7 @@ __global__ void __launch_bounds__(256) huge_centroid_kernel(const unsigned long 
     const uint32_t a = seg_start[s], b = seg_start[s + 1], n = b - a;
     AxisAcc w[3];
     FastAxis fa[3];
-    const float4 p0 = items[perm[a]];
+    const float4 p0 = item_at(items, perm, a);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       w[c].init();
@@ -651,7 +656,7 @@ __global__ void __launch_bounds__(256) huge_centroid_kernel(const unsigned long 
     {
       uint32_t i = a + threadIdx.x;
       for (; i + 768 < b; i += 1024) {  // four independent gathers in flight
-        const float4 ps[4] = {items[perm[i]], items[perm[i + 256]], items[perm[i + 512]], items[perm[i + 768]]};
+        const float4 ps[4] = {item_at(items, perm, i), item_at(items, perm, i + 256), item_at(items, perm, i + 512), item_at(items, perm, i + 768)};
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -661,7 +666,7 @@ __global__ void __launch_bounds__(256) huge_centroid_kernel(const unsigned long 
           }
       }
       for (; i < b; i += 256) {
-        const float4 p = items[perm[i]];
+        const float4 p = item_at(items, perm, i);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           if (fa[c].on) fa[c].add(axis_of(p, c));
@@ -708,7 +713,7 @@ __global__ void __launch_bounds__(256) huge_centroid_kernel(const unsigned long 
 #pragma unroll
       for (int c = 0; c < 3; ++c) t[c].lo = t[c].hi = 0ull;
       for (uint32_t i = a + threadIdx.x; i < b; i += 256) {
-        const float4 p = items[perm[i]];
+        const float4 p = item_at(items, perm, i);
 #pragma unroll
         for (int c = 0; c < 3; ++c)
           if (fit[c]) w[c].add(t[c], axis_of(p, c));
@@ -805,7 +810,7 @@ inline unsigned grid_for(int64_t n, int threads) { return (unsigned)((n + thread
 // Steps a1-a2 count for the ns scans described in m.s.desc; total_n bounds the
 // point count, which the kernels read on the device (dc->n_points, desc[ns].off).
 cudaError_t launch_transform_count(MapState& m, int ns, int64_t total_n) {
-  const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(total_n, 256), (int64_t)m.sm_count * 16));
+  const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(total_n, 256), (int64_t)m.sm_count * m.tune.ingest_ctas_per_sm));
   transform_count_kernel<<<blocks, 256, 0, m.stream>>>(m.s.desc, ns, m.g, m.s.world, m.s.cnt, m.dc);
   m.launches += 1 + 3 + 1;  // transform, scan, check
   cudaError_t e = exclusive_scan_u64(m.s.cnt, total_n, m.s.scan_tmp, m.stream, &m.dc->n_points);
@@ -816,7 +821,7 @@ cudaError_t launch_transform_count(MapState& m, int ns, int64_t total_n) {
 
 cudaError_t launch_emit(MapState& m, int ns, int64_t total_n, const KeyFrame& kf) {
   const int64_t warps = (total_n + 31) / 32;
-  unsigned blocks = (unsigned)std::min<int64_t>((warps + 7) / 8, (int64_t)m.sm_count * 16);
+  unsigned blocks = (unsigned)std::min<int64_t>((warps + 7) / 8, (int64_t)m.sm_count * m.tune.ingest_ctas_per_sm);
   if (blocks == 0) blocks = 1;
   emit_kernel<<<blocks, 256, 0, m.stream>>>(m.s.world, m.s.cnt, m.s.desc, ns, m.g, kf, m.s.items, m.s.keys, m.s.vals,
                                             m.dc);
@@ -830,22 +835,23 @@ cudaError_t launch_downsample_n(MapState& m, const KeyFrame& kf, int64_t nitems)
   Scratch& s = m.s;
   const int bits = kf.total_bits + kf.scan_bits;
   m.launches += 1 + (bits + 7) / 8 + 1 + 3 + 1 + 3;  // sort, segments, centroids
+  // the last pass also moves the items into sorted order (s.sitems), so the centroids read them in a stream
   cudaError_t e = radix_sort_pairs(s.keys, s.vals, s.keys2, s.vals2, &m.dc->n_items, nitems, bits, s.hist,
-                                   m.sm_count, m.dc, m.stream);
+                                   m.sm_count, m.dc, m.stream, s.items, s.sitems);
   if (e != cudaSuccess) return e;
-  const unsigned sblocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(nitems, 256), (int64_t)m.sm_count * 16));
+  const unsigned sblocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(nitems, 256), (int64_t)m.sm_count * m.tune.ingest_ctas_per_sm));
   seg_flags_kernel<<<sblocks, 256, 0, m.stream>>>(s.keys, nitems, s.flags, m.dc);
   e = exclusive_scan_u32(s.flags, nitems, s.scan_tmp, m.stream, &m.dc->n_items);
   if (e != cudaSuccess) return e;
   seg_start_kernel<<<sblocks, 256, 0, m.stream>>>(s.keys, nitems, s.flags, s.seg_start, m.dc);
   {
-    const unsigned cblocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((nitems + 255) / 256, (int64_t)m.sm_count * 16));
-    centroid_kernel<<<cblocks, 256, 0, m.stream>>>(s.keys, s.vals, s.items, s.seg_start, m.g, s.train, s.desc, kf,
+    const unsigned cblocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((nitems + 255) / 256, (int64_t)m.sm_count * m.tune.ingest_ctas_per_sm));
+    centroid_kernel<<<cblocks, 256, 0, m.stream>>>(s.keys, nullptr, s.sitems, s.seg_start, m.g, s.train, s.desc, kf,
                                                    s.huge, s.mid, m.dc);
-    mid_centroid_kernel<<<(unsigned)m.sm_count * 8, 256, 0, m.stream>>>(s.keys, s.vals, s.items, s.seg_start, m.g,
+    mid_centroid_kernel<<<(unsigned)(m.sm_count * std::max(1, m.tune.ingest_ctas_per_sm / 2)), 256, 0, m.stream>>>(s.keys, nullptr, s.sitems, s.seg_start, m.g,
                                                                         s.train, s.desc, kf, s.mid, m.dc);
     huge_centroid_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(nitems / kHuge + 1, 1024)), 256, 0,
-                           m.stream>>>(s.keys, s.vals, s.items, s.seg_start, m.g, s.train, s.desc, kf, s.huge, m.dc);
+                           m.stream>>>(s.keys, nullptr, s.sitems, s.seg_start, m.g, s.train, s.desc, kf, s.huge, m.dc);
   }
   return cudaGetLastError();
 }

@@ -15,7 +15,7 @@
 // Limits: at most kMaxPoints input points and kMaxItems hits + free samples
 // per call; larger inputs are rejected with SBKI_ERR_INVALID_ARG (points) or
 // SBKI_ERR_CAPACITY (items, known only after counting on the device).  The
-// array (kScratchBytes, about 8.9 MB) is reserved on every device that loads
+// array (kScratchBytes, about 11 MB) is reserved on every device that loads
 // the library, for the life of the process.  All calls share it and it keeps
 // the last call's contents; the device counters are cleared at the start of
 // each call, every other buffer is written before it is read.  Calls whose
@@ -40,7 +40,8 @@ constexpr size_t kOffCounters = 0;
 constexpr size_t kOffWorld = align256(kOffCounters + sizeof(sbki::DevCounters));
 constexpr size_t kOffCnt = align256(kOffWorld + 16 * kMaxPoints);
 constexpr size_t kOffItems = align256(kOffCnt + 8 * (kMaxPoints + 1));
-constexpr size_t kOffKeys = align256(kOffItems + 16 * kMaxItems);
+constexpr size_t kOffSitems = align256(kOffItems + 16 * kMaxItems);
+constexpr size_t kOffKeys = align256(kOffSitems + 16 * kMaxItems);
 constexpr size_t kOffKeys2 = align256(kOffKeys + 8 * kMaxItems);
 constexpr size_t kOffVals = align256(kOffKeys2 + 8 * kMaxItems);
 constexpr size_t kOffVals2 = align256(kOffVals + 4 * kMaxItems);
@@ -144,6 +145,7 @@ sbki_status run(const sbki_params* params, const float* points, const int32_t* l
   s.cnt = reinterpret_cast<unsigned long long*>(base + kOffCnt);
   s.n_cap = kMaxPoints;
   s.items = reinterpret_cast<float4*>(base + kOffItems);
+  s.sitems = reinterpret_cast<float4*>(base + kOffSitems);
   s.keys = reinterpret_cast<unsigned long long*>(base + kOffKeys);
   s.keys2 = reinterpret_cast<unsigned long long*>(base + kOffKeys2);
   s.vals = reinterpret_cast<uint32_t*>(base + kOffVals);

@@ -44,8 +44,8 @@ __device__ __forceinline__ int32_t find_pool_slot(const unsigned long long* hkey
 struct PointFrame {
   int v0[3];        // voxel of the point
   float hi[3], lo[3];  // compensated offset c(v0) - x per axis
-  int part;         // sub-voxel part 0..26 (thirds per axis)
-  int blo[3], nb[3];   // first block per axis and blocks spanned by v0 +- R
+  int part;         // sub-voxel part 0..kParts^3-1 (kParts per axis)
+  int blo[3], nb[3];   // the 3 x 3 x 3 blocks around the point's block: first block, count (3)
 };
 
 __device__ __forceinline__ PointFrame point_frame(float x, float y, float z, int R, const Geom& g) {
@@ -56,13 +56,14 @@ __device__ __forceinline__ PointFrame point_frame(float x, float y, float z, int
     const float xa = ax == 0 ? x : (ax == 1 ? y : z);
     f.v0[ax] = floor_small(__fmul_rn(xa, g.inv_res));
     centre_offset0(f.v0[ax], xa, g, f.hi[ax], f.lo[ax]);
-    // sub-voxel position 1/2 - E0/res (accurate anywhere in the map), in thirds
+    // sub-voxel position 1/2 - E0/res (accurate anywhere in the map), in kParts-ths
     const float phi = 0.5f - __fmul_rn(__fadd_rn(f.hi[ax], f.lo[ax]), g.inv_res);
-    pt[ax] = min(2, max(0, floor_small(phi * 3.0f)));
-    f.blo[ax] = (f.v0[ax] - R) >> g.B_shift;
-    f.nb[ax] = ((f.v0[ax] + R) >> g.B_shift) - f.blo[ax] + 1;
+    pt[ax] = min(kParts - 1, max(0, floor_small(phi * (float)kParts)));
+    // every voxel within R <= B of v0 lies in the point's block or a neighbour
+    f.blo[ax] = (f.v0[ax] >> g.B_shift) - 1;
+    f.nb[ax] = 3;
   }
-  f.part = pt[0] + 3 * pt[1] + 9 * pt[2];
+  f.part = pt[0] + kParts * (pt[1] + kParts * pt[2]);
   return f;
 }
 

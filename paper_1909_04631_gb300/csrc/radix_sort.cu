@@ -12,9 +12,12 @@
 //      look-back: a tile never waits on a later one, and every earlier tile
 //      was claimed by a running CTA, so the waits end; each wait is bounded
 //      and gives SBKI_ERR_TIMEOUT instead of spinning on);
-//   3. scatters its items stably: each warp ranks its 512 consecutive items
-//      (16 rounds of 32) with warp matches on the digit and its own digit
-//      counters, so equal keys keep their input order.
+//   3. scatters its items stably: each warp ranks its consecutive items
+//      (rounds of 32) with warp matches on the digit and its own digit
+//      counters, so equal keys keep their input order; the tile is staged in
+//      shared memory in sorted order and written out so that consecutive
+//      threads write consecutive positions of a digit's run.
+// The last pass can also move a float4 payload: payload_out[pos] = payload[value].
 // Destination of an item = (items of smaller digits) + (items of its digit in
 // earlier tiles) + (its rank among its digit in this tile).
 #include <algorithm>
@@ -76,14 +79,23 @@ __device__ __forceinline__ uint32_t load_volatile(const uint32_t* p) {
 }
 __device__ __forceinline__ void store_volatile(uint32_t* p, uint32_t v) { *reinterpret_cast<volatile uint32_t*>(p) = v; }
 
+constexpr size_t kStageBytes = (size_t)kRadixTile * (sizeof(unsigned long long) + sizeof(uint32_t));
+
 __global__ void __launch_bounds__(kThreads) onesweep_kernel(const unsigned long long* __restrict__ keys,
                                                             const uint32_t* __restrict__ vals,
                                                             unsigned long long* __restrict__ keys_out,
                                                             uint32_t* __restrict__ vals_out, const uint32_t* n_dev,
-                                                            int pass, int64_t ntiles, Work w, DevCounters* dc) {
+                                                            int pass, int64_t ntiles, Work w,
+                                                            const float4* __restrict__ payload,
+                                                            float4* __restrict__ payload_out, DevCounters* dc) {
+  extern __shared__ __align__(16) unsigned char s_stage[];  // the tile in sorted order: keys, then values
+  unsigned long long* s_k = reinterpret_cast<unsigned long long*>(s_stage);
+  uint32_t* s_v = reinterpret_cast<uint32_t*>(s_k + kRadixTile);
   __shared__ uint32_t s_dbase[kRadix];         // items of smaller digits (this pass)
   __shared__ uint32_t s_base[kRadix];          // first output position of each digit in this tile
-  __shared__ uint32_t s_wc[kWarps][kRadix];    // per warp: digit counts, then the warp's offset in the tile
+  __shared__ uint32_t s_tstart[kRadix];        // first position of each digit within the tile
+  __shared__ uint32_t s_wc[kWarps][kRadix];    // per warp: digit counts, then the warp's offset in the digit
+  __shared__ uint32_t s_wsum[kRadix / 32];
   __shared__ uint32_t s_tile;
   __shared__ int s_fail;
   const int shift = 8 * pass;
@@ -195,22 +207,49 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(const unsigned long 
         }
         store_volatile(my, kPre | (excl + cnt));
       }
-      s_base[threadIdx.x] = s_dbase[threadIdx.x] + excl;
+        s_base[threadIdx.x] = s_dbase[threadIdx.x] + excl;
+      // exclusive scan of the tile's digit counts (warps 0..7 hold the 256 digits)
+      uint32_t inc = cnt;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += u;
+      }
+      if (lane == 31) s_wsum[warp] = inc;
+      s_tstart[threadIdx.x] = inc - cnt;  // within the warp; warp offsets added below
     }
     __syncthreads();
     if (s_fail) {
       if (threadIdx.x == 0) set_error(dc, SBKI_ERR_TIMEOUT);
       break;
     }
-    // 3. scatter: digit base + the warp's offset within the digit + the item's rank
+    if (dthread) {
+      uint32_t off = 0;
+      for (int k = 0; k < warp; ++k) off += s_wsum[k];
+      s_tstart[threadIdx.x] += off;
+    }
+    __syncthreads();
+    // 3. stage the tile in sorted order in shared memory ...
 #pragma unroll
     for (int r = 0; r < kRounds; ++r) {
       if (wbase + r * 32 + lane < n) {
         const uint32_t d = (uint32_t)(kreg[r] >> shift) & (kRadix - 1);
-        const uint32_t pos = s_base[d] + s_wc[warp][d] + rreg[r];
-        keys_out[pos] = kreg[r];
-        vals_out[pos] = vreg[r];
+        const uint32_t lp = s_tstart[d] + s_wc[warp][d] + rreg[r];
+        s_k[lp] = kreg[r];
+        s_v[lp] = vreg[r];
       }
+    }
+    __syncthreads();
+    // ... and write it out: consecutive threads write consecutive positions of a digit's run
+    const int tile_n = (int)(n - t * kRadixTile < kRadixTile ? n - t * kRadixTile : kRadixTile);
+    for (int j = threadIdx.x; j < tile_n; j += kThreads) {
+      const unsigned long long key = s_k[j];
+      const uint32_t val = s_v[j];
+      const uint32_t d = (uint32_t)(key >> shift) & (kRadix - 1);
+      const uint32_t pos = s_base[d] + (uint32_t)j - s_tstart[d];
+      keys_out[pos] = key;
+      vals_out[pos] = val;
+      if (payload_out) payload_out[pos] = payload[val];
     }
   }
 }
@@ -221,7 +260,8 @@ int64_t radix_hist_entries(int64_t cap) { return radix_work_entries(cap); }
 
 cudaError_t radix_sort_pairs(unsigned long long*& keys, uint32_t*& vals, unsigned long long*& keys_alt,
                              uint32_t*& vals_alt, const uint32_t* n_dev, int64_t cap, int bits, uint32_t* hist,
-                             int sm_count, DevCounters* dc, cudaStream_t st) {
+                             int sm_count, DevCounters* dc, cudaStream_t st, const float4* payload,
+                             float4* payload_out) {
   if (cap <= 0 || bits <= 0) return cudaSuccess;
   const int passes = (bits + 7) / 8;
   if (passes > kMaxPasses) return cudaErrorInvalidValue;
@@ -232,12 +272,16 @@ cudaError_t radix_sort_pairs(unsigned long long*& keys, uint32_t*& vals, unsigne
   const int hgrid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)sm_count * 8));
   global_hist_kernel<<<hgrid, kHistThreads, 0, st>>>(keys, n_dev, passes, w, ntiles, dc);
   // persistent: as many CTAs as fit at once (tiles are claimed in order, so no CTA waits on one not running)
+  e = cudaFuncSetAttribute(onesweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStageBytes);
+  if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, onesweep_kernel, kThreads, 0);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, onesweep_kernel, kThreads, kStageBytes);
   if (e != cudaSuccess) return e;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)sm_count * std::max(1, per_sm)));
   for (int p = 0; p < passes; ++p) {
-    onesweep_kernel<<<grid, kThreads, 0, st>>>(keys, vals, keys_alt, vals_alt, n_dev, p, ntiles, w, dc);
+    const bool last = p == passes - 1;
+    onesweep_kernel<<<grid, kThreads, kStageBytes, st>>>(keys, vals, keys_alt, vals_alt, n_dev, p, ntiles, w,
+                                                         last ? payload : nullptr, last ? payload_out : nullptr, dc);
     std::swap(keys, keys_alt);
     std::swap(vals, vals_alt);
   }

@@ -520,6 +520,7 @@ sbki_status sbki_create_map(const sbki_params* params, sbki_map** out) {
   const int64_t S = params->sample_capacity;
   s.s_cap = S;
   if ((ce = dalloc(&s.items, S)) != cudaSuccess) return bail("items", ce);
+  if ((ce = dalloc(&s.sitems, S)) != cudaSuccess) return bail("sorted items", ce);
   if ((ce = dalloc(&s.keys, S)) != cudaSuccess) return bail("keys", ce);
   if ((ce = dalloc(&s.keys2, S)) != cudaSuccess) return bail("keys2", ce);
   if ((ce = dalloc(&s.vals, S)) != cudaSuccess) return bail("vals", ce);
@@ -561,7 +562,7 @@ void sbki_destroy_map(sbki_map* map) {
   {
     DeviceGuard dg(m.device);
     if (m.stream || m.dc) cudaStreamSynchronize(m.stream);
-    void* ptrs[] = {m.gpool, m.dacc, m.ctab, m.hkeys, m.hvals, m.hmark, m.hcnt, m.hcur, m.boff, m.blist, m.alpha, m.pool_keys, m.pairs, m.dc, m.s.items, m.s.keys, m.s.keys2,
+    void* ptrs[] = {m.clen, m.gpool, m.dacc, m.ctab, m.hkeys, m.hvals, m.hmark, m.hcnt, m.hcur, m.boff, m.blist, m.alpha, m.pool_keys, m.pairs, m.dc, m.s.items, m.s.sitems, m.s.keys, m.s.keys2,
                     m.s.vals, m.s.vals2, m.s.flags, m.s.seg_start, m.s.train, m.s.hist, m.s.scan_tmp, m.s.touched, m.s.fresh, m.s.bbox, m.s.huge, m.s.mid,
                     m.s.desc};
     for (void* p : ptrs)
@@ -581,6 +582,30 @@ void sbki_destroy_map(sbki_map* map) {
 sbki_status sbki_insert_scan(sbki_map* map, const float* points, const int32_t* labels, int64_t n,
                              const double sensor_pose[16], sbki_stats* stats) {
   return insert_scan_impl(map, points, labels, n, sensor_pose, true, stats);
+}
+
+sbki_status sbki_get_tuning(const sbki_map* map, sbki_tuning* out) {
+  if (!map || !out) return fail(nullptr, SBKI_ERR_INVALID_ARG, "bad arguments");
+  *out = map->st.tune;
+  return SBKI_OK;
+}
+
+sbki_status sbki_set_tuning(sbki_map* map, const sbki_tuning* t) {
+  if (!map || !t) return fail(nullptr, SBKI_ERR_INVALID_ARG, "bad arguments");
+  MapState& m = map->st;
+  if (t->accumulate_ctas_per_sm < 0 || t->accumulate_ctas_per_sm > 32 || t->accumulate_chunk < 1 ||
+      t->accumulate_chunk > 64 || t->touch_ctas_per_sm < 1 || t->touch_ctas_per_sm > 64 || t->ingest_ctas_per_sm < 1 ||
+      t->ingest_ctas_per_sm > 64)
+    return fail(&m, SBKI_ERR_INVALID_ARG, "tuning out of range");
+  DeviceGuard dg(m.device);
+  CK(&m, cudaStreamSynchronize(m.stream));
+  m.tune = *t;
+  for (int i = 0; i <= kMaxScans; ++i)
+    if (m.batch_exec[i]) {
+      cudaGraphExecDestroy(m.batch_exec[i]);
+      m.batch_exec[i] = nullptr;
+    }
+  return SBKI_OK;
 }
 
 sbki_status sbki_select_map(sbki_map* map, int32_t map_id) {

@@ -21,6 +21,7 @@ constexpr int kMaxProbes = 4096;         // hash probe bound (then SBKI_ERR_CAPA
 constexpr int kTileShift = 3;            // training-point tiles are 8^3 ds cells
 constexpr int kTileEdge = 1 << kTileShift;
 constexpr int kLocalBits = 3 * kTileShift;
+constexpr int kParts = 8;                // candidate lists: sub-voxel parts per axis (kParts^3 lists)
 
 // ---------------------------------------------------------------- device counters
 // One instance per map, in device memory; every kernel reads its sizes here so
@@ -98,6 +99,7 @@ struct Scratch {
   int64_t n_cap = 0;
   // per item (hits + free samples)
   float4* items = nullptr;        // [s_cap] xyz + label at source position
+  float4* sitems = nullptr;       // [s_cap] the items in sorted (scan, cell, label) order
   unsigned long long* keys = nullptr;   // [s_cap]
   unsigned long long* keys2 = nullptr;  // [s_cap]
   uint32_t* vals = nullptr;       // [s_cap] source positions
@@ -150,13 +152,15 @@ struct MapState {
   int64_t launches = 0;                 // kernels launched on this map
   int acc_mode = 0;                     // 0: point-major (global reductions), 1: block-major (shared tile)
   int active_map = 0;                   // map index the single-map calls act on
+  sbki_tuning tune{0, 8, 8, 16};        // launch shapes (sbki_set_tuning)
   cudaStream_t rec_stream = nullptr;    // private stream the batched update is recorded on
   cudaGraphExec_t batch_exec[kMaxScans + 1] = {};  // recorded batched updates, by scan count
   int64_t batch_kernels[kMaxScans + 1] = {};       // kernels in each recording
   uint64_t batch_gen[kMaxScans + 1] = {};          // scratch generation each recording used
   uint64_t scratch_gen = 1;             // advances when scratch buffers move
   ScanDesc* hdesc = nullptr;            // pinned host staging of s.desc
-  uint32_t* ctab = nullptr;             // point-major candidate lists [27][ctab_pad]
+  uint32_t* ctab = nullptr;             // point-major candidate lists [kParts^3][ctab_pad]
+  int32_t* clen = nullptr;              // [kParts^3] entries of each list
   float* gpool = nullptr;               // dL/dalpha [pool_blocks][K1][B3] (differentiable form, on first use)
   double* dacc = nullptr;               // [4]: held-out LL, sum G f, sum G u^4 D d, keys missed (as u64)
   int ctab_pad = 0, ctab_R = 0;
@@ -269,9 +273,11 @@ constexpr int kMaxPasses = 8;
 constexpr int64_t radix_work_entries(int64_t cap) {
   return 2 * 256 * ((cap + kRadixTile - 1) / kRadixTile) + kMaxPasses * 256 + kMaxPasses;
 }
+// The last pass also writes payload_out[pos] = payload[value] when payload_out is given.
 cudaError_t radix_sort_pairs(unsigned long long*& keys, uint32_t*& vals, unsigned long long*& keys_alt,
                              uint32_t*& vals_alt, const uint32_t* n_dev, int64_t cap, int bits, uint32_t* hist,
-                             int sm_count, DevCounters* dc, cudaStream_t st);
+                             int sm_count, DevCounters* dc, cudaStream_t st, const float4* payload = nullptr,
+                             float4* payload_out = nullptr);
 int64_t radix_hist_entries(int64_t cap);
 
 // ingest.cu

@@ -24,7 +24,8 @@ EXPORTED = ["sbki_default_params", "sbki_create_map", "sbki_destroy_map", "sbki_
             "sbki_insert_scan_async", "sbki_sync", "sbki_training_set", "sbki_insert_training", "sbki_query_probs",
             "sbki_voxel_count", "sbki_export", "sbki_profile", "sbki_profile_read", "sbki_kernel_values", "sbki_last_error", "sbki_status_string",
             "sbki_training_set_noalloc", "sbki_grad_clear", "sbki_heldout_loglik", "sbki_grad_add_alpha",
-            "sbki_backward", "sbki_forward_alpha", "sbki_grad", "sbki_insert_batch", "sbki_select_map"]
+            "sbki_backward", "sbki_forward_alpha", "sbki_grad", "sbki_insert_batch", "sbki_select_map",
+            "sbki_get_tuning", "sbki_set_tuning"]
 
 
 class SbkiError(RuntimeError):
@@ -45,6 +46,14 @@ class Params(C.Structure):
 class Scan(C.Structure):
     _fields_ = [("points", C.c_void_p), ("labels", C.c_void_p), ("n", C.c_int64), ("pose", C.c_double * 16),
                 ("map_id", C.c_int32)]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("accumulate_ctas_per_sm", C.c_int32), ("accumulate_chunk", C.c_int32),
+                ("touch_ctas_per_sm", C.c_int32), ("ingest_ctas_per_sm", C.c_int32)]
+
+    def as_dict(self):
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
 
 
 class ProfileData(C.Structure):
@@ -97,6 +106,8 @@ def load(build_if_missing: bool = True):
         L.sbki_query_probs.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp]
         L.sbki_insert_batch.argtypes = [vp, vp, i32, P(Stats)]
         L.sbki_select_map.argtypes = [vp, i32]
+        L.sbki_get_tuning.argtypes = [vp, P(Tuning)]
+        L.sbki_set_tuning.argtypes = [vp, P(Tuning)]
         L.sbki_grad_clear.argtypes = [vp]
         L.sbki_heldout_loglik.argtypes = [vp, vp, vp, i64, i32, P(C.c_double)]
         L.sbki_grad_add_alpha.argtypes = [vp, vp, vp, i64, P(i64)]
@@ -119,7 +130,7 @@ def load(build_if_missing: bool = True):
                   "sbki_training_set", "sbki_insert_training", "sbki_query_probs", "sbki_voxel_count",
                   "sbki_export", "sbki_training_set_noalloc", "sbki_grad_clear", "sbki_heldout_loglik",
                   "sbki_grad_add_alpha", "sbki_backward", "sbki_forward_alpha", "sbki_grad", "sbki_insert_batch",
-                  "sbki_select_map"):
+                  "sbki_select_map", "sbki_get_tuning", "sbki_set_tuning"):
             getattr(L, f).restype = C.c_int
         _lib = L
         return L
@@ -370,6 +381,21 @@ class Map:
         c = C.c_int64()
         self._check(self._L.sbki_voxel_count(self._h, C.byref(c)))
         return c.value
+
+    # ------------------------------------------------- launch shapes
+    def get_tuning(self):
+        t = Tuning()
+        self._check(self._L.sbki_get_tuning(self._h, C.byref(t)))
+        return t.as_dict()
+
+    def set_tuning(self, **kw):
+        t = Tuning()
+        self._check(self._L.sbki_get_tuning(self._h, C.byref(t)))
+        for k, v in kw.items():
+            if not hasattr(t, k):
+                raise TypeError("unknown tuning field %r" % k)
+            setattr(t, k, int(v))
+        self._check(self._L.sbki_set_tuning(self._h, C.byref(t)))
 
     # ------------------------------------------------- several maps, batched updates
     def select(self, map_id):

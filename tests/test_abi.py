@@ -54,7 +54,7 @@ def test_struct_layouts_match_the_c_compiler(tmp_path):
     """Offsets and sizes of the ctypes structures equal those gcc gives the header's structs."""
     from paper_1909_04631_gb300 import sbki
     structs = {"sbki_params": sbki.Params, "sbki_stats": sbki.Stats, "sbki_profile_data": sbki.ProfileData,
-               "sbki_scan": sbki.Scan}
+               "sbki_scan": sbki.Scan, "sbki_tuning": sbki.Tuning}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "sbki.h"', "int main(void) {"]
     for cname, py in structs.items():
         lines.append('printf("%s %%zu\\n", sizeof(%s));' % (cname, cname))

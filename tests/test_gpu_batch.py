@@ -137,3 +137,26 @@ def test_batch_errors_leave_maps_unchanged(sb, scans):
     k1, a1, _ = m.export()
     np.testing.assert_array_equal(k0, k1)
     np.testing.assert_array_equal(a0, a1)
+
+
+def test_tuning_changes_speed_not_results(sb, scans):
+    from paper_1909_04631_gb300 import autotune
+    outs = []
+    for tune in (dict(accumulate_ctas_per_sm=1, accumulate_chunk=1, touch_ctas_per_sm=1, ingest_ctas_per_sm=1),
+                 dict(accumulate_ctas_per_sm=0, accumulate_chunk=16, touch_ctas_per_sm=8, ingest_ctas_per_sm=16)):
+        m = sb.Map(_params(sb, 3))
+        m.set_tuning(**tune)
+        assert m.get_tuning() == tune
+        m.insert_batch(_as_batch(scans[:3], [0, 1, 2]))
+        m.insert_batch(_as_batch(scans[2:5], [0, 1, 2]))  # replays the recording made with this tuning
+        outs.append([(m.select(i), m.export(pairs=True))[1] for i in range(3)])
+    for (k1, a1, p1), (k2, a2, p2) in zip(*outs):
+        np.testing.assert_array_equal(k1, k2)
+        np.testing.assert_array_equal(p1, p2)
+        np.testing.assert_allclose(a1, a2, rtol=RTOL)
+    res = autotune.autotune(_params(sb, 3), _as_batch(scans[:3], [0, 1, 2]),
+                            candidates=dict(accumulate_ctas_per_sm=(0, 2), accumulate_chunk=(4,), touch_ctas_per_sm=(8,),
+                                            ingest_ctas_per_sm=(16,)), reps=1)
+    assert len(res["trials"]) == 2 and res["tuning"] in [t for t, _ in res["trials"]] and res["ms"] > 0
+    with pytest.raises(sb.SbkiError):
+        sb.Map(_params(sb, 1)).set_tuning(accumulate_chunk=0)
