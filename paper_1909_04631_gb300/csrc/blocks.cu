@@ -80,57 +80,6 @@ __device__ int64_t find_block(const TouchArgs& a, unsigned long long key) {
   return -1;
 }
 
-// per axis: smallest |e| over the block's voxels, e(j) = E0 + j res with E0
-// the compensated offset of the block's first voxel centre (hi + lo)
-__device__ __forceinline__ float axis_min32(float hi, float lo, const Geom& g, int& jbest) {
-  int j = (int)floorf(__fmul_rn(-hi, g.inv_res) + 0.5f);
-  j = min(max(j, 0), g.B - 1);
-  float best = 3.0e38f;
-  jbest = j;
-#pragma unroll
-  for (int d = -1; d <= 1; ++d) {
-    const int jj = j + d;
-    if (jj < 0 || jj >= g.B) continue;
-    const float e = fabsf(centre_offset_at(jj, hi, lo, g));
-    if (e < best) {
-      best = e;
-      jbest = jj;
-    }
-  }
-  return best;
-}
-
-__device__ __forceinline__ double axis_min64(int K0, int jc, float x, const Geom& g) {
-  double best = 1.0e300;
-  for (int d = -2; d <= 2; ++d) {
-    const int jj = jc + d;
-    if (jj < 0 || jj >= g.B) continue;
-    const double e = fabs(__dsub_rn(__dmul_rn(__dadd_rn((double)(K0 + jj), 0.5), g.res64), (double)x));
-    best = fmin(best, e);
-  }
-  return best;
-}
-
-// Does the block with first voxel K0 hold a voxel centre within l of x?
-__device__ bool touches_block(const int K0[3], const float xs[3], const Geom& g) {
-  float m[3];
-  int jb[3];
-#pragma unroll
-  for (int ax = 0; ax < 3; ++ax) {
-    float hi, lo;
-    centre_offset0(K0[ax], xs[ax], g, hi, lo);
-    m[ax] = axis_min32(hi, lo, g, jb[ax]);
-  }
-  const float d2 = __fmaf_rn(m[0], m[0], __fmaf_rn(m[1], m[1], __fmul_rn(m[2], m[2])));
-  if (d2 < g.l2_lo) return true;
-  if (!(d2 < g.l2_hi)) return false;
-  const double ex = axis_min64(K0[0], jb[0], xs[0], g);
-  const double ey = axis_min64(K0[1], jb[1], xs[1], g);
-  const double ez = axis_min64(K0[2], jb[2], xs[2], g);
-  const double d64 = __dadd_rn(__dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey)), __dmul_rn(ez, ez));
-  return d64 < g.l2_64;
-}
-
 // candidate block range of a point: at most 3 blocks per axis (l <= 0.75 B res)
 __device__ void candidate_blocks(const float xs[3], const Geom& g, int blo[3], int bhi[3]) {
   const float lw = __fmul_rn(sqrtf(g.l2_hi), 1.001f);
@@ -143,12 +92,74 @@ __device__ void candidate_blocks(const float xs[3], const Geom& g, int blo[3], i
   }
 }
 
+// Per point and axis, for each candidate block k on that axis: the squared
+// offset to the block's voxel nearest the point along the axis (the point's
+// own voxel index clamped into the block), from compensated offsets.  A block
+// holds a voxel centre within l iff the sum over the axes is below l^2: the
+// FP32 sum decides outside the relative band around l^2, FP64 (also trying
+// the clamped voxel's neighbours) inside it.
+struct PointBlocks {
+  float xs[3];
+  int v0[3], blo[3], nb[3], vn[3][3];
+  float m2[3][3];
+};
+
+__device__ __forceinline__ void point_blocks(const float4& p, const Geom& g, PointBlocks& pb) {
+  pb.xs[0] = p.x;
+  pb.xs[1] = p.y;
+  pb.xs[2] = p.z;
+  int bhi[3];
+  candidate_blocks(pb.xs, g, pb.blo, bhi);
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    pb.nb[ax] = bhi[ax] - pb.blo[ax] + 1;
+    pb.v0[ax] = floor_i(__fmul_rn(pb.xs[ax], g.inv_res));
+    float hi, lo;
+    centre_offset0(pb.v0[ax], pb.xs[ax], g, hi, lo);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int first = (pb.blo[ax] + k) << g.B_shift;
+      const int vn = min(max(pb.v0[ax], first), first + g.B - 1);
+      const float e = centre_offset_at(vn - pb.v0[ax], hi, lo, g);
+      pb.vn[ax][k] = vn;
+      pb.m2[ax][k] = __fmul_rn(e, e);
+    }
+  }
+}
+
+__device__ __forceinline__ double axis_min64_near(int vn, int first, const Geom& g, float x) {
+  double best = 1.0e300;
+#pragma unroll
+  for (int d = -1; d <= 1; ++d) {
+    const int v = vn + d;
+    if (v < first || v >= first + g.B) continue;
+    best = fmin(best, fabs(__dsub_rn(__dmul_rn(__dadd_rn((double)v, 0.5), g.res64), (double)x)));
+  }
+  return best;
+}
+
+// Does candidate block (kx, ky, kz) (indices into the point's ranges) hold a voxel centre within l?
+__device__ bool touches(const PointBlocks& pb, int kx, int ky, int kz, const Geom& g) {
+  const float d2 = __fadd_rn(__fadd_rn(pb.m2[0][kx], pb.m2[1][ky]), pb.m2[2][kz]);
+  if (d2 < g.l2_lo) return true;
+  if (!(d2 < g.l2_hi)) return false;
+  const int k[3] = {kx, ky, kz};
+  double s = 0.0;
+#pragma unroll
+  for (int ax = 0; ax < 3; ++ax) {
+    const double e = axis_min64_near(pb.vn[ax][k[ax]], (pb.blo[ax] + k[ax]) << g.B_shift, g, pb.xs[ax]);
+    s = __dadd_rn(s, __dmul_rn(e, e));
+  }
+  return s < g.l2_64;
+}
+
 // Every lane walks the same cube of candidate blocks around the block of its
 // point (warp-uniform trip count, at most 3x3x3), so the warp-wide match that
 // lets one lane insert a block reached by several lanes always sees all 32
 // lanes.  The
 // inserting lane also adds the number of lanes that touch the block to its
 // point count (used to lay out the per-block point lists).
+template <bool kCount>
 __global__ void __launch_bounds__(256) touch_kernel(TouchArgs a) {
   const Geom& g = a.g;
   if (a.dc->err != 0) return;
@@ -156,34 +167,30 @@ __global__ void __launch_bounds__(256) touch_kernel(TouchArgs a) {
   for (uint32_t base = blockIdx.x * blockDim.x; base < P; base += gridDim.x * blockDim.x) {  // warp-uniform
     const uint32_t i = base + threadIdx.x;
     const bool active = i < P;
-    float xs[3] = {0.f, 0.f, 0.f};
-    int blo[3] = {0, 0, 0}, bhi[3] = {-1, -1, -1};
+    PointBlocks pb;
     int map = 0;
     if (active) {
       const float4 p = a.train[i];
-      xs[0] = p.x;
-      xs[1] = p.y;
-      xs[2] = p.z;
       map = (int)p.w >> kLabelBits;
-      candidate_blocks(xs, g, blo, bhi);
+      point_blocks(p, g, pb);
+    } else {
+      pb.nb[0] = pb.nb[1] = pb.nb[2] = 0;
+      pb.blo[0] = pb.blo[1] = pb.blo[2] = 0;
     }
     // the warp walks the smallest cube of candidate offsets that covers every lane
-    const int mx = __reduce_max_sync(0xffffffffu, (unsigned)max(0, bhi[0] - blo[0] + 1));
-    const int my = __reduce_max_sync(0xffffffffu, (unsigned)max(0, bhi[1] - blo[1] + 1));
-    const int mz = __reduce_max_sync(0xffffffffu, (unsigned)max(0, bhi[2] - blo[2] + 1));
+    const int mx = __reduce_max_sync(0xffffffffu, (unsigned)pb.nb[0]);
+    const int my = __reduce_max_sync(0xffffffffu, (unsigned)pb.nb[1]);
+    const int mz = __reduce_max_sync(0xffffffffu, (unsigned)pb.nb[2]);
     const int nc = mx * my * mz;
     for (int c = 0; c < nc; ++c) {
-      const int bx = blo[0] + c % mx, by = blo[1] + (c / mx) % my, bz = blo[2] + c / (mx * my);
-      bool hit = bx <= bhi[0] && by <= bhi[1] && bz <= bhi[2];
-      if (hit) {
-        const int K0[3] = {bx << g.B_shift, by << g.B_shift, bz << g.B_shift};
-        hit = touches_block(K0, xs, g);
-      }
-      const unsigned long long key = hit ? pack_block(bx, by, bz, map) : kEmpty;
+      const int kx = c % mx, ky = (c / mx) % my, kz = c / (mx * my);
+      const bool hit = kx < pb.nb[0] && ky < pb.nb[1] && kz < pb.nb[2] && touches(pb, kx, ky, kz, g);
+      const unsigned long long key =
+          hit ? pack_block(pb.blo[0] + kx, pb.blo[1] + ky, pb.blo[2] + kz, map) : kEmpty;
       const unsigned peers = __match_any_sync(0xffffffffu, key);
       if (hit && (unsigned)(__ffs(peers) - 1) == (threadIdx.x & 31u)) {
         const int64_t slot = insert_block(a, key);
-        if (slot >= 0) atomicAdd(&a.hcnt[slot], (uint32_t)__popc(peers));
+        if (kCount && slot >= 0) atomicAdd(&a.hcnt[slot], (uint32_t)__popc(peers));
       }
     }
   }
@@ -198,31 +205,27 @@ __global__ void __launch_bounds__(256) bin_fill_kernel(TouchArgs a) {
   for (uint32_t base = blockIdx.x * blockDim.x; base < P; base += gridDim.x * blockDim.x) {  // warp-uniform
     const uint32_t i = base + threadIdx.x;
     const bool active = i < P;
-    float xs[3] = {0.f, 0.f, 0.f};
-    int blo[3] = {0, 0, 0}, bhi[3] = {-1, -1, -1};
+    PointBlocks pb;
     int map = 0;
     if (active) {
       const float4 p = a.train[i];
-      xs[0] = p.x;
-      xs[1] = p.y;
-      xs[2] = p.z;
       map = (int)p.w >> kLabelBits;
-      candidate_blocks(xs, g, blo, bhi);
+      point_blocks(p, g, pb);
+    } else {
+      pb.nb[0] = pb.nb[1] = pb.nb[2] = 0;
+      pb.blo[0] = pb.blo[1] = pb.blo[2] = 0;
     }
     const uint32_t lane_lt = (1u << (threadIdx.x & 31u)) - 1u;
-    // the warp walks the smallest cube of candidate offsets that covers every lane
-    const int mx = __reduce_max_sync(0xffffffffu, (unsigned)max(0, bhi[0] - blo[0] + 1));
-    const int my = __reduce_max_sync(0xffffffffu, (unsigned)max(0, bhi[1] - blo[1] + 1));
-    const int mz = __reduce_max_sync(0xffffffffu, (unsigned)max(0, bhi[2] - blo[2] + 1));
+    // the same walk as touch_kernel, so the same blocks
+    const int mx = __reduce_max_sync(0xffffffffu, (unsigned)pb.nb[0]);
+    const int my = __reduce_max_sync(0xffffffffu, (unsigned)pb.nb[1]);
+    const int mz = __reduce_max_sync(0xffffffffu, (unsigned)pb.nb[2]);
     const int nc = mx * my * mz;
     for (int c = 0; c < nc; ++c) {
-      const int bx = blo[0] + c % mx, by = blo[1] + (c / mx) % my, bz = blo[2] + c / (mx * my);
-      bool hit = bx <= bhi[0] && by <= bhi[1] && bz <= bhi[2];
-      if (hit) {
-        const int K0[3] = {bx << g.B_shift, by << g.B_shift, bz << g.B_shift};
-        hit = touches_block(K0, xs, g);
-      }
-      const unsigned long long key = hit ? pack_block(bx, by, bz, map) : kEmpty;
+      const int kx = c % mx, ky = (c / mx) % my, kz = c / (mx * my);
+      const bool hit = kx < pb.nb[0] && ky < pb.nb[1] && kz < pb.nb[2] && touches(pb, kx, ky, kz, g);
+      const unsigned long long key =
+          hit ? pack_block(pb.blo[0] + kx, pb.blo[1] + ky, pb.blo[2] + kz, map) : kEmpty;
       const unsigned peers = __match_any_sync(0xffffffffu, key);
       const int leader = __ffs(peers) - 1;
       uint32_t base = 0;
@@ -307,7 +310,8 @@ cudaError_t launch_touch_blocks(MapState& m, const KeyFrame& /*kf*/, int64_t bou
   // bound: the training points never exceed the items of the update
   const int64_t blocks =
       std::max<int64_t>(1, std::min<int64_t>((bound + 255) / 256, (int64_t)m.sm_count * m.tune.touch_ctas_per_sm));
-  touch_kernel<<<(unsigned)blocks, 256, 0, m.stream>>>(a);
+  if (m.acc_mode == 1) touch_kernel<true><<<(unsigned)blocks, 256, 0, m.stream>>>(a);  // counts for the block lists
+  else touch_kernel<false><<<(unsigned)blocks, 256, 0, m.stream>>>(a);
   m.launches += 1;
   return cudaGetLastError();
 }
