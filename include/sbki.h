@@ -295,6 +295,25 @@ sbki_status sbki_forward_alpha(const sbki_params* params, const float* xyzl, int
 sbki_status sbki_grad(const sbki_params* params, const float* xyzl, int64_t p, const int64_t* keys,
                       const float* grad_alpha, int64_t count, double* grad_l, double* grad_sigma0, float* grad_xyz);
 
+/* Restores contents written by sbki_export into the selected map (a snapshot
+ * and resume path): keys [count,3] int64 voxel indices, alpha [count,K+1]
+ * float32 with prior (host or device).  The block of every key is created if
+ * missing and the voxel's increments are set to alpha - alpha0 (one FP32
+ * subtraction, so a re-export equals the snapshot to an ulp); other voxels of
+ * created blocks read the prior, voxels not listed keep their values.  An
+ * increment below half an ulp of alpha0 is already lost in the exported alpha
+ * (alpha0 + increment rounds to alpha0), so such a voxel is restored with no
+ * kernel mass and reads as unknown.  Pair counts are not restored.  SBKI_ERR_CAPACITY (pool full) leaves the block
+ * set unchanged. */
+sbki_status sbki_import(sbki_map* map, const int64_t* keys, const float* alpha, int64_t count);
+
+/* Failure-detection self-test on `device` (diagnostic): runs the segment pass
+ * of the downsampling step on a small input whose first tile is never
+ * processed, so every bounded wait on it runs out (about a second); the
+ * kernel reports SBKI_ERR_TIMEOUT in *device_status instead of spinning, and
+ * the context stays usable.  Returns SBKI_OK when the test itself ran. */
+sbki_status sbki_selftest_bounded_wait(int32_t device, int32_t* device_status);
+
 /* Message of the last failure on this map (or of the last sbki_create_map
  * failure when map is NULL). */
 const char* sbki_last_error(const sbki_map* map);

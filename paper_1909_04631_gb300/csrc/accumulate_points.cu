@@ -378,6 +378,13 @@ cudaError_t launch_points_nit(const PtArgs& a, int sm_count, int ctas_per_sm, cu
 
 }  // namespace
 
+cudaError_t launch_fresh_fill(MapState& m) {
+  fresh_fill_kernel<<<m.sm_count * 4, 256, 0, m.stream>>>(m.s.fresh, m.hvals, m.alpha, m.pairs, m.g.K1 * m.g.B3,
+                                                          m.g.B3, m.dc);
+  m.launches += 1;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_accumulate_points(MapState& m) {
   fresh_fill_kernel<<<m.sm_count * 4, 256, 0, m.stream>>>(m.s.fresh, m.hvals, m.alpha, m.pairs, m.g.K1 * m.g.B3,
                                                           m.g.B3, m.dc);

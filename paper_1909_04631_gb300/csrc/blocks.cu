@@ -291,6 +291,58 @@ __global__ void commit_counts_kernel(int64_t pool_blocks, DevCounters* dc) {
   dc->n_blocks = nb + dc->n_new;
 }
 
+// Restoring exported contents: the blocks of the given voxel keys (warp-deduplicated
+// inserts, like touch_kernel), then the voxels' increments alpha - alpha0.
+__global__ void __launch_bounds__(256) import_blocks_kernel(TouchArgs a, const int64_t* __restrict__ keys,
+                                                            int64_t count, int map) {
+  const Geom& g = a.g;
+  if (a.dc->err != 0) return;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < count; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = base + threadIdx.x;
+    unsigned long long key = kEmpty;
+    if (q < count) {
+      const int64_t kx = keys[3 * q], ky = keys[3 * q + 1], kz = keys[3 * q + 2];
+      if (kx <= -kKeyLimit || kx >= kKeyLimit || ky <= -kKeyLimit || ky >= kKeyLimit || kz <= -kKeyLimit ||
+          kz >= kKeyLimit)
+        set_error(a.dc, SBKI_ERR_INVALID_ARG);
+      else
+        key = pack_block((int32_t)(kx >> g.B_shift), (int32_t)(ky >> g.B_shift), (int32_t)(kz >> g.B_shift), map);
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    if (key != kEmpty && (unsigned)(__ffs(peers) - 1) == (threadIdx.x & 31u)) insert_block(a, key);
+  }
+}
+
+__global__ void __launch_bounds__(256) import_alpha_kernel(Geom g, const unsigned long long* __restrict__ hkeys,
+                                                           const int32_t* __restrict__ hvals, int64_t hash_cap,
+                                                           const int64_t* __restrict__ keys,
+                                                           const float* __restrict__ alpha, int64_t count, int map,
+                                                           float alpha0, float* __restrict__ pool,
+                                                           DevCounters* dc) {
+  if (dc->err != 0) return;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < count; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t kx = keys[3 * q], ky = keys[3 * q + 1], kz = keys[3 * q + 2];
+    const unsigned long long bkey =
+        pack_block((int32_t)(kx >> g.B_shift), (int32_t)(ky >> g.B_shift), (int32_t)(kz >> g.B_shift), map);
+    uint32_t slot = hash_slot(bkey, hash_cap);
+    int32_t pl = -1;
+    for (int probe = 0; probe < kMaxProbes; ++probe) {
+      const unsigned long long k = hkeys[slot];
+      if (k == bkey) {
+        pl = hvals[slot];
+        break;
+      }
+      if (k == kEmpty) break;
+      slot = (uint32_t)((slot + 1) & (uint32_t)(hash_cap - 1));
+    }
+    if (pl < 0) continue;
+    const int m = g.B - 1;
+    const int local = ((((int)kz & m) << g.B_shift) + ((int)ky & m)) * g.B + ((int)kx & m);
+    float* dst = pool + (size_t)pl * g.K1 * g.B3 + local;
+    for (int k = 0; k < g.K1; ++k) dst[(size_t)k * g.B3] = __fsub_rn(alpha[q * g.K1 + k], alpha0);
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_touch_blocks(MapState& m, const KeyFrame& /*kf*/, int64_t bound) {
@@ -342,6 +394,32 @@ cudaError_t launch_bin_points(MapState& m, int64_t bound) {
       std::max<int64_t>(1, std::min<int64_t>((bound + 255) / 256, (int64_t)m.sm_count * m.tune.touch_ctas_per_sm));
   bin_fill_kernel<<<(unsigned)blocks, 256, 0, m.stream>>>(a);
   m.launches += 1 + 3 + 1 + 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_import(MapState& m, const int64_t* keys, const float* alpha, int64_t count) {
+  TouchArgs a;
+  a.g = m.g;
+  a.train = nullptr;
+  a.hkeys = m.hkeys;
+  a.hvals = m.hvals;
+  a.hmark = m.hmark;
+  a.hash_cap = m.hash_cap;
+  a.touched = m.s.touched;
+  a.fresh = m.s.fresh;
+  a.hcnt = m.hcnt;
+  a.hcur = m.hcur;
+  a.blist = m.blist;
+  a.dc = m.dc;
+  const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((count + 255) / 256, (int64_t)m.sm_count * 8));
+  import_blocks_kernel<<<blocks, 256, 0, m.stream>>>(a, keys, count, m.active_map);
+  cudaError_t e = launch_commit_blocks(m);
+  if (e != cudaSuccess) return e;
+  e = launch_fresh_fill(m);
+  if (e != cudaSuccess) return e;
+  import_alpha_kernel<<<blocks, 256, 0, m.stream>>>(m.g, m.hkeys, m.hvals, m.hash_cap, keys, alpha, count,
+                                                    m.active_map, (float)m.prm.alpha0, m.alpha, m.dc);
+  m.launches += 2;
   return cudaGetLastError();
 }
 

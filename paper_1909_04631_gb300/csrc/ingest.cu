@@ -127,20 +127,27 @@ __global__ void __launch_bounds__(256) transform_count_kernel(const ScanDesc* __
                                                                float4* __restrict__ world,
                                                                unsigned long long* __restrict__ cnt, DevCounters* dc) {
   __shared__ int64_t s_off[kMaxScans + 1];
+  __shared__ int s_box[6];
   for (int t = threadIdx.x; t <= ns; t += blockDim.x) s_off[t] = desc[t].off;
+  if (threadIdx.x < 6) s_box[threadIdx.x] = threadIdx.x < 3 ? INT_MAX : INT_MIN;
   __syncthreads();
   const int64_t total = s_off[ns];
   int tlo[3] = {INT_MAX, INT_MAX, INT_MAX}, thi[3] = {INT_MIN, INT_MIN, INT_MIN};
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
     transform_count_one(desc[scan_of(s_off, ns, i)], i, s_off, g, world, cnt, dc, tlo, thi);
-  // tile bounding box of the kept hits: one atomic per warp and bound
+  // tile bounding box of the kept hits: warp, then CTA, then one global atomic per CTA and bound
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const int lo = __reduce_min_sync(0xffffffffu, tlo[a]), hi = __reduce_max_sync(0xffffffffu, thi[a]);
     if ((threadIdx.x & 31) == 0 && lo <= hi) {
-      atomicMin(&dc->tbox[a], lo);
-      atomicMax(&dc->tbox[3 + a], hi);
+      atomicMin(&s_box[a], lo);
+      atomicMax(&s_box[3 + a], hi);
     }
+  }
+  __syncthreads();
+  if (threadIdx.x < 3 && s_box[threadIdx.x] <= s_box[3 + threadIdx.x]) {
+    atomicMin(&dc->tbox[threadIdx.x], s_box[threadIdx.x]);
+    atomicMax(&dc->tbox[3 + threadIdx.x], s_box[3 + threadIdx.x]);
   }
 }
 
@@ -235,25 +242,115 @@ __global__ void __launch_bounds__(256) emit_kernel(const float4* __restrict__ wo
   }
 }
 
-// segment heads of the sorted items (count read on the device, at most cap)
-__global__ void seg_flags_kernel(const unsigned long long* __restrict__ keys, int64_t cap, uint32_t* __restrict__ flags,
-                                 const DevCounters* dc) {
-  if (dc->err) return;
-  const int64_t n = min(cap, (int64_t)dc->n_items);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    flags[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1u : 0u;
-}
+// Segments of the sorted items in one pass: tiles of kSegTile items are claimed
+// in order; each counts its segment heads (key differs from its predecessor),
+// publishes the count, finds the heads before it by a warp-wide look-back over
+// up to 32 preceding tiles at once (bounded waits, SBKI_ERR_TIMEOUT), and
+// writes seg_start[head index] = item index.  The tile holding the last item
+// writes seg_start[P] = n and the segment count P.  work: [ntiles] status words
+// then a tile counter, zero on entry.
+constexpr int kSegThreads = 512;
+constexpr int kSegPer = 8;
+constexpr int kSegTile = kSegThreads * kSegPer;
+constexpr uint32_t kSegAgg = 1u << 30, kSegPre = 2u << 30, kSegVal = kSegAgg - 1u;
 
-__global__ void seg_start_kernel(const unsigned long long* __restrict__ keys, int64_t cap,
-                                 const uint32_t* __restrict__ segid, uint32_t* __restrict__ seg_start,
-                                 DevCounters* dc) {
+__global__ void __launch_bounds__(kSegThreads) seg_heads_kernel(const unsigned long long* __restrict__ keys,
+                                                               int64_t cap, uint32_t* __restrict__ seg_start,
+                                                               uint32_t* __restrict__ work, int64_t ntiles_cap,
+                                                               DevCounters* dc) {
+  __shared__ uint32_t s_wsum[kSegThreads / 32];
+  __shared__ uint32_t s_tile, s_excl;
+  __shared__ int s_fail;
   if (dc->err) return;
   const int64_t n = min(cap, (int64_t)dc->n_items);
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    if (i == 0 || keys[i] != keys[i - 1]) seg_start[segid[i]] = (uint32_t)i;
-    if (i == n - 1) {
-      seg_start[segid[n]] = (uint32_t)n;
-      dc->n_train = segid[n];
+  const int64_t nt = (n + kSegTile - 1) / kSegTile;
+  uint32_t* status = work;
+  uint32_t* counter = work + ntiles_cap;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_tile = atomicAdd(counter, 1u);
+      s_fail = 0;
+    }
+    __syncthreads();
+    const int64_t t = s_tile;
+    if (t >= nt) break;
+    const int64_t first = t * kSegTile + (int64_t)threadIdx.x * kSegPer;
+    uint32_t heads = 0;  // bit k: item first + k starts a segment
+    unsigned long long prev = first > 0 && first <= n ? keys[first - 1] : 0ull;
+#pragma unroll
+    for (int k = 0; k < kSegPer; ++k) {
+      const int64_t i = first + k;
+      if (i < n) {
+        const unsigned long long key = keys[i];
+        if (i == 0 || key != prev) heads |= 1u << k;
+        prev = key;
+      }
+    }
+    // exclusive prefix of the head counts over the CTA's threads
+    const uint32_t c = __popc(heads);
+    uint32_t inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t u = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += u;
+    }
+    if (lane == 31) s_wsum[warp] = inc;
+    __syncthreads();
+    uint32_t wpre = 0, total = 0;
+#pragma unroll
+    for (int k = 0; k < kSegThreads / 32; ++k) {
+      const uint32_t v = s_wsum[k];
+      wpre += k < warp ? v : 0u;
+      total += v;
+    }
+    // the tile's place among all heads: publish, then one warp looks back 32 tiles at a time
+    if (warp == 0) {
+      uint32_t excl = 0;
+      if (t == 0) {
+        if (lane == 0) *reinterpret_cast<volatile uint32_t*>(status) = kSegPre | total;
+      } else {
+        if (lane == 0) *reinterpret_cast<volatile uint32_t*>(status + t) = kSegAgg | total;
+        int64_t j = t - 1;
+        int spins = 0;
+        for (;;) {
+          const int64_t q = j - lane;
+          const uint32_t v = q >= 0 ? *reinterpret_cast<const volatile uint32_t*>(status + q) : kSegPre;
+          const unsigned pre = __ballot_sync(0xffffffffu, (v & kSegPre) != 0);
+          const unsigned ready = __ballot_sync(0xffffffffu, (v & (kSegAgg | kSegPre)) != 0);
+          const int stop = pre ? __ffs(pre) - 1 : 31;  // nearest inclusive prefix in the window
+          const unsigned need = stop == 31 ? 0xffffffffu : ((2u << stop) - 1u);
+          if ((ready & need) == need) {  // every word up to it is published
+            uint32_t part = lane <= stop ? (v & kSegVal) : 0u;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+            excl += part;
+            if (pre) break;
+            j -= 32;
+          } else if (++spins > (1 << 20)) {
+            if (lane == 0) s_fail = 1;
+            break;
+          } else {
+            __nanosleep(20);
+          }
+        }
+        if (lane == 0) *reinterpret_cast<volatile uint32_t*>(status + t) = kSegPre | (excl + total);
+      }
+      if (lane == 0) s_excl = excl;
+    }
+    __syncthreads();
+    if (s_fail) {
+      if (threadIdx.x == 0) set_error(dc, SBKI_ERR_TIMEOUT);
+      break;
+    }
+    uint32_t idx = s_excl + wpre + inc - c;
+#pragma unroll
+    for (int k = 0; k < kSegPer; ++k)
+      if (heads & (1u << k)) seg_start[idx++] = (uint32_t)(first + k);
+    if (first <= n - 1 && n - 1 < first + kSegPer) {  // this thread holds the last item
+      seg_start[s_excl + total] = (uint32_t)n;
+      dc->n_train = s_excl + total;
     }
   }
 }
@@ -834,16 +931,21 @@ cudaError_t launch_emit(MapState& m, int ns, int64_t total_n, const KeyFrame& kf
 cudaError_t launch_downsample_n(MapState& m, const KeyFrame& kf, int64_t nitems) {
   Scratch& s = m.s;
   const int bits = kf.total_bits + kf.scan_bits;
-  m.launches += 1 + (bits + 7) / 8 + 1 + 3 + 1 + 3;  // sort, segments, centroids
+  m.launches += 1 + (bits + 7) / 8 + 1 + 3;  // sort, segments, centroids
   // the last pass also moves the items into sorted order (s.sitems), so the centroids read them in a stream
   cudaError_t e = radix_sort_pairs(s.keys, s.vals, s.keys2, s.vals2, &m.dc->n_items, nitems, bits, s.hist,
                                    m.sm_count, m.dc, m.stream, s.items, s.sitems);
   if (e != cudaSuccess) return e;
-  const unsigned sblocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(nitems, 256), (int64_t)m.sm_count * m.tune.ingest_ctas_per_sm));
-  seg_flags_kernel<<<sblocks, 256, 0, m.stream>>>(s.keys, nitems, s.flags, m.dc);
-  e = exclusive_scan_u32(s.flags, nitems, s.scan_tmp, m.stream, &m.dc->n_items);
-  if (e != cudaSuccess) return e;
-  seg_start_kernel<<<sblocks, 256, 0, m.stream>>>(s.keys, nitems, s.flags, s.seg_start, m.dc);
+  {  // segments in one pass; s.flags holds its tile status words and counter
+    const int64_t stiles = (nitems + kSegTile - 1) / kSegTile;
+    e = cudaMemsetAsync(s.flags, 0, sizeof(uint32_t) * (stiles + 1), m.stream);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, seg_heads_kernel, kSegThreads, 0);
+    if (e != cudaSuccess) return e;
+    const unsigned sblocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(stiles, (int64_t)m.sm_count * std::max(1, per_sm)));
+    seg_heads_kernel<<<sblocks, kSegThreads, 0, m.stream>>>(s.keys, nitems, s.seg_start, s.flags, stiles, m.dc);
+  }
   {
     const unsigned cblocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((nitems + 255) / 256, (int64_t)m.sm_count * m.tune.ingest_ctas_per_sm));
     centroid_kernel<<<cblocks, 256, 0, m.stream>>>(s.keys, nullptr, s.sitems, s.seg_start, m.g, s.train, s.desc, kf,
@@ -871,6 +973,25 @@ cudaError_t launch_train_prepare(MapState& m, const float4* in, int64_t p, const
   if (e != cudaSuccess) return e;
   train_gather_kernel<<<grid_for(p, 256), 256, 0, m.stream>>>(in, s.vals, p, m.active_map, s.train, s.seg_start,
                                                                m.dc);
+  return cudaGetLastError();
+}
+
+// Failure-detection self-test: the segment pass over three tiles whose tile
+// counter starts at 1, so tile 0 is never claimed and the look-back of the
+// others runs out; they must end with SBKI_ERR_TIMEOUT instead of spinning on.
+// Buffers are the caller's (device): keys [3 kSegTile] (any values),
+// seg_start [3 kSegTile + 1], work [4], dc (zeroed DevCounters).
+cudaError_t launch_wait_selftest(unsigned long long* keys, uint32_t* seg_start, uint32_t* work, DevCounters* dc,
+                                 cudaStream_t st) {
+  const int64_t n = 3 * kSegTile;
+  cudaError_t e = cudaMemsetAsync(work, 0, sizeof(uint32_t) * 4, st);
+  if (e != cudaSuccess) return e;
+  const uint32_t one = 1u, items = (uint32_t)n;
+  e = cudaMemcpyAsync(work + 3, &one, sizeof(one), cudaMemcpyHostToDevice, st);  // tile counter: skip tile 0
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(&dc->n_items, &items, sizeof(items), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return e;
+  seg_heads_kernel<<<2, kSegThreads, 0, st>>>(keys, n, seg_start, work, 3, dc);
   return cudaGetLastError();
 }
 

@@ -1199,6 +1199,59 @@ sbki_status sbki_grad(const sbki_params* params, const float* xyzl, int64_t p, c
   return st;
 }
 
+sbki_status sbki_import(sbki_map* map, const int64_t* keys, const float* alpha, int64_t count) {
+  if (!map) return fail(nullptr, SBKI_ERR_INVALID_ARG, "map is NULL");
+  MapState& m = map->st;
+  if (count < 0 || (count > 0 && (!keys || !alpha))) return fail(&m, SBKI_ERR_INVALID_ARG, "bad arguments");
+  DeviceGuard dg(m.device);
+  if (count == 0) return SBKI_OK;
+  TmpFree tf;
+  tf.st = m.stream;
+  const int64_t* dk = nullptr;
+  const float* da = nullptr;
+  sbki_status st = device_input(m, keys, (size_t)count * 3, &dk, &tf.p[0]);
+  if (st != SBKI_OK) return st;
+  if ((st = device_input(m, alpha, (size_t)count * m.g.K1, &da, &tf.p[1])) != SBKI_OK) return st;
+  m.epoch += 1;
+  begin_kernel<<<1, 1, 0, m.stream>>>(m.dc, m.epoch, 0u);
+  m.launches += 1;
+  CK(&m, launch_import(m, dk, da, count));
+  st = read_counters(m);
+  if (st != SBKI_OK) return st;
+  m.host_blocks = m.hc->n_blocks;
+  return status_from_device(m);
+}
+
+sbki_status sbki_selftest_bounded_wait(int32_t device, int32_t* device_status) {
+  if (!device_status) return fail(nullptr, SBKI_ERR_INVALID_ARG, "device_status is NULL");
+  *device_status = SBKI_OK;
+  DeviceGuard dg(device);
+  const int64_t n = 3 * 4096;
+  unsigned long long* keys = nullptr;
+  uint32_t *seg = nullptr, *work = nullptr;
+  DevCounters* dc = nullptr;
+  cudaStream_t st = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = dalloc(&keys, n);
+  if (e == cudaSuccess) e = dalloc(&seg, n + 1);
+  if (e == cudaSuccess) e = dalloc(&work, 4);
+  if (e == cudaSuccess) e = dalloc(&dc, 1);
+  if (e == cudaSuccess) e = cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * n, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dc, 0, sizeof(DevCounters), st);
+  if (e == cudaSuccess) e = launch_wait_selftest(keys, seg, work, dc, st);
+  int32_t err = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&err, &dc->err, sizeof(err), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(keys);
+  cudaFree(seg);
+  cudaFree(work);
+  cudaFree(dc);
+  if (st) cudaStreamDestroy(st);
+  if (e != cudaSuccess) return fail(nullptr, SBKI_ERR_CUDA, "bounded-wait self-test: %s", cudaGetErrorString(e));
+  *device_status = err;
+  return SBKI_OK;
+}
+
 const char* sbki_last_error(const sbki_map* map) { return map ? map->st.last_error : g_create_error; }
 
 const char* sbki_status_string(sbki_status s) {

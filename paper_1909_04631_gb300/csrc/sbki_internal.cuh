@@ -287,15 +287,20 @@ cudaError_t launch_emit(MapState& m, int ns, int64_t total_n, const KeyFrame& kf
 cudaError_t launch_downsample_n(MapState& m, const KeyFrame& kf, int64_t nitems);
 cudaError_t launch_train_bbox(MapState& m, const float4* in, int64_t p, int* bbox_dev);
 cudaError_t launch_train_prepare(MapState& m, const float4* in, int64_t p, const KeyFrame& kf);
+cudaError_t launch_wait_selftest(unsigned long long* keys, uint32_t* seg_start, uint32_t* work, DevCounters* dc,
+                                 cudaStream_t st);
 
 // blocks.cu
 cudaError_t launch_touch_blocks(MapState& m, const KeyFrame& kf, int64_t bound);
 cudaError_t launch_commit_blocks(MapState& m);
+// blocks of the given voxel keys (selected map), commit, zero-fill, then alpha - alpha0 at the keys
+cudaError_t launch_import(MapState& m, const int64_t* keys, const float* alpha, int64_t count);
 cudaError_t launch_bin_points(MapState& m, int64_t bound);
 
 // accumulate.cu
 cudaError_t launch_accumulate(MapState& m, const KeyFrame& kf);
 cudaError_t launch_accumulate_points(MapState& m);
+cudaError_t launch_fresh_fill(MapState& m);  // zero the blocks created by this update
 cudaError_t build_candidate_tables(MapState& m);
 // backward.cu: held-out log-likelihood (+ dLL/dalpha into grad), upstream gradient at voxel keys,
 // and the backward pass through Eq. (kernel) into acc_dev[0..1] and grad_xyz

@@ -25,7 +25,7 @@ EXPORTED = ["sbki_default_params", "sbki_create_map", "sbki_destroy_map", "sbki_
             "sbki_voxel_count", "sbki_export", "sbki_profile", "sbki_profile_read", "sbki_kernel_values", "sbki_last_error", "sbki_status_string",
             "sbki_training_set_noalloc", "sbki_grad_clear", "sbki_heldout_loglik", "sbki_grad_add_alpha",
             "sbki_backward", "sbki_forward_alpha", "sbki_grad", "sbki_insert_batch", "sbki_select_map",
-            "sbki_get_tuning", "sbki_set_tuning"]
+            "sbki_get_tuning", "sbki_set_tuning", "sbki_import", "sbki_selftest_bounded_wait"]
 
 
 class SbkiError(RuntimeError):
@@ -107,6 +107,8 @@ def load(build_if_missing: bool = True):
         L.sbki_insert_batch.argtypes = [vp, vp, i32, P(Stats)]
         L.sbki_select_map.argtypes = [vp, i32]
         L.sbki_get_tuning.argtypes = [vp, P(Tuning)]
+        L.sbki_import.argtypes = [vp, vp, vp, i64]
+        L.sbki_selftest_bounded_wait.argtypes = [i32, P(i32)]
         L.sbki_set_tuning.argtypes = [vp, P(Tuning)]
         L.sbki_grad_clear.argtypes = [vp]
         L.sbki_heldout_loglik.argtypes = [vp, vp, vp, i64, i32, P(C.c_double)]
@@ -130,7 +132,8 @@ def load(build_if_missing: bool = True):
                   "sbki_training_set", "sbki_insert_training", "sbki_query_probs", "sbki_voxel_count",
                   "sbki_export", "sbki_training_set_noalloc", "sbki_grad_clear", "sbki_heldout_loglik",
                   "sbki_grad_add_alpha", "sbki_backward", "sbki_forward_alpha", "sbki_grad", "sbki_insert_batch",
-                  "sbki_select_map", "sbki_get_tuning", "sbki_set_tuning"):
+                  "sbki_select_map", "sbki_get_tuning", "sbki_set_tuning", "sbki_import",
+                  "sbki_selftest_bounded_wait"):
             getattr(L, f).restype = C.c_int
         _lib = L
         return L
@@ -209,6 +212,16 @@ def grad(params: Params, xyzl, keys, grad_alpha):
     if st != OK:
         raise SbkiError(st, L.sbki_last_error(None).decode())
     return gl.value, gs.value, gx[:x.shape[0]]
+
+
+def selftest_bounded_wait(device=0):
+    """Status the device reported when a bounded wait ran out (expected: ERR_TIMEOUT)."""
+    L = load()
+    out = C.c_int32()
+    st = L.sbki_selftest_bounded_wait(int(device), C.byref(out))
+    if st != OK:
+        raise SbkiError(st, L.sbki_last_error(None).decode())
+    return out.value
 
 
 def kernel_values(r, method=0):
@@ -470,6 +483,14 @@ class Map:
         if gx is not None and not hasattr(gx, "data_ptr"):
             gx = gx[:p]
         return gl.value, gs.value, gx
+
+    def import_(self, keys, alpha):
+        """Restore exported contents (keys [n,3], alpha [n,K+1] with prior) into the selected map."""
+        k = _as_i64(keys, 3)
+        a = _as(alpha, np.float32, self.K1)
+        kp, k1 = _ptr(k)
+        ap, k2 = _ptr(a)
+        self._check(self._L.sbki_import(self._h, kp, ap, k.shape[0]))
 
     def export(self, pairs=False):
         """(keys int64 [n,3], alpha float32 [n,K+1], pairs int32 [n] or None), sorted by key."""
