@@ -307,11 +307,12 @@ sbki_status sbki_grad(const sbki_params* params, const float* xyzl, int64_t p, c
  * set unchanged. */
 sbki_status sbki_import(sbki_map* map, const int64_t* keys, const float* alpha, int64_t count);
 
-/* Failure-detection self-test on `device` (diagnostic): runs the segment pass
- * of the downsampling step on a small input whose first tile is never
- * processed, so every bounded wait on it runs out (about a second); the
- * kernel reports SBKI_ERR_TIMEOUT in *device_status instead of spinning, and
- * the context stays usable.  Returns SBKI_OK when the test itself ran. */
+/* Failure-detection self-test on `device` (diagnostic): runs one digit pass
+ * of the downsampling step's radix sort over three tiles whose first tile is
+ * never processed, so every bounded wait of the others on it runs out (about a
+ * second); the kernel reports SBKI_ERR_TIMEOUT in *device_status instead of
+ * spinning, and the context stays usable.  Returns SBKI_OK when the test itself
+ * ran. */
 sbki_status sbki_selftest_bounded_wait(int32_t device, int32_t* device_status);
 
 /* Message of the last failure on this map (or of the last sbki_create_map

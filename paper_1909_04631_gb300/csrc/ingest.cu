@@ -242,135 +242,19 @@ __global__ void __launch_bounds__(256) emit_kernel(const float4* __restrict__ wo
   }
 }
 
-// Segments of the sorted items in one pass: tiles of kSegTile items are claimed
-// in order; each counts its segment heads (key differs from its predecessor),
-// publishes the count, finds the heads before it by a warp-wide look-back over
-// up to 32 preceding tiles at once (bounded waits, SBKI_ERR_TIMEOUT), and
-// writes seg_start[head index] = item index.  The tile holding the last item
-// writes seg_start[P] = n and the segment count P.  work: [ntiles] status words
-// then a tile counter, zero on entry.
-constexpr int kSegThreads = 512;
-constexpr int kSegPer = 8;
-constexpr int kSegTile = kSegThreads * kSegPer;
-constexpr uint32_t kSegAgg = 1u << 30, kSegPre = 2u << 30, kSegVal = kSegAgg - 1u;
-
-__global__ void __launch_bounds__(kSegThreads) seg_heads_kernel(const unsigned long long* __restrict__ keys,
-                                                               int64_t cap, uint32_t* __restrict__ seg_start,
-                                                               uint32_t* __restrict__ work, int64_t ntiles_cap,
-                                                               DevCounters* dc) {
-  __shared__ uint32_t s_wsum[kSegThreads / 32];
-  __shared__ uint32_t s_tile, s_excl;
-  __shared__ int s_fail;
-  if (dc->err) return;
-  const int64_t n = min(cap, (int64_t)dc->n_items);
-  const int64_t nt = (n + kSegTile - 1) / kSegTile;
-  uint32_t* status = work;
-  uint32_t* counter = work + ntiles_cap;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (;;) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      s_tile = atomicAdd(counter, 1u);
-      s_fail = 0;
-    }
-    __syncthreads();
-    const int64_t t = s_tile;
-    if (t >= nt) break;
-    const int64_t first = t * kSegTile + (int64_t)threadIdx.x * kSegPer;
-    uint32_t heads = 0;  // bit k: item first + k starts a segment
-    unsigned long long prev = first > 0 && first <= n ? keys[first - 1] : 0ull;
-#pragma unroll
-    for (int k = 0; k < kSegPer; ++k) {
-      const int64_t i = first + k;
-      if (i < n) {
-        const unsigned long long key = keys[i];
-        if (i == 0 || key != prev) heads |= 1u << k;
-        prev = key;
-      }
-    }
-    // exclusive prefix of the head counts over the CTA's threads
-    const uint32_t c = __popc(heads);
-    uint32_t inc = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t u = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc += u;
-    }
-    if (lane == 31) s_wsum[warp] = inc;
-    __syncthreads();
-    uint32_t wpre = 0, total = 0;
-#pragma unroll
-    for (int k = 0; k < kSegThreads / 32; ++k) {
-      const uint32_t v = s_wsum[k];
-      wpre += k < warp ? v : 0u;
-      total += v;
-    }
-    // the tile's place among all heads: publish, then one warp looks back 32 tiles at a time
-    if (warp == 0) {
-      uint32_t excl = 0;
-      if (t == 0) {
-        if (lane == 0) *reinterpret_cast<volatile uint32_t*>(status) = kSegPre | total;
-      } else {
-        if (lane == 0) *reinterpret_cast<volatile uint32_t*>(status + t) = kSegAgg | total;
-        int64_t j = t - 1;
-        int spins = 0;
-        for (;;) {
-          const int64_t q = j - lane;
-          const uint32_t v = q >= 0 ? *reinterpret_cast<const volatile uint32_t*>(status + q) : kSegPre;
-          const unsigned pre = __ballot_sync(0xffffffffu, (v & kSegPre) != 0);
-          const unsigned ready = __ballot_sync(0xffffffffu, (v & (kSegAgg | kSegPre)) != 0);
-          const int stop = pre ? __ffs(pre) - 1 : 31;  // nearest inclusive prefix in the window
-          const unsigned need = stop == 31 ? 0xffffffffu : ((2u << stop) - 1u);
-          if ((ready & need) == need) {  // every word up to it is published
-            uint32_t part = lane <= stop ? (v & kSegVal) : 0u;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-            excl += part;
-            if (pre) break;
-            j -= 32;
-          } else if (++spins > (1 << 20)) {
-            if (lane == 0) s_fail = 1;
-            break;
-          } else {
-            __nanosleep(20);
-          }
-        }
-        if (lane == 0) *reinterpret_cast<volatile uint32_t*>(status + t) = kSegPre | (excl + total);
-      }
-      if (lane == 0) s_excl = excl;
-    }
-    __syncthreads();
-    if (s_fail) {
-      if (threadIdx.x == 0) set_error(dc, SBKI_ERR_TIMEOUT);
-      break;
-    }
-    uint32_t idx = s_excl + wpre + inc - c;
-#pragma unroll
-    for (int k = 0; k < kSegPer; ++k)
-      if (heads & (1u << k)) seg_start[idx++] = (uint32_t)(first + k);
-    if (first <= n - 1 && n - 1 < first + kSegPer) {  // this thread holds the last item
-      seg_start[s_excl + total] = (uint32_t)n;
-      dc->n_train = s_excl + total;
-    }
-  }
-}
-
 // Centroids: per axis the exact mean of the members' FP32 coordinates,
-// rounded once to FP32 (nearest, ties to even).  No floating point is used:
+// rounded once to FP32 (nearest, ties to even), with exact steps only:
 // every nonzero |x| is m 2^e with an integer m < 2^24 and e = its exponent of
-// the last mantissa bit; with E the smallest such e in the cell,
+// the last mantissa bit; with E at or below the smallest such e in the cell,
 //     sum |x| = T 2^E,   T = sum m 2^(e - E)
-// is an integer held exactly in 128 bits whenever the members' e span fewer
-// than 127 - 24 - ceil(log2 n) binades (cells next to a coordinate plane
-// included), and the mean is T 2^E / n, rounded with integer division.  The
-// members of a cell share a sign per axis (the cell index fixes it).  Cells
-// beyond that span, or whose mean is below the FP32 normal range, take a
-// one-thread path with 512-bit arithmetic (exact for every FP32 input).
-// Short segments (<= kShort members) are summed by one lane
-// (centroid_kernel), longer ones by a warp (mid_centroid_kernel), the longest
-// (> kHuge) by a whole CTA (huge_centroid_kernel).
-constexpr uint32_t kShort = 16;
-constexpr uint32_t kHuge = 1024;
+// and the mean is T 2^E / n, rounded with integer division.  The segment pass
+// (seg_reduce_kernel) sums x 2^-E as signed 64-bit integers with E fixed by the
+// sort tile; the cells it cannot decide go to slow_cell, where the members of
+// a cell are taken to share a sign per axis (the cell index fixes it, except
+// that x fp32(1/ds) of a negative subnormal x can round to -0 when ds > 1):
+// T in 128 bits when the members' e span less than 127 - 24 - ceil(log2 n)
+// binades, else (and for a mean below the FP32 normal range, or mixed signs) a
+// one-thread signed 512-bit sum, exact for every FP32 input.
 
 struct U128 {
   unsigned long long lo, hi;
@@ -409,11 +293,11 @@ __device__ __forceinline__ int bitlen64(unsigned long long v) { return v ? 64 - 
 
 struct AxisAcc {
   int emin, emax;  // range of the members' last-mantissa-bit exponents
-  bool neg;
+  bool neg, pos;   // a member below / above zero
   __device__ void init() {
     emin = 1 << 20;
     emax = -(1 << 20);
-    neg = false;
+    neg = pos = false;
   }
   __device__ void see(float v) {
     unsigned m;
@@ -422,13 +306,14 @@ struct AxisAcc {
       emin = min(emin, e);
       emax = max(emax, e);
       neg |= v < 0.0f;
+      pos |= v > 0.0f;
     }
   }
   __device__ bool empty() const { return emax < emin; }
-  __device__ bool fits(uint32_t n) const {  // T stays below 2^127
+  __device__ bool fits(uint32_t n) const {  // one sign, and T stays below 2^127
     int lg = 0;
-    while ((1u << lg) < n) ++lg;
-    return empty() || emax - emin + 24 + lg <= 126;
+    while (lg < 32 && (1ull << lg) < n) ++lg;
+    return empty() || (!(neg && pos) && emax - emin + 24 + lg <= 126);
   }
   __device__ void add(U128& t, float v) const {
     unsigned m;
@@ -477,24 +362,41 @@ __device__ bool round_mean(U128 T, unsigned long long n, int s, float& out) {
 }
 
 // One thread: exact mean of axis ax of members [a, b) for any FP32 input.
-// The sum is held in 16 32-bit limbs in units of 2^-149 (512 bits).
+// Positive and negative members are summed apart, in 16 32-bit limbs in units
+// of 2^-149 each (512 bits), and the smaller sum is subtracted from the larger.
 __device__ float wide_mean(const float4* __restrict__ items, const uint32_t* __restrict__ perm, uint32_t a,
                            uint32_t b, int ax) {
-  uint32_t w[16];
-  for (int i = 0; i < 16; ++i) w[i] = 0u;
-  bool neg = false;
+  uint32_t wp[16], wn[16];
+  for (int i = 0; i < 16; ++i) wp[i] = wn[i] = 0u;
   for (uint32_t i = a; i < b; ++i) {
     const float v = axis_of(item_at(items, perm, i), ax);
     unsigned m;
     int e;
     if (!decompose(v, m, e)) continue;
-    neg |= v < 0.0f;
+    uint32_t* w = v < 0.0f ? wn : wp;
     const int sh = e + 149, li = sh >> 5, bi = sh & 31;
     unsigned long long add = (unsigned long long)m << bi;  // < 2^55
     for (int j = li; j < 16 && add; ++j) {
       const unsigned long long t = (unsigned long long)w[j] + (add & 0xffffffffull);
       w[j] = (uint32_t)t;
       add = (add >> 32) + (t >> 32);
+    }
+  }
+  bool neg = false;  // the negative members outweigh the positive ones
+  for (int j = 15; j >= 0; --j)
+    if (wn[j] != wp[j]) {
+      neg = wn[j] > wp[j];
+      break;
+    }
+  uint32_t w[16];
+  {
+    const uint32_t* hi = neg ? wn : wp;
+    const uint32_t* lo = neg ? wp : wn;
+    unsigned long long borrow = 0ull;
+    for (int j = 0; j < 16; ++j) {
+      const unsigned long long d = (unsigned long long)hi[j] - lo[j] - borrow;
+      w[j] = (uint32_t)d;
+      borrow = (d >> 63) & 1ull;
     }
   }
   const unsigned long long n = b - a;
@@ -590,261 +492,511 @@ __device__ __forceinline__ void warp_range(AxisAcc& s) {
     s.emax = max(s.emax, __shfl_xor_sync(0xffffffffu, s.emax, o));
   }
   s.neg = __any_sync(0xffffffffu, s.neg);
+  s.pos = __any_sync(0xffffffffu, s.pos);
 }
 
-__global__ void __launch_bounds__(256) centroid_kernel(const unsigned long long* __restrict__ keys,
-                                                       const uint32_t* __restrict__ perm,
-                                                       const float4* __restrict__ items,
-                                                       const uint32_t* __restrict__ seg_start, Geom g,
-                                                       float4* __restrict__ train, const ScanDesc* __restrict__ desc,
-                                                       KeyFrame kf, uint32_t* __restrict__ huge,
-                                                       uint32_t* __restrict__ mid, DevCounters* dc) {
-  if (dc->err) return;
-  const uint32_t P = dc->n_train;
-  const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
-  const uint32_t nthreads = gridDim.x * blockDim.x;
+// Exact mean of a cell the segment pass could not decide (cell s, members
+// [seg_start[s], seg_start[s + 1]) of the sorted items), by a whole warp.  An
+// axis whose first member has |x0| >= 2.5 ds is summed in one pass in 64 bits
+// (FastAxis); any other axis takes its exponent range first, then the 128-bit
+// sum, else wide_mean.
+__device__ void slow_cell(uint32_t s, const unsigned long long* __restrict__ keys, const float4* __restrict__ items,
+                          const uint32_t* __restrict__ seg_start, const Geom& g, float4* __restrict__ train,
+                          const ScanDesc* __restrict__ desc, const KeyFrame& kf) {
   const int lane = threadIdx.x & 31;
-  const uint32_t warp = gtid >> 5, nwarps = nthreads >> 5;
-  for (uint32_t base = warp * 32; base < P; base += nwarps * 32) {
-    const uint32_t s = base + lane;
-    const bool valid = s < P;
-    const uint32_t a = valid ? seg_start[s] : 0, b = valid ? seg_start[s + 1] : 0;
-    const uint32_t n = b - a;
-    const bool is_huge = valid && n > kHuge;
-    if (is_huge) huge[atomicAdd(&dc->n_huge, 1u)] = s;
-    AxisAcc ax[3];
-    FastAxis fa[3];
-    U128 T[3];
-    bool fit[3] = {false, false, false};
+  const uint32_t* perm = nullptr;
+  const uint32_t a = seg_start[s], b = seg_start[s + 1], n = b - a;
+  AxisAcc w[3];
+  FastAxis fa[3];
+  U128 t[3];
+  const float4 p0 = item_at(items, perm, a);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    w[c].init();
+    t[c].lo = t[c].hi = 0ull;
+    fa[c].init(axis_of(p0, c), g.fast_lim);
+  }
+  const bool two_pass = !fa[0].on || !fa[1].on || !fa[2].on;  // warp-uniform
+  for (uint32_t i = a + lane; i < b; i += 32) {
+    const float4 p = item_at(items, perm, i);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      ax[c].init();
-      T[c].lo = T[c].hi = 0ull;
-    }
-    if (valid && n <= kShort) {
-      const float4 p0 = item_at(items, perm, a);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) fa[c].init(axis_of(p0, c), g.fast_lim);
-      for (uint32_t i = a; i < b; ++i) {
-        const float4 p = i == a ? p0 : item_at(items, perm, i);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          if (fa[c].on) fa[c].add(axis_of(p, c));
-          else ax[c].see(axis_of(p, c));
-        }
-      }
-      if (!fa[0].on || !fa[1].on || !fa[2].on) {  // a cell next to a coordinate plane
-#pragma unroll
-        for (int c = 0; c < 3; ++c) fit[c] = !fa[c].on && ax[c].fits(n);
-        for (uint32_t i = a; i < b; ++i) {
-          const float4 p = item_at(items, perm, i);
-#pragma unroll
-          for (int c = 0; c < 3; ++c)
-            if (fit[c]) ax[c].add(T[c], axis_of(p, c));
-        }
-      }
-    }
-    const bool is_mid = valid && n > kShort && !is_huge;
-    if (is_mid) mid[atomicAdd(&dc->n_mid, 1u)] = s;
-    if (valid && n <= kShort) {
-      const unsigned long long k = keys[a];
-      const int label = (int)(k & ((1ull << g.label_bits) - 1));
-      float out[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-        out[c] = fa[c].on ? fa[c].finish(n) : finish_axis(ax[c], fit[c], T[c], n, items, perm, a, b, c);
-      train[s] = make_float4(out[0], out[1], out[2], (float)(label + 32 * map_of_segment(k, kf, desc)));
+      if (fa[c].on) fa[c].add(axis_of(p, c));
+      else w[c].see(axis_of(p, c));
     }
   }
-}
-
-// Segments of kShort+1 .. kHuge members: one warp each, spread over the grid
-// (neighbouring cells near the sensor are all long; a warp per group of 32
-// consecutive cells would serialise them).
-__global__ void __launch_bounds__(256) mid_centroid_kernel(const unsigned long long* __restrict__ keys,
-                                                           const uint32_t* __restrict__ perm,
-                                                           const float4* __restrict__ items,
-                                                           const uint32_t* __restrict__ seg_start, Geom g,
-                                                           float4* __restrict__ train,
-                                                           const ScanDesc* __restrict__ desc, KeyFrame kf,
-                                                           const uint32_t* __restrict__ mid, DevCounters* dc) {
-  if (dc->err) return;
-  const uint32_t nm = dc->n_mid;
-  const int lane = threadIdx.x & 31;
-  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t j = warp; j < nm; j += nwarps) {
-    const uint32_t s = mid[j];
-    const uint32_t a = seg_start[s], b = seg_start[s + 1], n = b - a;
-    AxisAcc w[3];
-    FastAxis fa[3];
-    U128 t[3];
-    const float4 p0 = item_at(items, perm, a);
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+    if (fa[c].on) fa[c].T = warp_sum_u64(fa[c].T);
+  bool fit[3] = {false, false, false};
+  if (two_pass) {
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      w[c].init();
-      t[c].lo = t[c].hi = 0ull;
-      fa[c].init(axis_of(p0, c), g.fast_lim);
+      warp_range(w[c]);
+      fit[c] = !fa[c].on && w[c].fits(n);
     }
-    const bool slow = !fa[0].on || !fa[1].on || !fa[2].on;  // warp-uniform
     for (uint32_t i = a + lane; i < b; i += 32) {
       const float4 p = item_at(items, perm, i);
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        if (fa[c].on) fa[c].add(axis_of(p, c));
-        else w[c].see(axis_of(p, c));
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-      if (fa[c].on) fa[c].T = warp_sum_u64(fa[c].T);
-    bool fit[3] = {false, false, false};
-    if (slow) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        warp_range(w[c]);
-        fit[c] = !fa[c].on && w[c].fits(n);
-      }
-      for (uint32_t i = a + lane; i < b; i += 32) {
-        const float4 p = item_at(items, perm, i);
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-          if (fit[c]) w[c].add(t[c], axis_of(p, c));
-      }
-#pragma unroll
-      for (int c = 0; c < 3; ++c) t[c] = warp_sum_u128(t[c]);
-    }
-    if (lane == 0) {
-      float out[3];
       for (int c = 0; c < 3; ++c)
-        out[c] = fa[c].on ? fa[c].finish(n) : finish_axis(w[c], fit[c], t[c], n, items, perm, a, b, c);
-      const unsigned long long k = keys[a];
-      const int label = (int)(k & ((1ull << g.label_bits) - 1));
-      train[s] = make_float4(out[0], out[1], out[2], (float)(label + 32 * map_of_segment(k, kf, desc)));
+        if (fit[c]) w[c].add(t[c], axis_of(p, c));
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) t[c] = warp_sum_u128(t[c]);
+  }
+  if (lane == 0) {
+    float out[3];
+    for (int c = 0; c < 3; ++c)
+      out[c] = fa[c].on ? fa[c].finish(n) : finish_axis(w[c], fit[c], t[c], n, items, perm, a, b, c);
+    const unsigned long long k = keys[a];
+    const int label = (int)(k & ((1ull << g.label_bits) - 1));
+    train[s] = make_float4(out[0], out[1], out[2], (float)(label + 32 * map_of_segment(k, kf, desc)));
+  }
+}
+
+// --- segments and centroids in one pass ---------------------------------------
+// The sorted items are cut into tiles of kSegTile.  seg_count_kernel counts
+// each tile's segment heads (items whose key differs from the predecessor's).
+// seg_reduce_kernel, a persistent grid, then takes the tiles one by one:
+// stages the tile's keys and items through shared memory (coalesced reads),
+// marks its heads, sums the head counts of the tiles before it (so it waits on
+// no other CTA) and writes seg_start.  Each thread then sums its members: per axis a coordinate x adds
+// the integer x 2^-E (an exact FP32 product, converted exactly), with E fixed
+// by the member's sort tile of 8^3 cells (kSegShift + 23 below the exponent of
+// (8 |t| + 10) ds, t the tile index on that axis, an upper bound of the tile's
+// |x|), so a cell's sum is a plain signed 64-bit integer in any order.  A
+// nonzero member with |x| 2^-E below 2^23 (it would have a fraction: within
+// about 2^-21 ds of a coordinate plane), a cell of 2^15 or more members, or a
+// mean below the FP32 normal range leaves the cell to slow_cell.
+// A thread stores the sums of every cell whose head it holds in shared memory;
+// the run before its first head (the end of a cell begun in an earlier thread)
+// is added there with shared-memory atomics; then the CTA rounds every cell.
+// A cell that continues into the next tile leaves partial sums (the cell's
+// part in its head's tile, the run that opens each following tile), which
+// finish_cells_kernel joins and rounds.
+constexpr int kSegThreads = 256;
+constexpr int kSegPer = 8;
+constexpr int kSegTile = kSegThreads * kSegPer;
+constexpr int kSegWarps = kSegThreads / 32;
+constexpr int kSegShift = 24;      // binades between a tile's |x| bound and its members' smallest last bit
+constexpr uint32_t kSegMaxN = 1u << (63 - 24 - kSegShift);  // |T| < n 2^(24 + kSegShift) < 2^63 below this
+static_assert(kSegTile == kSegTileItems, "segment tile size");
+
+struct SegState {           // sums of a run of members of one cell
+  unsigned long long T[3];  // per axis: sum of x 2^-E, two's complement
+  uint32_t n;               // members
+  uint32_t flags;           // bit 1 kSegBad: see above; bits 2 + 9a: E + 256 of axis a (the same for every
+                            // member of a cell, so runs join by OR)
+};
+constexpr uint32_t kSegBad = 2u;
+
+// Dynamic shared memory: the cells' sums and first items; the first part
+// doubles as the load stage (items, then keys, one pad entry per kSegPer so
+// that each thread's consecutive entries fall in distinct banks).
+__host__ __device__ constexpr int seg_pad(int i) { return i + i / kSegPer; }
+constexpr size_t kSegCellBytes = (size_t)kSegTile * sizeof(SegState);
+constexpr size_t kSegStageItems = 0;
+constexpr size_t kSegStageKeys = (size_t)seg_pad(kSegTile) * 16;
+constexpr size_t kSegSmemBytes = kSegCellBytes + (size_t)kSegTile * sizeof(uint32_t);
+static_assert(kSegStageKeys + (size_t)seg_pad(kSegTile + 2) * 8 <= kSegCellBytes, "load stage fits the cell stage");
+
+struct SegCarry {   // partial sums of a cell that crosses a tile boundary
+  SegState st;
+  uint32_t s;       // part in the head's tile: the cell's index
+  uint32_t closed;  // run that opens a tile: 1 when the cell ends inside the tile
+  uint32_t pad[2];
+};
+static_assert(sizeof(SegCarry) == kSegCarryBytes, "segment carry layout");
+
+// The sort tile a key names: E per axis packed as in SegState::flags, the
+// scales 2^-E, and kSegBad when a scale is outside the FP32 normal range.
+struct TileUnit {
+  uint32_t meta, bad;
+  float scale[3];
+};
+__device__ __forceinline__ TileUnit tile_unit(unsigned long long key, const Geom& g, const KeyFrame& kf,
+                                              const ScanDesc* __restrict__ desc) {
+  int o0 = kf.org[0], o1 = kf.org[1], o2 = kf.org[2];
+  if (kf.scan_bits) {
+    const ScanDesc& d = desc[(int)(key >> kf.total_bits)];
+    o0 = d.org[0];
+    o1 = d.org[1];
+    o2 = d.org[2];
+  }
+  const unsigned long long tile = key >> (g.label_bits + kLocalBits);
+  const int t[3] = {(int)((tile >> (kf.bits[1] + kf.bits[2])) & ((1ull << kf.bits[0]) - 1)) + o0,
+                    (int)((tile >> kf.bits[2]) & ((1ull << kf.bits[1]) - 1)) + o1,
+                    (int)(tile & ((1ull << kf.bits[2]) - 1)) + o2};
+  TileUnit u;
+  u.meta = 0u;
+  u.bad = 0u;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int mag = t[a] < 0 ? -t[a] : t[a];
+    const float U = __fmul_rn((float)(kTileEdge * mag + kTileEdge + 2), g.ds);
+    const int E = (int)(__float_as_uint(U) >> 23) - 150 - kSegShift;  // |x| < U < 2^(E + 48)
+    u.meta |= (uint32_t)(E + 256) << (2 + 9 * a);
+    const bool ok = E >= -126 && E <= 126;
+    u.scale[a] = ok ? __uint_as_float((uint32_t)(127 - E) << 23) : 0.f;
+    if (!ok) u.bad = kSegBad;
+  }
+  return u;
+}
+__device__ __forceinline__ int meta_E(uint32_t flags, int a) { return (int)((flags >> (2 + 9 * a)) & 511u) - 256; }
+
+__device__ __forceinline__ void seg_clear(SegState& s) {
+  s.T[0] = s.T[1] = s.T[2] = 0ull;
+  s.n = 0u;
+  s.flags = 0u;
+}
+
+__device__ __forceinline__ void seg_add(SegState& s, const TileUnit& u, float x, float y, float z) {
+  s.n += 1u;
+  const float v[3] = {x, y, z};
+  bool bad = false;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float q = __fmul_rn(v[a], u.scale[a]);  // x 2^-E, exact when |q| >= 2^23
+    const float aq = fabsf(q);
+    bad = bad || (aq < 8388608.0f && aq != 0.0f) || aq >= 281474976710656.0f;
+    s.T[a] += (unsigned long long)__float2ll_rz(q);
+  }
+  s.flags |= u.meta | u.bad | (bad ? kSegBad : 0u);
+}
+
+// a := a and b joined (two runs of one cell)
+__device__ __forceinline__ void seg_merge(SegState& a, const SegState& b) {
+  a.T[0] += b.T[0];
+  a.T[1] += b.T[1];
+  a.T[2] += b.T[2];
+  a.n += b.n;
+  a.flags |= b.flags;
+}
+
+// round(T 2^E / n) to FP32, nearest with ties to even, for 0 < T < 2^64 and
+// 0 < n < 2^16; false when the result is below the FP32 normal range.  The
+// integer quotient is estimated twice with a single-precision reciprocal of n,
+// every rounding toward zero so that no estimate exceeds the true quotient,
+// and each estimate is corrected with its exact integer remainder.
+__device__ __forceinline__ bool round_mean64(unsigned long long T, uint32_t n, int E, float& out) {
+  const int bt = 64 - __clzll((long long)T), bn = 32 - __clz((int)n);
+  const int k = 26 + bn - bt;  // q = floor(T 2^k / n) lies in [2^25, 2^27)
+  unsigned long long num;
+  bool sticky;
+  if (k >= 0) {
+    num = T << k;  // below 2^(26 + bn) <= 2^42
+    sticky = false;
+  } else {
+    num = T >> -k;
+    sticky = (T & ((1ull << -k) - 1ull)) != 0ull;
+  }
+  const float r = __frcp_rz((float)n);
+  unsigned long long q = (unsigned long long)__fmul_rz(__ull2float_rz(num), r);  // short by at most 48
+  unsigned long long rem = num - q * n;                                           // below 49 n < 2^22
+  q += (unsigned long long)__fmul_rz((float)rem, r);                              // short by at most 1
+  rem = num - q * n;
+  if (rem >= n) {
+    ++q;
+    rem -= n;
+  }
+  sticky = sticky || rem != 0ull;
+  const int qb = 64 - __clzll((long long)q);  // 26 or 27
+  const int lead = qb - 1 - k + E;            // exponent of the leading bit
+  if (lead < -126) return false;
+  const int sh = qb - 24;
+  uint32_t mant = (uint32_t)(q >> sh);
+  const uint32_t rb = (uint32_t)q & ((1u << sh) - 1u), half = 1u << (sh - 1);
+  if (rb > half || (rb == half && (sticky || (mant & 1u)))) ++mant;
+  int ex = lead;
+  if (mant == (1u << 24)) {
+    mant >>= 1;
+    ++ex;
+  }
+  out = __uint_as_float(((uint32_t)(ex + 127) << 23) | (mant & 0x7fffffu));
+  return true;
+}
+
+// Training point s from the complete sums of its cell (key: any member's key);
+// false, with nothing written, when this form cannot give the exact mean.
+__device__ __forceinline__ bool try_round_cell(const SegState& st, uint32_t s, unsigned long long key, const Geom& g,
+                                               const KeyFrame& kf, const ScanDesc* __restrict__ desc,
+                                               float4* __restrict__ train) {
+  bool ok = !(st.flags & kSegBad) && st.n < kSegMaxN;
+  float out[3] = {0.f, 0.f, 0.f};
+  if (ok) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const long long T = (long long)st.T[a];
+      if (T) {
+        float f = 0.f;
+        ok = round_mean64(T < 0 ? (unsigned long long)(-T) : (unsigned long long)T, st.n, meta_E(st.flags, a), f) &&
+             ok;
+        out[a] = T < 0 ? -f : f;
+      }
+    }
+  }
+  if (ok) {
+    const int label = (int)(key & ((1ull << g.label_bits) - 1));
+    train[s] = make_float4(out[0], out[1], out[2], (float)(label + 32 * map_of_segment(key, kf, desc)));
+  }
+  return ok;
+}
+
+__device__ __forceinline__ void st_carry(SegCarry* dst, const SegState& st, uint32_t s, uint32_t closed) {
+  SegCarry c;
+  c.st = st;
+  c.s = s;
+  c.closed = closed;
+  c.pad[0] = c.pad[1] = 0u;
+  *dst = c;
+}
+
+// Heads per tile of the sorted items: counts[t] for every tile t below
+// ceil(n / kSegTile), n = min(cap, dc->n_items).  Grid-stride over tiles.
+__global__ void __launch_bounds__(kSegThreads) seg_count_kernel(const unsigned long long* __restrict__ keys,
+                                                              int64_t cap, uint32_t* __restrict__ counts,
+                                                              const DevCounters* dc) {
+  __shared__ uint32_t s_w[kSegWarps];
+  if (dc->err) return;
+  const int64_t n = min(cap, (int64_t)dc->n_items);
+  const int64_t nt = (n + kSegTile - 1) / kSegTile;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t t = blockIdx.x; t < nt; t += gridDim.x) {
+    uint32_t c = 0u;
+#pragma unroll
+    for (int r = 0; r < kSegPer; ++r) {
+      const int64_t i = t * kSegTile + r * kSegThreads + threadIdx.x;
+      if (i < n) c += (i == 0 || keys[i] != keys[i - 1]) ? 1u : 0u;
+    }
+    c = __reduce_add_sync(0xffffffffu, c);
+    if (lane == 0) s_w[warp] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t total = 0u;
+#pragma unroll
+      for (int w = 0; w < kSegWarps; ++w) total += s_w[w];
+      counts[t] = total;
+    }
+    __syncthreads();
+  }
+}
+
+// work: [ntiles_cap] head counts (seg_count_kernel), tile counter, an unused
+// word, [ntiles_cap] closing flags (these two zero on entry).  carry: [2 ntiles_cap].
+// Dynamic shared memory: kSegSmemBytes.
+__global__ void __launch_bounds__(kSegThreads, 3) seg_reduce_kernel(
+    const unsigned long long* __restrict__ keys, const float4* __restrict__ items, int64_t cap,
+    uint32_t* __restrict__ seg_start, uint32_t* __restrict__ work, int64_t ntiles_cap, SegCarry* __restrict__ carry,
+    Geom g, float4* __restrict__ train, const ScanDesc* __restrict__ desc, KeyFrame kf, uint32_t* __restrict__ slow,
+    DevCounters* dc) {
+  extern __shared__ __align__(16) unsigned char seg_smem[];
+  SegState* s_cell = reinterpret_cast<SegState*>(seg_smem);                   // by tile-local cell index
+  uint32_t* s_head = reinterpret_cast<uint32_t*>(seg_smem + kSegCellBytes);  // the cell's first item
+  float4* s_items = reinterpret_cast<float4*>(seg_smem + kSegStageItems);     // load stage (aliases s_cell)
+  unsigned long long* s_keys = reinterpret_cast<unsigned long long*>(seg_smem + kSegStageKeys);
+  __shared__ SegState s_open;  // the run that opens the tile, of a cell whose head lies in an earlier tile
+  __shared__ uint32_t s_wsum[kSegWarps], s_wbefore[kSegWarps];
+  __shared__ uint32_t s_tile;
+  __shared__ int s_cross;      // the tile's last cell goes on in the next tile
+  if (dc->err) return;
+  const int64_t n = min(cap, (int64_t)dc->n_items);
+  const int64_t nt = (n + kSegTile - 1) / kSegTile;
+  const uint32_t* counts = work;
+  uint32_t* claim = work + ntiles_cap;
+  uint32_t* closing = claim + 2;
+  SegCarry* opening_run = carry;
+  SegCarry* closing_run = carry + ntiles_cap;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_tile = atomicAdd(claim, 1u);
+      s_cross = 0;
+      seg_clear(s_open);
+    }
+    __syncthreads();
+    const int64_t t = s_tile;
+    if (t >= nt) break;
+    const int64_t base = t * kSegTile;
+    const int64_t first = base + (int64_t)threadIdx.x * kSegPer;
+    const int64_t tile_last = min(n, base + kSegTile) - 1;
+    // stage the tile (s_keys[seg_pad(1 + r)] = key of item base + r; entries 0 and
+    // kSegTile + 1: the items just before and after the tile), then take the thread's members
+#pragma unroll
+    for (int r = 0; r < kSegPer; ++r) {
+      const int li = r * kSegThreads + (int)threadIdx.x;
+      if (base + li < n) {
+        s_keys[seg_pad(1 + li)] = keys[base + li];
+        s_items[seg_pad(li)] = items[base + li];
+      }
+    }
+    if (threadIdx.x == 0 && base > 0) s_keys[seg_pad(0)] = keys[base - 1];
+    if (threadIdx.x == 1 && base + kSegTile < n) s_keys[seg_pad(kSegTile + 1)] = keys[base + kSegTile];
+    __syncthreads();
+    unsigned long long kk[kSegPer];
+    float px[kSegPer], py[kSegPer], pz[kSegPer];
+    uint32_t heads = 0u;
+    const int l0 = (int)threadIdx.x * kSegPer;
+    unsigned long long prev = first > 0 && first <= n ? s_keys[seg_pad(l0)] : 0ull;
+#pragma unroll
+    for (int k = 0; k < kSegPer; ++k) {
+      const int64_t i = first + k;
+      kk[k] = 0ull;
+      px[k] = py[k] = pz[k] = 0.f;
+      if (i < n) {
+        kk[k] = s_keys[seg_pad(l0 + k + 1)];
+        const float4 p = s_items[seg_pad(l0 + k)];
+        px[k] = p.x;
+        py[k] = p.y;
+        pz[k] = p.z;
+        if (i == 0 || kk[k] != prev) heads |= 1u << k;
+        prev = kk[k];
+      }
+    }
+    uint32_t ends = heads >> 1;
+    if (first + kSegPer < n && s_keys[seg_pad(l0 + kSegPer + 1)] != prev) ends |= 1u << (kSegPer - 1);
+    if (first <= n - 1 && n - 1 < first + kSegPer) ends |= 1u << (int)(n - 1 - first);
+    const bool has_items = first < n;
+    const int last_k = has_items ? (int)(min(n - 1, first + kSegPer - 1) - first) : 0;
+    if (has_items && first + last_k == tile_last) s_cross = (ends & (1u << last_k)) ? 0 : 1;
+    // heads before this thread in the tile, in the tile, and before the tile
+    // (the barrier also ends the stage's reads)
+    const uint32_t c = __popc(heads);
+    uint32_t inc = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t u = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += u;
+    }
+    uint32_t before = 0u;
+    for (int64_t q = threadIdx.x; q < t; q += kSegThreads) before += counts[q];
+    before = __reduce_add_sync(0xffffffffu, before);
+    if (lane == 31) s_wsum[warp] = inc;
+    if (lane == 0) s_wbefore[warp] = before;
+    __syncthreads();
+    uint32_t hthread = inc - c, total = 0u, excl = 0u;
+#pragma unroll
+    for (int w = 0; w < kSegWarps; ++w) {
+      const uint32_t v = s_wsum[w];
+      hthread += w < warp ? v : 0u;
+      total += v;
+      excl += s_wbefore[w];
+    }
+    {
+      uint32_t j = hthread;
+#pragma unroll
+      for (int k = 0; k < kSegPer; ++k)
+        if (heads & (1u << k)) {
+          seg_start[excl + j] = (uint32_t)(first + k);
+          s_head[j++] = (uint32_t)(first + k);
+        }
+      if (first <= n - 1 && n - 1 < first + kSegPer) {  // this thread holds the last item
+        seg_start[excl + total] = (uint32_t)n;
+        dc->n_train = excl + total;
+      }
+    }
+    // sum the members: the run before the first head (P), then one run per head,
+    // each stored at its cell's tile-local index
+    SegState R, P;
+    seg_clear(R);
+    seg_clear(P);
+    bool hashead = false;
+    uint32_t j = hthread - 1u;  // tile-local index of the running cell once a head is seen
+    const int tshift = g.label_bits + kLocalBits;
+    unsigned long long tprev = ~0ull;  // sort tile of the previous member, and its unit
+    TileUnit unit;
+    unit.meta = unit.bad = 0u;
+    unit.scale[0] = unit.scale[1] = unit.scale[2] = 0.f;
+#pragma unroll
+    for (int k = 0; k < kSegPer; ++k) {
+      if (first + k < n) {
+        if ((kk[k] >> tshift) != tprev) {
+          tprev = kk[k] >> tshift;
+          unit = tile_unit(kk[k], g, kf, desc);
+        }
+        if (heads & (1u << k)) {
+          if (!hashead) P = R;
+          hashead = true;
+          seg_clear(R);
+          ++j;
+        }
+        seg_add(R, unit, px[k], py[k], pz[k]);
+        if (hashead && ((ends & (1u << k)) || k == last_k)) s_cell[j] = R;
+      }
+    }
+    if (!hashead) P = R;
+    __syncthreads();
+    if (has_items && !(heads & 1u)) {  // the end of a cell begun before this thread
+      SegState* dst = hthread > 0u ? s_cell + (hthread - 1u) : &s_open;
+      atomicAdd(&dst->T[0], P.T[0]);
+      atomicAdd(&dst->T[1], P.T[1]);
+      atomicAdd(&dst->T[2], P.T[2]);
+      atomicAdd(&dst->n, P.n);
+      atomicOr(&dst->flags, P.flags);
+    }
+    __syncthreads();
+    // round every cell whose head lies in the tile, but a last one that goes on
+    const bool cross_out = s_cross && total > 0u;
+    const uint32_t nround = total - (cross_out ? 1u : 0u);
+    for (uint32_t q = threadIdx.x; q < nround; q += kSegThreads)
+      if (!try_round_cell(s_cell[q], excl + q, keys[s_head[q]], g, kf, desc, train))
+        slow[atomicAdd(&dc->n_slow, 1u)] = excl + q;
+    if (threadIdx.x == 0) {
+      if (cross_out) {
+        st_carry(closing_run + t, s_cell[total - 1u], excl + total - 1u, 0u);
+        closing[t] = 1u;
+      }
+      if (s_open.n) st_carry(opening_run + t, s_open, 0u, (total > 0u || !s_cross) ? 1u : 0u);
     }
   }
 }
 
-// Segments of more than kHuge members (cells next to the sensor): one CTA
-// each, same arithmetic as centroid_kernel.
-__global__ void __launch_bounds__(256) huge_centroid_kernel(const unsigned long long* __restrict__ keys,
-                                                            const uint32_t* __restrict__ perm,
-                                                            const float4* __restrict__ items,
-                                                            const uint32_t* __restrict__ seg_start, Geom g,
-                                                            float4* __restrict__ train,
-                                                            const ScanDesc* __restrict__ desc, KeyFrame kf,
-                                                            const uint32_t* __restrict__ huge, DevCounters* dc) {
-  __shared__ int s_emin[3][8], s_emax[3][8], s_neg[3][8];
-  __shared__ unsigned long long s_lo[3][8], s_hi[3][8];
+// After seg_reduce_kernel: the cells it left to the slow form (`slow`, one warp
+// each), and the cells that cross a tile boundary (one warp per tile whose
+// closing flag is set: lane 0 joins the partial sums of the following tiles up
+// to the one where the cell ends, and rounds them, or the warp takes the slow
+// form).  work and carry as seg_reduce_kernel left them.
+__global__ void __launch_bounds__(256) finish_cells_kernel(const unsigned long long* __restrict__ keys,
+                                                           const float4* __restrict__ items, int64_t cap,
+                                                           const uint32_t* __restrict__ seg_start,
+                                                           const uint32_t* __restrict__ work, int64_t ntiles_cap,
+                                                           const SegCarry* __restrict__ carry, Geom g,
+                                                           float4* __restrict__ train,
+                                                           const ScanDesc* __restrict__ desc, KeyFrame kf,
+                                                           const uint32_t* __restrict__ slow, DevCounters* dc) {
   if (dc->err) return;
-  const uint32_t nh = dc->n_huge;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (uint32_t h = blockIdx.x; h < nh; h += gridDim.x) {
-    const uint32_t s = huge[h];
-    const uint32_t a = seg_start[s], b = seg_start[s + 1], n = b - a;
-    AxisAcc w[3];
-    FastAxis fa[3];
-    const float4 p0 = item_at(items, perm, a);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      w[c].init();
-      fa[c].init(axis_of(p0, c), g.fast_lim);
+  const int64_t n = min(cap, (int64_t)dc->n_items);
+  const int64_t nt = (n + kSegTile - 1) / kSegTile;
+  const uint32_t ns = dc->n_slow;
+  const uint32_t* closing = work + ntiles_cap + 2;
+  const SegCarry* opening_run = carry;
+  const SegCarry* closing_run = carry + ntiles_cap;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t j = warp; j < (int64_t)ns + nt; j += nwarps) {
+    if (j < (int64_t)ns) {
+      slow_cell(slow[j], keys, items, seg_start, g, train, desc, kf);
+      continue;
     }
-    const bool slow = !fa[0].on || !fa[1].on || !fa[2].on;  // CTA-uniform
-    {
-      uint32_t i = a + threadIdx.x;
-      for (; i + 768 < b; i += 1024) {  // four independent gathers in flight
-        const float4 ps[4] = {item_at(items, perm, i), item_at(items, perm, i + 256), item_at(items, perm, i + 512), item_at(items, perm, i + 768)};
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int c = 0; c < 3; ++c) {
-            if (fa[c].on) fa[c].add(axis_of(ps[u], c));
-            else w[c].see(axis_of(ps[u], c));
-          }
+    const int64_t u = j - ns;
+    if (!closing[u]) continue;  // warp-uniform
+    int done = 0;
+    uint32_t s = 0u;
+    if (lane == 0) {
+      const SegCarry h = closing_run[u];
+      SegState acc = h.st;
+      for (int64_t v = u + 1; v < nt; ++v) {
+        const SegCarry o = opening_run[v];
+        seg_merge(acc, o.st);
+        if (o.closed) break;
       }
-      for (; i < b; i += 256) {
-        const float4 p = item_at(items, perm, i);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          if (fa[c].on) fa[c].add(axis_of(p, c));
-          else w[c].see(axis_of(p, c));
-        }
-      }
+      s = h.s;
+      done = try_round_cell(acc, s, keys[(u + 1) * kSegTile - 1], g, kf, desc, train) ? 1 : 0;
     }
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      if (fa[c].on) {
-        const unsigned long long tsum = warp_sum_u64(fa[c].T);
-        if (lane == 0) {
-          s_lo[c][warp] = tsum;
-          s_hi[c][warp] = 0ull;
-        }
-      }
-    }
-    bool fit[3] = {false, false, false};
-    if (slow) {  // an axis next to a coordinate plane: range first, then the 128-bit sums
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        warp_range(w[c]);
-        if (lane == 0) {
-          s_emin[c][warp] = w[c].emin;
-          s_emax[c][warp] = w[c].emax;
-          s_neg[c][warp] = w[c].neg ? 1 : 0;
-        }
-      }
-      __syncthreads();
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        int mn = 1 << 20, mx = -(1 << 20), ng = 0;
-        for (int k = 0; k < 8; ++k) {
-          mn = min(mn, s_emin[c][k]);
-          mx = max(mx, s_emax[c][k]);
-          ng |= s_neg[c][k];
-        }
-        w[c].emin = mn;
-        w[c].emax = mx;
-        w[c].neg = ng != 0;
-        fit[c] = !fa[c].on && w[c].fits(n);
-      }
-      U128 t[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) t[c].lo = t[c].hi = 0ull;
-      for (uint32_t i = a + threadIdx.x; i < b; i += 256) {
-        const float4 p = item_at(items, perm, i);
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-          if (fit[c]) w[c].add(t[c], axis_of(p, c));
-      }
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        if (!fa[c].on) {
-          t[c] = warp_sum_u128(t[c]);
-          if (lane == 0) {
-            s_lo[c][warp] = t[c].lo;
-            s_hi[c][warp] = t[c].hi;
-          }
-        }
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      float out[3];
-      for (int c = 0; c < 3; ++c) {
-        U128 tt;
-        tt.lo = tt.hi = 0ull;
-        for (int k = 0; k < 8; ++k) u128_add(tt, s_lo[c][k], s_hi[c][k]);
-        if (fa[c].on) {
-          fa[c].T = tt.lo;
-          out[c] = fa[c].finish(n);
-        } else {
-          out[c] = finish_axis(w[c], fit[c], tt, n, items, perm, a, b, c);
-        }
-      }
-      const unsigned long long k = keys[a];
-      const int label = (int)(k & ((1ull << g.label_bits) - 1));
-      train[s] = make_float4(out[0], out[1], out[2], (float)(label + 32 * map_of_segment(k, kf, desc)));
-    }
-    __syncthreads();
+    done = __shfl_sync(0xffffffffu, done, 0);
+    s = __shfl_sync(0xffffffffu, s, 0);
+    if (!done) slow_cell(s, keys, items, seg_start, g, train, desc, kf);
   }
 }
 
@@ -931,30 +1083,29 @@ cudaError_t launch_emit(MapState& m, int ns, int64_t total_n, const KeyFrame& kf
 cudaError_t launch_downsample_n(MapState& m, const KeyFrame& kf, int64_t nitems) {
   Scratch& s = m.s;
   const int bits = kf.total_bits + kf.scan_bits;
-  m.launches += 1 + (bits + 7) / 8 + 1 + 3;  // sort, segments, centroids
-  // the last pass also moves the items into sorted order (s.sitems), so the centroids read them in a stream
+  m.launches += 1 + (bits + 7) / 8 + 3;  // sort, head counts, segment pass, crossing and slow cells
+  // the last pass also moves the items into sorted order (s.sitems), so the segment pass reads them in a stream
   cudaError_t e = radix_sort_pairs(s.keys, s.vals, s.keys2, s.vals2, &m.dc->n_items, nitems, bits, s.hist,
                                    m.sm_count, m.dc, m.stream, s.items, s.sitems);
   if (e != cudaSuccess) return e;
-  {  // segments in one pass; s.flags holds its tile status words and counter
-    const int64_t stiles = (nitems + kSegTile - 1) / kSegTile;
-    e = cudaMemsetAsync(s.flags, 0, sizeof(uint32_t) * (stiles + 1), m.stream);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, seg_heads_kernel, kSegThreads, 0);
-    if (e != cudaSuccess) return e;
-    const unsigned sblocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(stiles, (int64_t)m.sm_count * std::max(1, per_sm)));
-    seg_heads_kernel<<<sblocks, kSegThreads, 0, m.stream>>>(s.keys, nitems, s.seg_start, s.flags, stiles, m.dc);
-  }
-  {
-    const unsigned cblocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((nitems + 255) / 256, (int64_t)m.sm_count * m.tune.ingest_ctas_per_sm));
-    centroid_kernel<<<cblocks, 256, 0, m.stream>>>(s.keys, nullptr, s.sitems, s.seg_start, m.g, s.train, s.desc, kf,
-                                                   s.huge, s.mid, m.dc);
-    mid_centroid_kernel<<<(unsigned)(m.sm_count * std::max(1, m.tune.ingest_ctas_per_sm / 2)), 256, 0, m.stream>>>(s.keys, nullptr, s.sitems, s.seg_start, m.g,
-                                                                        s.train, s.desc, kf, s.mid, m.dc);
-    huge_centroid_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(nitems / kHuge + 1, 1024)), 256, 0,
-                           m.stream>>>(s.keys, nullptr, s.sitems, s.seg_start, m.g, s.train, s.desc, kf, s.huge, m.dc);
-  }
+  const int64_t stiles = (nitems + kSegTile - 1) / kSegTile;
+  e = cudaMemsetAsync(s.flags + stiles, 0, sizeof(uint32_t) * (stiles + 2), m.stream);
+  if (e != cudaSuccess) return e;
+  seg_count_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(stiles, 65535)), kSegThreads, 0, m.stream>>>(
+      s.keys, nitems, s.flags, m.dc);
+  e = cudaFuncSetAttribute(seg_reduce_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSegSmemBytes);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, seg_reduce_kernel, kSegThreads, kSegSmemBytes);
+  if (e != cudaSuccess) return e;
+  const unsigned sblocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(stiles, (int64_t)m.sm_count * std::max(1, per_sm)));
+  seg_reduce_kernel<<<sblocks, kSegThreads, kSegSmemBytes, m.stream>>>(s.keys, s.sitems, nitems, s.seg_start, s.flags,
+                                                                       stiles, static_cast<SegCarry*>(s.carry), m.g,
+                                                                       s.train, s.desc, kf, s.slow, m.dc);
+  const unsigned fblocks = (unsigned)std::min<int64_t>(4096, std::max<int64_t>(2 * m.sm_count, (stiles + 7) / 8));
+  finish_cells_kernel<<<fblocks, 256, 0, m.stream>>>(s.keys, s.sitems, nitems, s.seg_start, s.flags,
+                                                                       stiles, static_cast<const SegCarry*>(s.carry),
+                                                                       m.g, s.train, s.desc, kf, s.slow, m.dc);
   return cudaGetLastError();
 }
 
@@ -973,25 +1124,6 @@ cudaError_t launch_train_prepare(MapState& m, const float4* in, int64_t p, const
   if (e != cudaSuccess) return e;
   train_gather_kernel<<<grid_for(p, 256), 256, 0, m.stream>>>(in, s.vals, p, m.active_map, s.train, s.seg_start,
                                                                m.dc);
-  return cudaGetLastError();
-}
-
-// Failure-detection self-test: the segment pass over three tiles whose tile
-// counter starts at 1, so tile 0 is never claimed and the look-back of the
-// others runs out; they must end with SBKI_ERR_TIMEOUT instead of spinning on.
-// Buffers are the caller's (device): keys [3 kSegTile] (any values),
-// seg_start [3 kSegTile + 1], work [4], dc (zeroed DevCounters).
-cudaError_t launch_wait_selftest(unsigned long long* keys, uint32_t* seg_start, uint32_t* work, DevCounters* dc,
-                                 cudaStream_t st) {
-  const int64_t n = 3 * kSegTile;
-  cudaError_t e = cudaMemsetAsync(work, 0, sizeof(uint32_t) * 4, st);
-  if (e != cudaSuccess) return e;
-  const uint32_t one = 1u, items = (uint32_t)n;
-  e = cudaMemcpyAsync(work + 3, &one, sizeof(one), cudaMemcpyHostToDevice, st);  // tile counter: skip tile 0
-  if (e != cudaSuccess) return e;
-  e = cudaMemcpyAsync(&dc->n_items, &items, sizeof(items), cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return e;
-  seg_heads_kernel<<<2, kSegThreads, 0, st>>>(keys, n, seg_start, work, 3, dc);
   return cudaGetLastError();
 }
 

@@ -46,12 +46,13 @@ constexpr size_t kOffKeys2 = align256(kOffKeys + 8 * kMaxItems);
 constexpr size_t kOffVals = align256(kOffKeys2 + 8 * kMaxItems);
 constexpr size_t kOffVals2 = align256(kOffVals + 4 * kMaxItems);
 constexpr size_t kOffFlags = align256(kOffVals2 + 4 * kMaxItems);
-constexpr size_t kOffSeg = align256(kOffFlags + 4 * (kMaxItems + 1));
+constexpr size_t kFlagWords = kMaxItems + 1 > 2 * sbki::seg_tiles(kMaxItems) + 2 ? kMaxItems + 1 : 2 * sbki::seg_tiles(kMaxItems) + 2;
+constexpr size_t kOffSeg = align256(kOffFlags + 4 * kFlagWords);
 constexpr size_t kOffTrain = align256(kOffSeg + 4 * (kMaxItems + 1));
-constexpr size_t kOffMid = align256(kOffTrain + 16 * kMaxItems);
-constexpr size_t kOffHuge = align256(kOffMid + 4 * (kMaxItems / 16 + 2));
+constexpr size_t kOffSlow = align256(kOffTrain + 16 * kMaxItems);
+constexpr size_t kOffCarry = align256(kOffSlow + 4 * (kMaxItems + 2));
 constexpr size_t kHistEntries = (size_t)sbki::radix_work_entries(kMaxItems);
-constexpr size_t kOffHist = align256(kOffHuge + 4 * (kMaxItems / 1024 + 2));
+constexpr size_t kOffHist = align256(kOffCarry + (size_t)sbki::kSegCarryBytes * 2 * sbki::seg_tiles(kMaxItems));
 constexpr size_t kOffScanTmp = align256(kOffHist + 4 * kHistEntries);
 constexpr size_t kScanTmpBytes = 8 * ((kMaxItems + 2) / 2048 + 64);  // partial sums of the largest scan
 constexpr size_t kOffDesc = align256(kOffScanTmp + kScanTmpBytes);
@@ -153,8 +154,8 @@ sbki_status run(const sbki_params* params, const float* points, const int32_t* l
   s.flags = reinterpret_cast<uint32_t*>(base + kOffFlags);
   s.seg_start = reinterpret_cast<uint32_t*>(base + kOffSeg);
   s.train = reinterpret_cast<float4*>(base + kOffTrain);
-  s.mid = reinterpret_cast<uint32_t*>(base + kOffMid);
-  s.huge = reinterpret_cast<uint32_t*>(base + kOffHuge);
+  s.slow = reinterpret_cast<uint32_t*>(base + kOffSlow);
+  s.carry = base + kOffCarry;
   s.hist = reinterpret_cast<uint32_t*>(base + kOffHist);
   s.hist_cap = (int64_t)kHistEntries;
   s.scan_tmp = base + kOffScanTmp;

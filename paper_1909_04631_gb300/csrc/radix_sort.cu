@@ -288,4 +288,21 @@ cudaError_t radix_sort_pairs(unsigned long long*& keys, uint32_t*& vals, unsigne
   return cudaGetLastError();
 }
 
+cudaError_t radix_wait_selftest(unsigned long long* keys, uint32_t* vals, unsigned long long* keys_out,
+                                uint32_t* vals_out, uint32_t* n_dev, uint32_t* work, DevCounters* dc, cudaStream_t st) {
+  const int64_t ntiles = (kSelftestItems + kRadixTile - 1) / kRadixTile;
+  const Work w = work_of(work, ntiles);
+  cudaError_t e = cudaMemsetAsync(work, 0, sizeof(uint32_t) * radix_work_entries(kSelftestItems), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * kSelftestItems, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(vals, 0, sizeof(uint32_t) * kSelftestItems, st);
+  const uint32_t one = 1u, items = (uint32_t)kSelftestItems;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(w.tiles, &one, sizeof(one), cudaMemcpyHostToDevice, st);  // skip tile 0
+  if (e == cudaSuccess) e = cudaMemcpyAsync(n_dev, &items, sizeof(items), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(onesweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStageBytes);
+  if (e != cudaSuccess) return e;
+  onesweep_kernel<<<2, kThreads, kStageBytes, st>>>(keys, vals, keys_out, vals_out, n_dev, 0, ntiles, w, nullptr,
+                                                    nullptr, dc);
+  return cudaGetLastError();
+}
+
 }  // namespace sbki

@@ -96,8 +96,7 @@ __global__ void begin_kernel(DevCounters* dc, uint32_t epoch, uint32_t n_points)
   dc->n_tiles = 0;
   dc->n_touched = 0;
   dc->n_new = 0;
-  dc->n_huge = 0;
-  dc->n_mid = 0;
+  dc->n_slow = 0;
   dc->work_next = 0;
   dc->epoch = epoch;
   dc->n_blocks_before = dc->n_blocks;
@@ -120,8 +119,7 @@ __global__ void batch_begin_kernel(DevCounters* dc, const ScanDesc* desc, int ns
   dc->n_tiles = 0;
   dc->n_touched = 0;
   dc->n_new = 0;
-  dc->n_huge = 0;
-  dc->n_mid = 0;
+  dc->n_slow = 0;
   dc->work_next = 0;
   dc->epoch = dc->epoch + 1;
   dc->n_blocks_before = dc->n_blocks;
@@ -525,7 +523,7 @@ sbki_status sbki_create_map(const sbki_params* params, sbki_map** out) {
   if ((ce = dalloc(&s.keys2, S)) != cudaSuccess) return bail("keys2", ce);
   if ((ce = dalloc(&s.vals, S)) != cudaSuccess) return bail("vals", ce);
   if ((ce = dalloc(&s.vals2, S)) != cudaSuccess) return bail("vals2", ce);
-  if ((ce = dalloc(&s.flags, S + 1)) != cudaSuccess) return bail("flags", ce);
+  if ((ce = dalloc(&s.flags, std::max<int64_t>(S + 1, 2 * seg_tiles(S) + 2))) != cudaSuccess) return bail("flags", ce);
   if ((ce = dalloc(&s.seg_start, S + 1)) != cudaSuccess) return bail("seg_start", ce);
   if ((ce = dalloc(&s.train, S)) != cudaSuccess) return bail("train", ce);
   s.hist_cap = radix_hist_entries(S);
@@ -534,8 +532,9 @@ sbki_status sbki_create_map(const sbki_params* params, sbki_map** out) {
   if ((ce = cudaMalloc(&s.scan_tmp, scan_tmp_bytes(scan_n))) != cudaSuccess) return bail("scan partials", ce);
   if ((ce = dalloc(&s.touched, m.hash_cap)) != cudaSuccess) return bail("touched list", ce);
   if ((ce = dalloc(&s.bbox, 8)) != cudaSuccess) return bail("bbox", ce);
-  if ((ce = dalloc(&s.huge, S / 1024 + 2)) != cudaSuccess) return bail("huge cells", ce);
-  if ((ce = dalloc(&s.mid, S / 16 + 2)) != cudaSuccess) return bail("long cells", ce);
+  if ((ce = dalloc(&s.slow, S + 2)) != cudaSuccess) return bail("slow cells", ce);
+  if ((ce = cudaMalloc(&s.carry, (size_t)kSegCarryBytes * 2 * seg_tiles(S))) != cudaSuccess)
+    return bail("segment carries", ce);
   if ((ce = dalloc(&s.desc, kMaxScans + 1)) != cudaSuccess) return bail("scan descriptors", ce);
   if ((ce = cudaMallocHost((void**)&m.hdesc, sizeof(ScanDesc) * (kMaxScans + 1))) != cudaSuccess)
     return bail("host scan descriptors", ce);
@@ -563,7 +562,7 @@ void sbki_destroy_map(sbki_map* map) {
     DeviceGuard dg(m.device);
     if (m.stream || m.dc) cudaStreamSynchronize(m.stream);
     void* ptrs[] = {m.clen, m.gpool, m.dacc, m.ctab, m.hkeys, m.hvals, m.hmark, m.hcnt, m.hcur, m.boff, m.blist, m.alpha, m.pool_keys, m.pairs, m.dc, m.s.items, m.s.sitems, m.s.keys, m.s.keys2,
-                    m.s.vals, m.s.vals2, m.s.flags, m.s.seg_start, m.s.train, m.s.hist, m.s.scan_tmp, m.s.touched, m.s.fresh, m.s.bbox, m.s.huge, m.s.mid,
+                    m.s.vals, m.s.vals2, m.s.flags, m.s.seg_start, m.s.train, m.s.hist, m.s.scan_tmp, m.s.touched, m.s.fresh, m.s.bbox, m.s.slow, m.s.carry,
                     m.s.desc};
     for (void* p : ptrs)
       if (p) cudaFree(p);
@@ -1226,26 +1225,25 @@ sbki_status sbki_selftest_bounded_wait(int32_t device, int32_t* device_status) {
   if (!device_status) return fail(nullptr, SBKI_ERR_INVALID_ARG, "device_status is NULL");
   *device_status = SBKI_OK;
   DeviceGuard dg(device);
-  const int64_t n = 3 * 4096;
-  unsigned long long* keys = nullptr;
-  uint32_t *seg = nullptr, *work = nullptr;
+  unsigned long long *keys = nullptr, *keys_out = nullptr;
+  uint32_t *vals = nullptr, *vals_out = nullptr, *n_dev = nullptr, *work = nullptr;
   DevCounters* dc = nullptr;
   cudaStream_t st = nullptr;
   cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = dalloc(&keys, n);
-  if (e == cudaSuccess) e = dalloc(&seg, n + 1);
-  if (e == cudaSuccess) e = dalloc(&work, 4);
+  if (e == cudaSuccess) e = dalloc(&keys, kSelftestItems);
+  if (e == cudaSuccess) e = dalloc(&keys_out, kSelftestItems);
+  if (e == cudaSuccess) e = dalloc(&vals, kSelftestItems);
+  if (e == cudaSuccess) e = dalloc(&vals_out, kSelftestItems);
+  if (e == cudaSuccess) e = dalloc(&n_dev, 1);
+  if (e == cudaSuccess) e = dalloc(&work, radix_work_entries(kSelftestItems));
   if (e == cudaSuccess) e = dalloc(&dc, 1);
-  if (e == cudaSuccess) e = cudaMemsetAsync(keys, 0, sizeof(unsigned long long) * n, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(dc, 0, sizeof(DevCounters), st);
-  if (e == cudaSuccess) e = launch_wait_selftest(keys, seg, work, dc, st);
+  if (e == cudaSuccess) e = radix_wait_selftest(keys, vals, keys_out, vals_out, n_dev, work, dc, st);
   int32_t err = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&err, &dc->err, sizeof(err), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  cudaFree(keys);
-  cudaFree(seg);
-  cudaFree(work);
-  cudaFree(dc);
+  void* ptrs[] = {keys, keys_out, vals, vals_out, n_dev, work, dc};
+  for (void* p : ptrs) cudaFree(p);
   if (st) cudaStreamDestroy(st);
   if (e != cudaSuccess) return fail(nullptr, SBKI_ERR_CUDA, "bounded-wait self-test: %s", cudaGetErrorString(e));
   *device_status = err;

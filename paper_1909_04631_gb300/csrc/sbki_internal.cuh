@@ -22,6 +22,10 @@ constexpr int kTileShift = 3;            // training-point tiles are 8^3 ds cell
 constexpr int kTileEdge = 1 << kTileShift;
 constexpr int kLocalBits = 3 * kTileShift;
 constexpr int kParts = 8;                // candidate lists: sub-voxel parts per axis (kParts^3 lists)
+constexpr int kSegTileItems = 2048;      // sorted items per tile of the segment pass
+constexpr int kSegCarryBytes = 48;       // one partial cell sum carried across a segment tile
+// tiles of the segment pass over n items
+constexpr int64_t seg_tiles(int64_t n) { return (n + kSegTileItems - 1) / kSegTileItems; }
 
 // ---------------------------------------------------------------- device counters
 // One instance per map, in device memory; every kernel reads its sizes here so
@@ -42,8 +46,7 @@ struct DevCounters {
   uint32_t epoch;                     // scan counter (touched marks)
   uint32_t n_blocks_before;           // n_blocks when this scan started
   uint32_t n_list;                    // (training point, touched block) pairs, this scan
-  uint32_t n_huge;                    // downsampling cells summed by a whole CTA, this scan
-  uint32_t n_mid;                     // downsampling cells summed by a warp, this scan
+  uint32_t n_slow;                    // downsampling cells left to the slow exact mean, this scan
   uint32_t n_points;                  // input points of the update (all scans)
   int32_t tbox[6];                    // ds-tile bounding box of the kept hits (min xyz, max xyz)
 };
@@ -104,7 +107,7 @@ struct Scratch {
   unsigned long long* keys2 = nullptr;  // [s_cap]
   uint32_t* vals = nullptr;       // [s_cap] source positions
   uint32_t* vals2 = nullptr;      // [s_cap]
-  uint32_t* flags = nullptr;      // [s_cap+1] segment heads, scanned
+  uint32_t* flags = nullptr;      // [max(s_cap + 1, 2 seg_tiles(s_cap) + 2)] segment-pass tile words
   uint32_t* seg_start = nullptr;  // [s_cap+1]
   float4* train = nullptr;        // [s_cap] training points (xyz, label bits), tile-sorted
   int64_t s_cap = 0;
@@ -116,8 +119,8 @@ struct Scratch {
   uint32_t* touched = nullptr;    // [hash_cap] hash slots touched this scan
   uint32_t* fresh = nullptr;      // [hash_cap] hash slots created this scan
   int* bbox = nullptr;            // [6] tile bounding box of a given training set
-  uint32_t* huge = nullptr;       // [s_cap / 1024 + 2] very long downsampling cells
-  uint32_t* mid = nullptr;        // [s_cap / 16 + 2] long downsampling cells
+  uint32_t* slow = nullptr;       // [s_cap + 2] downsampling cells left to the slow exact mean
+  void* carry = nullptr;          // [2 seg_tiles(s_cap)] partial sums of cells crossing a segment tile
   ScanDesc* desc = nullptr;       // [kMaxScans + 1] scans of the current update
 };
 
@@ -279,6 +282,14 @@ cudaError_t radix_sort_pairs(unsigned long long*& keys, uint32_t*& vals, unsigne
                              int sm_count, DevCounters* dc, cudaStream_t st, const float4* payload = nullptr,
                              float4* payload_out = nullptr);
 int64_t radix_hist_entries(int64_t cap);
+// Failure-detection self-test of the sort's bounded waits: one digit pass over
+// kSelftestItems items (device buffers of that many entries; work:
+// radix_work_entries(kSelftestItems) words; n_dev one word; dc zeroed) whose
+// tile counter starts at 1, so tile 0 never publishes its counts and the
+// look-back of the other tiles runs out with SBKI_ERR_TIMEOUT.
+constexpr int64_t kSelftestItems = 3 * kRadixTile;
+cudaError_t radix_wait_selftest(unsigned long long* keys, uint32_t* vals, unsigned long long* keys_out,
+                                uint32_t* vals_out, uint32_t* n_dev, uint32_t* work, DevCounters* dc, cudaStream_t st);
 
 // ingest.cu
 // ingest of the ns scans described in m.s.desc (ns + 1 entries, the last holding the total)
@@ -287,8 +298,6 @@ cudaError_t launch_emit(MapState& m, int ns, int64_t total_n, const KeyFrame& kf
 cudaError_t launch_downsample_n(MapState& m, const KeyFrame& kf, int64_t nitems);
 cudaError_t launch_train_bbox(MapState& m, const float4* in, int64_t p, int* bbox_dev);
 cudaError_t launch_train_prepare(MapState& m, const float4* in, int64_t p, const KeyFrame& kf);
-cudaError_t launch_wait_selftest(unsigned long long* keys, uint32_t* seg_start, uint32_t* work, DevCounters* dc,
-                                 cudaStream_t st);
 
 // blocks.cu
 cudaError_t launch_touch_blocks(MapState& m, const KeyFrame& kf, int64_t bound);

@@ -1,6 +1,7 @@
 """Failure detection without a GPU fault: a device-side wait whose flag is never
-set (the first tile of the single-pass segment step is never processed) runs
-out after its bound and reports SBKI_ERR_TIMEOUT; the context stays usable."""
+set (the look-back of one radix-sort digit pass, over tiles whose first one is
+never processed) runs out after its bound and reports SBKI_ERR_TIMEOUT; the
+context stays usable."""
 import time
 
 import numpy as np

@@ -131,6 +131,70 @@ def test_training_set_bit_exact_small_scan(sb, orc):
     np.testing.assert_array_equal(gx, ox)
 
 
+def _plane_cells_scan():
+    """Hits (identity pose, sensor at the origin) whose cells lie next to the
+    coordinate planes: members whose exponents span about 95 binades (past a
+    64-bit sum), a subnormal member beside normal ones (past a 128-bit sum),
+    cells with a subnormal exact mean, a long cell of tiny and zero coordinates,
+    and a cell of 9000 members, which crosses whole segment tiles.  The free
+    samples of the nearly parallel rays pile into long cells of their own."""
+    rng = np.random.default_rng(23)
+    rows = []
+    for y in (1e-30, 0.05, 3e-3, 7e-25, 0.02):
+        rows.append((4.02, y, 0.52))
+    for y in (1e-44, 0.05, 0.031):
+        rows.append((5.02, y, 0.52))
+    for y in (1e-39, 2e-39, 3.5e-39):
+        rows.append((6.02, y, 0.52))
+    for y in (-1e-30, -0.05, -2e-9):
+        rows.append((4.02, y, 1.52))
+    for z in (1e-30, 0.07, 4e-12, -1e-33, -0.06):
+        rows.append((4.52, 1.05, z))
+    long_y = rng.uniform(0.0, 0.09, 6000).astype(np.float32)
+    long_y[:50] = 0.0
+    long_y[50:60] = np.float32(1e-30)
+    rows += [(3.02 + 0.05 * rng.random(), y, 2.02) for y in long_y]
+    rows += [(4.0 + 0.09 * rng.random(), 1.0 + 0.09 * rng.random(), 2.55) for _ in range(9000)]
+    pts = np.array(rows, np.float32)
+    lab = np.ones(len(pts), np.int32)
+    lab[-9000:] = 2
+    return pts, lab
+
+
+def test_centroids_exact_next_to_coordinate_planes(sb, orc):
+    prm = dict(res=0.1, length_scale=0.3, sigma0=1.0, alpha0=0.001, free_step=0.3, num_classes=3)
+    pts, lab = _plane_cells_scan()
+    T = np.eye(4)
+    m = _gpu_map(sb, prm)
+    gx, gl = m.training_set(pts, lab, T)
+    ox, ol, st = orc.training_set(orc.params(**prm), pts, lab, T)
+    assert len(gx) == st["train"]
+    gx, gl = _sorted_train(gx, gl)
+    ox, ol = _sorted_train(ox, ol)
+    np.testing.assert_array_equal(gl, ol)
+    np.testing.assert_array_equal(gx, ox)
+    # the subnormal-mean cells really have subnormal centroids
+    assert np.any((np.abs(gx[:, 1]) > 0) & (np.abs(gx[:, 1]) < np.finfo(np.float32).tiny))
+
+
+def test_centroid_of_a_cell_with_both_signs(sb, orc):
+    """ds = 2: x fp32(1/ds) of -2^-149 rounds to -0, so that member shares cell 0
+    with positive coordinates; the mean is exact over the signed members."""
+    prm = dict(res=0.1, length_scale=0.3, sigma0=1.0, alpha0=0.001, free_step=0.3, num_classes=3, ds_res=2.0)
+    tiny = np.float32(np.finfo(np.float32).smallest_subnormal)
+    pts = np.array([[5.0, -tiny, 0.5], [5.0, 0.5, 0.5], [5.0, 0.25, 0.7], [7.0, -tiny, 0.5], [7.0, -tiny, 0.5],
+                    [7.0, tiny, 0.5]], np.float32)
+    lab = np.array([1, 1, 1, 2, 2, 2], np.int32)
+    m = _gpu_map(sb, prm, ds_res=2.0)
+    gx, gl = m.training_set(pts, lab, np.eye(4))
+    ox, ol, st = orc.training_set(orc.params(**prm), pts, lab, np.eye(4))
+    assert len(gx) == st["train"]
+    gx, gl = _sorted_train(gx, gl)
+    ox, ol = _sorted_train(ox, ol)
+    np.testing.assert_array_equal(gl, ol)
+    np.testing.assert_array_equal(gx, ox)
+
+
 def test_scan_drops_and_edge_cases(sb, orc):
     prm = dict(res=0.1, length_scale=0.3, sigma0=1.0, alpha0=0.001, num_classes=3, min_range=0.5, max_range=8.0)
     T = scenes.pose_matrix([0.3, -0.2, 1.0], yaw=0.4)
