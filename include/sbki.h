@@ -303,8 +303,8 @@ sbki_status sbki_grad(const sbki_params* params, const float* xyzl, int64_t p, c
  * created blocks read the prior, voxels not listed keep their values.  An
  * increment below half an ulp of alpha0 is already lost in the exported alpha
  * (alpha0 + increment rounds to alpha0), so such a voxel is restored with no
- * kernel mass and reads as unknown.  Pair counts are not restored.  SBKI_ERR_CAPACITY (pool full) leaves the block
- * set unchanged. */
+ * kernel mass and reads as unknown.  Pair counts are not restored.
+ * SBKI_ERR_CAPACITY (pool full) leaves the block set unchanged. */
 sbki_status sbki_import(sbki_map* map, const int64_t* keys, const float* alpha, int64_t count);
 
 /* Failure-detection self-test on `device` (diagnostic): runs one digit pass

@@ -566,8 +566,8 @@ __device__ void slow_cell(uint32_t s, const unsigned long long* __restrict__ key
 // (8 |t| + 10) ds, t the tile index on that axis, an upper bound of the tile's
 // |x|), so a cell's sum is a plain signed 64-bit integer in any order.  A
 // nonzero member with |x| 2^-E below 2^23 (it would have a fraction: within
-// about 2^-21 ds of a coordinate plane), a cell of 2^15 or more members, or a
-// mean below the FP32 normal range leaves the cell to slow_cell.
+// about 2^-21 ds of a coordinate plane) or a mean below the FP32 normal range
+// leaves the cell to slow_cell.
 // A thread stores the sums of every cell whose head it holds in shared memory;
 // the run before its first head (the end of a cell begun in an earlier thread)
 // is added there with shared-memory atomics; then the CTA rounds every cell.
@@ -954,8 +954,12 @@ __global__ void __launch_bounds__(kSegThreads, 3) seg_reduce_kernel(
 // After seg_reduce_kernel: the cells it left to the slow form (`slow`, one warp
 // each), and the cells that cross a tile boundary (one warp per tile whose
 // closing flag is set: lane 0 joins the partial sums of the following tiles up
-// to the one where the cell ends, and rounds them, or the warp takes the slow
-// form).  work and carry as seg_reduce_kernel left them.
+// to the one where the cell ends, in 128 bits (each part holds at most one
+// tile's members, but a cell may span many tiles), and rounds them, or the warp
+// takes the slow form).  work and carry as seg_reduce_kernel left them.
+__device__ __forceinline__ void add_i128(U128& t, unsigned long long v) {  // t += v read as signed 64-bit
+  u128_add(t, v, (long long)v < 0 ? ~0ull : 0ull);
+}
 __global__ void __launch_bounds__(256) finish_cells_kernel(const unsigned long long* __restrict__ keys,
                                                            const float4* __restrict__ items, int64_t cap,
                                                            const uint32_t* __restrict__ seg_start,
@@ -985,14 +989,43 @@ __global__ void __launch_bounds__(256) finish_cells_kernel(const unsigned long l
     uint32_t s = 0u;
     if (lane == 0) {
       const SegCarry h = closing_run[u];
-      SegState acc = h.st;
+      U128 T[3];
+      uint32_t cn = h.st.n, flags = h.st.flags;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        T[c].lo = T[c].hi = 0ull;
+        add_i128(T[c], h.st.T[c]);
+      }
       for (int64_t v = u + 1; v < nt; ++v) {
         const SegCarry o = opening_run[v];
-        seg_merge(acc, o.st);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) add_i128(T[c], o.st.T[c]);
+        cn += o.st.n;
+        flags |= o.st.flags;
         if (o.closed) break;
       }
       s = h.s;
-      done = try_round_cell(acc, s, keys[(u + 1) * kSegTile - 1], g, kf, desc, train) ? 1 : 0;
+      bool ok = !(flags & kSegBad);
+      float out[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        if (!ok || (T[c].lo | T[c].hi) == 0ull) continue;
+        const bool neg = (long long)T[c].hi < 0;
+        U128 mag = T[c];
+        if (neg) {  // two's complement negation
+          mag.lo = ~T[c].lo + 1ull;
+          mag.hi = ~T[c].hi + (mag.lo == 0ull ? 1ull : 0ull);
+        }
+        float f = 0.f;
+        ok = round_mean(mag, cn, meta_E(flags, c), f);
+        out[c] = neg ? -f : f;
+      }
+      if (ok) {
+        const unsigned long long key = keys[(u + 1) * kSegTile - 1];
+        const int label = (int)(key & ((1ull << g.label_bits) - 1));
+        train[s] = make_float4(out[0], out[1], out[2], (float)(label + 32 * map_of_segment(key, kf, desc)));
+      }
+      done = ok ? 1 : 0;
     }
     done = __shfl_sync(0xffffffffu, done, 0);
     s = __shfl_sync(0xffffffffu, s, 0);

@@ -177,6 +177,27 @@ def test_centroids_exact_next_to_coordinate_planes(sb, orc):
     assert np.any((np.abs(gx[:, 1]) > 0) & (np.abs(gx[:, 1]) < np.finfo(np.float32).tiny))
 
 
+def test_cells_whose_sums_outgrow_64_bits(sb, orc):
+    """80000 hits inside one cell near the top of its sort tile, seen from the
+    origin: the hit cell and the free-sample cells along the nearly parallel
+    rays hold ~80000 members each, span dozens of segment tiles, and their
+    integer coordinate sums exceed 2^63; the centroids equal the oracle's."""
+    rng = np.random.default_rng(31)
+    n = 80000
+    pts = np.stack([9.951 + 0.045 * rng.random(n), 3.051 + 0.045 * rng.random(n), 1.051 + 0.045 * rng.random(n)],
+                   1).astype(np.float32)
+    lab = np.ones(n, np.int32)
+    prm = dict(res=0.1, length_scale=0.3, sigma0=1.0, alpha0=0.001, free_step=0.3, num_classes=3)
+    m = _gpu_map(sb, prm)
+    gx, gl = m.training_set(pts, lab, np.eye(4))
+    ox, ol, st = orc.training_set(orc.params(**prm), pts, lab, np.eye(4))
+    assert len(gx) == st["train"] and st["hits"] == n
+    gx, gl = _sorted_train(gx, gl)
+    ox, ol = _sorted_train(ox, ol)
+    np.testing.assert_array_equal(gl, ol)
+    np.testing.assert_array_equal(gx, ox)
+
+
 def test_centroid_of_a_cell_with_both_signs(sb, orc):
     """ds = 2: x fp32(1/ds) of -2^-149 rounds to -0, so that member shares cell 0
     with positive coordinates; the mean is exact over the signed members."""
