@@ -38,29 +38,52 @@ struct TouchArgs {
 
 __device__ __forceinline__ int floor_i(float v) { return (int)floorf(v); }
 
-__device__ void mark_touched(const TouchArgs& a, uint32_t slot) {
+// Marks the slot touched by this update; 1 for the call that marked it first.
+// kList: that call also appends the slot to the touched list (the block-major
+// form walks it; the point-major form only counts the touched blocks).  A plain
+// read skips the atomic when the mark is already there (a mark, once set in
+// this update, never changes back).
+template <bool kList>
+__device__ __forceinline__ uint32_t mark_touched(const TouchArgs& a, uint32_t slot) {
   const uint32_t epoch = a.dc->epoch;
-  if (atomicExch(&a.hmark[slot], epoch) != epoch) {
+  if (a.hmark[slot] == epoch) return 0u;
+  if (atomicExch(&a.hmark[slot], epoch) == epoch) return 0u;
+  if (kList) {
     const uint32_t t = atomicAdd(&a.dc->n_touched, 1u);
     a.touched[t] = slot;
   }
+  return 1u;
 }
 
-// returns the slot of key (inserted if new), or -1 when the probe bound is hit
-__device__ int64_t insert_block(const TouchArgs& a, unsigned long long key) {
+// returns the slot of key (inserted if new), or -1 when the probe bound is hit;
+// first += 1 when this call marked the block touched first.  A slot holds the
+// empty key or, for good, one block key, so a plain read that finds the key
+// needs no atomic.
+template <bool kList = true>
+__device__ int64_t insert_block(const TouchArgs& a, unsigned long long key, uint32_t* first = nullptr) {
   uint32_t slot = hash_slot(key, a.hash_cap);
   for (int probe = 0; probe < kMaxProbes; ++probe) {
-    const unsigned long long prev = atomicCAS(&a.hkeys[slot], kEmpty, key);
-    if (prev == kEmpty) {
-      const uint32_t i = atomicAdd(&a.dc->n_new, 1u);
-      a.fresh[i] = slot;
-      a.hvals[slot] = -1;
-      mark_touched(a, slot);
+    const unsigned long long cur = a.hkeys[slot];
+    if (cur == key) {
+      const uint32_t f = mark_touched<kList>(a, slot);
+      if (first) *first += f;
       return slot;
     }
-    if (prev == key) {
-      mark_touched(a, slot);
-      return slot;
+    if (cur == kEmpty) {
+      const unsigned long long prev = atomicCAS(&a.hkeys[slot], kEmpty, key);
+      if (prev == kEmpty) {
+        const uint32_t i = atomicAdd(&a.dc->n_new, 1u);
+        a.fresh[i] = slot;
+        a.hvals[slot] = -1;
+        const uint32_t f = mark_touched<kList>(a, slot);
+        if (first) *first += f;
+        return slot;
+      }
+      if (prev == key) {
+        const uint32_t f = mark_touched<kList>(a, slot);
+        if (first) *first += f;
+        return slot;
+      }
     }
     slot = (uint32_t)((slot + 1) & (uint32_t)(a.hash_cap - 1));
   }
@@ -164,6 +187,7 @@ __global__ void __launch_bounds__(256) touch_kernel(TouchArgs a) {
   const Geom& g = a.g;
   if (a.dc->err != 0) return;
   const uint32_t P = a.dc->n_train;
+  uint32_t nfirst = 0;  // blocks this thread marked touched first
   for (uint32_t base = blockIdx.x * blockDim.x; base < P; base += gridDim.x * blockDim.x) {  // warp-uniform
     const uint32_t i = base + threadIdx.x;
     const bool active = i < P;
@@ -189,9 +213,20 @@ __global__ void __launch_bounds__(256) touch_kernel(TouchArgs a) {
           hit ? pack_block(pb.blo[0] + kx, pb.blo[1] + ky, pb.blo[2] + kz, map) : kEmpty;
       const unsigned peers = __match_any_sync(0xffffffffu, key);
       if (hit && (unsigned)(__ffs(peers) - 1) == (threadIdx.x & 31u)) {
-        const int64_t slot = insert_block(a, key);
+        const int64_t slot = insert_block<kCount>(a, key, &nfirst);
         if (kCount && slot >= 0) atomicAdd(&a.hcnt[slot], (uint32_t)__popc(peers));
       }
+    }
+  }
+  if (!kCount) {  // the number of touched blocks: one addition per CTA
+    __shared__ uint32_t s_first[8];
+    const uint32_t w = __reduce_add_sync(0xffffffffu, nfirst);
+    if ((threadIdx.x & 31u) == 0) s_first[threadIdx.x >> 5] = w;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t t = 0;
+      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += s_first[k];
+      if (t) atomicAdd(&a.dc->n_touched, t);
     }
   }
 }
