@@ -590,7 +590,7 @@ struct SegState {           // sums of a run of members of one cell
 };
 constexpr uint32_t kSegBad = 2u;
 
-// Dynamic shared memory: the cells' sums and first items; the first part
+// Dynamic shared memory: the cells' sums and label words; the first part
 // doubles as the load stage (items, then keys, one pad entry per kSegPer so
 // that each thread's consecutive entries fall in distinct banks).
 __host__ __device__ constexpr int seg_pad(int i) { return i + i / kSegPer; }
@@ -716,10 +716,15 @@ __device__ __forceinline__ bool round_mean64(unsigned long long T, uint32_t n, i
   return true;
 }
 
-// Training point s from the complete sums of its cell (key: any member's key);
+// The label word of a training point (label + 32 map) from its cell's key
+__device__ __forceinline__ uint32_t label_word(unsigned long long key, const Geom& g, const KeyFrame& kf,
+                                               const ScanDesc* __restrict__ desc) {
+  return (uint32_t)(key & ((1ull << g.label_bits) - 1)) + 32u * (uint32_t)map_of_segment(key, kf, desc);
+}
+
+// Training point s from the complete sums of its cell (lw: its label word);
 // false, with nothing written, when this form cannot give the exact mean.
-__device__ __forceinline__ bool try_round_cell(const SegState& st, uint32_t s, unsigned long long key, const Geom& g,
-                                               const KeyFrame& kf, const ScanDesc* __restrict__ desc,
+__device__ __forceinline__ bool try_round_cell(const SegState& st, uint32_t s, uint32_t lw,
                                                float4* __restrict__ train) {
   bool ok = !(st.flags & kSegBad) && st.n < kSegMaxN;
   float out[3] = {0.f, 0.f, 0.f};
@@ -735,10 +740,7 @@ __device__ __forceinline__ bool try_round_cell(const SegState& st, uint32_t s, u
       }
     }
   }
-  if (ok) {
-    const int label = (int)(key & ((1ull << g.label_bits) - 1));
-    train[s] = make_float4(out[0], out[1], out[2], (float)(label + 32 * map_of_segment(key, kf, desc)));
-  }
+  if (ok) train[s] = make_float4(out[0], out[1], out[2], (float)lw);
   return ok;
 }
 
@@ -791,7 +793,7 @@ __global__ void __launch_bounds__(kSegThreads, 3) seg_reduce_kernel(
     DevCounters* dc) {
   extern __shared__ __align__(16) unsigned char seg_smem[];
   SegState* s_cell = reinterpret_cast<SegState*>(seg_smem);                   // by tile-local cell index
-  uint32_t* s_head = reinterpret_cast<uint32_t*>(seg_smem + kSegCellBytes);  // the cell's first item
+  uint32_t* s_head = reinterpret_cast<uint32_t*>(seg_smem + kSegCellBytes);  // the cell's label word
   float4* s_items = reinterpret_cast<float4*>(seg_smem + kSegStageItems);     // load stage (aliases s_cell)
   unsigned long long* s_keys = reinterpret_cast<unsigned long long*>(seg_smem + kSegStageKeys);
   __shared__ SegState s_open;  // the run that opens the tile, of a cell whose head lies in an earlier tile
@@ -888,7 +890,7 @@ __global__ void __launch_bounds__(kSegThreads, 3) seg_reduce_kernel(
       for (int k = 0; k < kSegPer; ++k)
         if (heads & (1u << k)) {
           seg_start[excl + j] = (uint32_t)(first + k);
-          s_head[j++] = (uint32_t)(first + k);
+          s_head[j++] = label_word(kk[k], g, kf, desc);
         }
       if (first <= n - 1 && n - 1 < first + kSegPer) {  // this thread holds the last item
         seg_start[excl + total] = (uint32_t)n;
@@ -939,7 +941,7 @@ __global__ void __launch_bounds__(kSegThreads, 3) seg_reduce_kernel(
     const bool cross_out = s_cross && total > 0u;
     const uint32_t nround = total - (cross_out ? 1u : 0u);
     for (uint32_t q = threadIdx.x; q < nround; q += kSegThreads)
-      if (!try_round_cell(s_cell[q], excl + q, keys[s_head[q]], g, kf, desc, train))
+      if (!try_round_cell(s_cell[q], excl + q, s_head[q], train))
         slow[atomicAdd(&dc->n_slow, 1u)] = excl + q;
     if (threadIdx.x == 0) {
       if (cross_out) {
