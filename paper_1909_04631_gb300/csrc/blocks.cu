@@ -206,8 +206,15 @@ __global__ void __launch_bounds__(256) touch_kernel(TouchArgs a) {
     const int my = __reduce_max_sync(0xffffffffu, (unsigned)pb.nb[1]);
     const int mz = __reduce_max_sync(0xffffffffu, (unsigned)pb.nb[2]);
     const int nc = mx * my * mz;
-    for (int c = 0; c < nc; ++c) {
-      const int kx = c % mx, ky = (c / mx) % my, kz = c / (mx * my);
+    int kx = 0, ky = 0, kz = 0;  // candidate c = kx + mx (ky + my kz), stepped without divisions
+    for (int c = 0; c < nc; ++c, ++kx) {
+      if (kx == mx) {
+        kx = 0;
+        if (++ky == my) {
+          ky = 0;
+          ++kz;
+        }
+      }
       const bool hit = kx < pb.nb[0] && ky < pb.nb[1] && kz < pb.nb[2] && touches(pb, kx, ky, kz, g);
       const unsigned long long key =
           hit ? pack_block(pb.blo[0] + kx, pb.blo[1] + ky, pb.blo[2] + kz, map) : kEmpty;
@@ -256,8 +263,15 @@ __global__ void __launch_bounds__(256) bin_fill_kernel(TouchArgs a) {
     const int my = __reduce_max_sync(0xffffffffu, (unsigned)pb.nb[1]);
     const int mz = __reduce_max_sync(0xffffffffu, (unsigned)pb.nb[2]);
     const int nc = mx * my * mz;
-    for (int c = 0; c < nc; ++c) {
-      const int kx = c % mx, ky = (c / mx) % my, kz = c / (mx * my);
+    int kx = 0, ky = 0, kz = 0;  // candidate c = kx + mx (ky + my kz), stepped without divisions
+    for (int c = 0; c < nc; ++c, ++kx) {
+      if (kx == mx) {
+        kx = 0;
+        if (++ky == my) {
+          ky = 0;
+          ++kz;
+        }
+      }
       const bool hit = kx < pb.nb[0] && ky < pb.nb[1] && kz < pb.nb[2] && touches(pb, kx, ky, kz, g);
       const unsigned long long key =
           hit ? pack_block(pb.blo[0] + kx, pb.blo[1] + ky, pb.blo[2] + kz, map) : kEmpty;
