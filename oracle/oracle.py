@@ -33,14 +33,16 @@ def build(force: bool = False) -> str:
 class OrcParams(C.Structure):
     _fields_ = [(n, C.c_double) for n in ("res", "length_scale", "sigma0", "alpha0", "free_step", "ds_res",
                                           "min_range", "max_range", "free_thresh", "occ_thresh")] + \
-               [("num_classes", C.c_int32), ("block_edge", C.c_int32)]
+               [("num_classes", C.c_int32), ("block_edge", C.c_int32), ("sensor_model", C.c_int32)]
 
 
 def params(res=0.1, length_scale=0.3, sigma0=0.1, alpha0=0.001, free_step=0.3, ds_res=None, min_range=0.0,
-           max_range=1e30, free_thresh=0.47, occ_thresh=0.6, num_classes=10, block_edge=8, **_ignored):
-    """Parameter block; defaults follow Table (parameters) and Sec. V-A of the paper."""
+           max_range=1e30, free_thresh=0.47, occ_thresh=0.6, num_classes=10, block_edge=8, sensor_model=0,
+           **_ignored):
+    """Parameter block; defaults follow Table (parameters) and Sec. V-A of the paper.
+    sensor_model 0: kernel inference, Eq. (alpha_kernel); 1: counting model, Eq. (alpha)."""
     return OrcParams(res, length_scale, sigma0, alpha0, free_step, res if ds_res is None else ds_res, min_range,
-                     max_range, free_thresh, occ_thresh, num_classes, block_edge)
+                     max_range, free_thresh, occ_thresh, num_classes, block_edge, sensor_model)
 
 
 _P = C.POINTER

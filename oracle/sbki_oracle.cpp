@@ -35,6 +35,10 @@
 //       evaluated as ((r0 px + r1 py) + r2 pz) + t; key = floorf(x * fp32(1/res)).
 //   K7  A voxel with no kernel mass reads as the prior with state "unknown";
 //       otherwise free if p_occ < free_thresh, occupied if p_occ > occ_thresh.
+//   K11 Counting model (S-CSM, Eq. (alpha), Sec. IV): the measurements it counts
+//       are the training points of steps a1..a3, each of weight 1 (as in K4),
+//       and "x_i in cell j" is the voxel key of K6.  Every counted point leaves
+//       one (voxel, point) pair, so the pair count of a voxel is its count.
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -51,6 +55,7 @@ struct Params {
       occ_thresh;
   int32_t num_classes;  // K occupied classes; alpha has K+1 entries
   int32_t block_edge;
+  int32_t sensor_model;  // 0: kernel inference, Eq. (alpha_kernel); 1: counting, Eq. (alpha)
 };
 
 const double kPi = 3.14159265358979323846;
@@ -322,6 +327,35 @@ void accumulate(Map& m, const std::vector<Sample>& train) {
   }
 }
 
+// Step a5 of the counting model, Eq. (alpha) with reading K11: every training
+// point adds 1 to alpha^{y_i} of the voxel that contains it.
+void accumulate_counts(Map& m, const std::vector<Sample>& train) {
+  const Params& p = m.p;
+  const int K1 = nclass(p);
+  const int64_t B = p.block_edge;
+  const float inv_res = (float)(1.0 / p.res);
+  for (const Sample& s : train) {
+    const int64_t vx = voxel_index(s.x, inv_res), vy = voxel_index(s.y, inv_res), vz = voxel_index(s.z, inv_res);
+    Key3 bk = {floor_div(vx, B), floor_div(vy, B), floor_div(vz, B)};
+    Block& blk = m.blocks[bk];
+    if (blk.inc.empty()) {
+      blk.inc.assign((size_t)(B * B * B * K1), 0.0);
+      blk.pairs.assign((size_t)(B * B * B), 0);
+    }
+    const int64_t li = ((vz - bk[2] * B) * B + (vy - bk[1] * B)) * B + (vx - bk[0] * B);
+    blk.inc[(size_t)(li * K1 + s.label)] += 1.0;
+    blk.pairs[(size_t)li] += 1;
+  }
+}
+
+// Step a5 of the map's sensor model.
+void update(Map& m, const std::vector<Sample>& train) {
+  if (m.p.sensor_model == 1)
+    accumulate_counts(m, train);
+  else
+    accumulate(m, train);
+}
+
 bool labels_ok(const Params& p, const int32_t* labels, int64_t n) {
   for (int64_t i = 0; i < n; ++i)
     if (labels[i] < 1 || labels[i] > p.num_classes) return false;
@@ -363,7 +397,7 @@ extern "C" {
 
 typedef struct {
   double res, length_scale, sigma0, alpha0, free_step, ds_res, min_range, max_range, free_thresh, occ_thresh;
-  int32_t num_classes, block_edge;
+  int32_t num_classes, block_edge, sensor_model;
 } orc_params;
 
 static Params conv(const orc_params* q) {
@@ -456,7 +490,7 @@ int orc_map_insert_training(void* h, const float* xyz, const int32_t* lab, int64
     if (lab[i] < 0 || lab[i] > m->p.num_classes) return -1;
     train[i] = {xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], lab[i]};
   }
-  accumulate(*m, train);
+  update(*m, train);
   return 0;
 }
 
@@ -467,7 +501,7 @@ int orc_map_insert_scan(void* h, const float* pts, const int32_t* labels, int64_
   if (!labels_ok(m->p, labels, n)) return -1;
   std::vector<Sample> train;
   training_set(m->p, pts, labels, n, T, train, stats);
-  accumulate(*m, train);
+  update(*m, train);
   return 0;
 }
 

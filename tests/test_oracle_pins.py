@@ -4,7 +4,8 @@ Every check here is independent of the oracle's own arithmetic: closed-form
 values of the sparse kernel (Eq. kernel), exact quadratures, brute-force
 all-pairs sums (Eq. alpha_kernel) written with numpy, Dirichlet moments from
 scipy (Eq. mode, Eq. variance), the binary counting/BKI special case
-(Sec. III), and finite differences of the oracle's own forward for its
+(Sec. III), counts fixed by construction for the counting model (Eq. alpha),
+and finite differences of the oracle's own forward for its
 analytic gradient.  None of them needs a GPU.
 """
 import json
@@ -301,6 +302,86 @@ def test_conservation_per_voxel(orc):
     a_one, _ = orc.alpha_bruteforce(orc.params(res=0.1, length_scale=0.3, sigma0=0.3, num_classes=1), xyz,
                                     np.zeros(60, np.int32), keys)
     np.testing.assert_allclose((alpha - p.alpha0).sum(1), a_one[:, 0] - p.alpha0, rtol=1e-12, atol=1e-15)
+
+
+# ---------------------------------------------------------------- a5 of the counting model (Eq. alpha)
+
+def test_counting_model_counts_by_construction(orc):
+    """Eq. (alpha): alpha_j^k = alpha0 + the number of training points of class k
+    inside cell j.  Points are placed well inside chosen voxels (the voxel is
+    known by construction, not computed), so every count is fixed in advance."""
+    rng = np.random.default_rng(23)
+    res = 0.1
+    cells = rng.integers(-12, 12, size=(25, 3))
+    cells[1] = cells[0]                                 # one voxel holds two groups
+    cells[2] = cells[0] + np.array([0, 0, 1])
+    which = rng.integers(0, len(cells), size=300)
+    u = rng.uniform(0.2, 0.8, size=(300, 3))
+    xyz = ((cells[which] + u) * res).astype(np.float32)
+    lab = rng.integers(0, 4, size=300).astype(np.int32)
+    expect = {}
+    for c, l in zip(map(tuple, cells[which]), lab):
+        expect.setdefault(c, np.zeros(4))[l] += 1.0
+    p = orc.params(res=res, length_scale=0.3, sigma0=0.1, num_classes=3, sensor_model=1)
+    m = orc.OracleMap(p)
+    m.insert_training(xyz, lab)
+    keys, alpha, pairs = m.export()
+    got = {tuple(k): (a, n) for k, a, n in zip(keys, alpha, pairs)}
+    for c, cnt in expect.items():
+        np.testing.assert_array_equal(got[c][0], p.alpha0 + cnt)   # integer counts: exact in FP64
+        assert got[c][1] == cnt.sum()
+    rest = [k for k in got if k not in expect]
+    assert all(np.all(got[k][0] == p.alpha0) and got[k][1] == 0 for k in rest)
+    # allocated blocks: exactly the 8^3 blocks that hold a point (Python floor division)
+    blocks = {tuple(np.asarray(c) // 8) for c in expect}
+    assert set(map(tuple, m.block_keys())) == blocks
+    # the kernel parameters do not enter the counting model
+    m2 = orc.OracleMap(orc.params(res=res, length_scale=0.17, sigma0=5.0, num_classes=3, sensor_model=1))
+    m2.insert_training(xyz, lab)
+    np.testing.assert_array_equal(m2.export()[1], alpha)
+
+
+def test_counting_model_reverts_to_binary_counting_sensor(orc):
+    """With K = 1 the counting model is the binary counting sensor model (Sec. IV):
+    along one beam every free sample adds a miss to its voxel and the hit adds a
+    hit, so E[theta^occ] = (alpha0 + hits) / (2 alpha0 + hits + misses)."""
+    a0 = 0.001
+    p = orc.params(res=0.1, free_step=0.3, alpha0=a0, num_classes=1, sensor_model=1)
+    T = np.eye(4)
+    T[:3, 3] = [0.02, 0.05, 0.05]
+    m = orc.OracleMap(p)
+    st = m.insert_scan(np.array([[1.0, 0.0, 0.0]], np.float32), np.array([1], np.int32), T)
+    assert st == dict(hits=1, free=3, train=4)          # samples at t = 0.7, 0.4, 0.1 (reading K3)
+    q = np.array([[1.02, 0.05, 0.05], [0.72, 0.05, 0.05], [0.42, 0.05, 0.05], [0.12, 0.05, 0.05],
+                  [0.55, 0.05, 0.05], [1.02, 0.15, 0.05]], np.float32)
+    r = m.query(q)
+    occ = (a0 + 1.0) / (2 * a0 + 1.0)
+    free = a0 / (2 * a0 + 1.0)
+    np.testing.assert_allclose(r["p_occ"], [occ, free, free, free, 0.5, 0.5], rtol=1e-14)
+    np.testing.assert_array_equal(r["state"], [2, 0, 0, 0, 1, 1])
+    # a second scan from the same pose doubles every count
+    m.insert_scan(np.array([[1.0, 0.0, 0.0]], np.float32), np.array([1], np.int32), T)
+    a, n = m.alpha_at(np.array([[10, 0, 0], [7, 0, 0]]))
+    np.testing.assert_array_equal(a, a0 + np.array([[0.0, 2.0], [2.0, 0.0]]))
+    np.testing.assert_array_equal(n, [2, 2])
+
+
+def test_counting_model_mass_equals_training_points(orc):
+    """Each training point is counted exactly once: the increments of a whole
+    scan sum to the number of training points, per class and in total."""
+    sc = scenes.small_region_scan(0, n_az=40, n_el=30)
+    prm = dict(scenes.SMALL_SCENE_PARAMS, sensor_model=1)
+    p = orc.params(**prm)
+    xyz, lab, st = orc.training_set(p, sc["points"], sc["labels"], sc["pose"])
+    m = orc.OracleMap(p)
+    assert m.insert_scan(sc["points"], sc["labels"], sc["pose"]) == st
+    keys, alpha, pairs = m.export()
+    K1 = p.num_classes + 1
+    counts = np.rint(alpha - p.alpha0)
+    np.testing.assert_allclose(alpha - p.alpha0, counts, rtol=0, atol=1e-9)   # whole counts
+    np.testing.assert_array_equal(counts.sum(0), np.bincount(lab, minlength=K1))
+    assert pairs.sum() == len(xyz)
+    np.testing.assert_array_equal(counts.sum(1), pairs)
 
 
 # ---------------------------------------------------------------- read-off (Eq. mode, Eq. variance)
