@@ -391,6 +391,44 @@ def run_reference(args, rank, world):
     return 0
 
 
+def counting_model(sb, torch, stream, p, dpts, dlab, poses, warmup, steps):
+    """The street sequence through the counting sensor model (Eq. alpha): the
+    same ingest, then one count per training point in the voxel holding it.
+    Device inputs, CUDA events; stage times from the library's own events."""
+    nscan = len(dpts)
+    with sb.Map(p, stream=stream, sensor_model=1) as m:
+        for i in range(warmup):
+            m.insert_scan(dpts[i % nscan], dlab[i % nscan], poses[i % nscan])
+        m.profile(True, reset=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stats = []
+        e0.record(stream)
+        for i in range(steps):
+            j = (warmup + i) % nscan
+            stats.append(m.insert_scan(dpts[j], dlab[j], poses[j]))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        prof = m.profile_read()
+    n = max(1, prof["inserts"])
+    K1 = scenes.STREET_PARAMS["num_classes"] + 1
+    train = sum(s["train_points"] for s in stats) / steps
+    newb = sum(s["new_blocks"] for s in stats) / steps
+    # algorithmic bytes of the count step per scan: the training point (16 B), its
+    # hash slot (key + pool index, 12 B) and the read-modify-write of one alpha
+    # word (8 B) per point, and the zero fill of the blocks created by the scan
+    acc_s = prof["accumulate_ms"] / 1e3 / n
+    bytes_alg = 36.0 * train + 4.0 * K1 * 512 * newb
+    bw, _, src = peaks()
+    return {"workload": "LiDAR street 64x2048 sequence, counting sensor model (Eq. alpha), 0.1 m voxels",
+            "scans": steps, "ms_per_scan": ms, "scans_per_s": 1e3 / ms, "train_points_per_scan": train,
+            "stage_ms": {"ingest": prof["ingest_ms"] / n, "blocks": prof["blocks_ms"] / n,
+                         "count": prof["accumulate_ms"] / n},
+            "count_step": {"bytes_alg": bytes_alg, "achieved_gbs": bytes_alg / acc_s / 1e9, "peak_gbs": bw,
+                           "frac": bytes_alg / acc_s / 1e9 / bw, "peak_source": "hbm_gbs of %s peaks" % src}}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_1909_04631_gb300 as sb
@@ -548,6 +586,7 @@ def run_ours(args, rank, world, local_rank):
         line["batched"] = batched_form(sb, torch, dev, stream, forms_input[0], reps=5)
         line["differentiable"] = differentiable_form(sb, torch, dev, stream, forms_input[1], reps=3)
         line["other_workloads"] = other_workloads(sb, torch, dev, stream, forms_input[2], forms_input[3])
+        line["counting_model"] = counting_model(sb, torch, stream, p, dpts, dlab, poses, args.warmup, args.steps)
     print(json.dumps(line), flush=True)
     return 0
 

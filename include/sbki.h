@@ -10,7 +10,9 @@
  * k(x_*, x_i) y_i into every voxel centre x_* within the support l of a
  * training point x_i, with the sparse kernel of Eq. (kernel); the update is
  * recursive over scans (Sec. IV).  Read-off follows Eq. (mode), Eq. (variance)
- * and the occupancy rule of Sec. V-C.
+ * and the occupancy rule of Sec. V-C.  A map can instead run the paper's
+ * counting sensor model (S-CSM, Eq. (alpha); params.sensor_model = 1): the
+ * same training points, each adding 1 to class y of the voxel containing it.
  *
  * Conventions shared by every entry point
  *  - Buffers are owned by the caller.  Pointer arguments may be host or device
@@ -70,6 +72,11 @@ typedef struct sbki_params {
                         * they share the block pool; see sbki_select_map and
                         * sbki_insert_batch */
   void* cuda_stream;   /* cudaStream_t for every launch and copy; NULL = legacy default stream */
+  int32_t sensor_model; /* 0: kernel inference, Eq. (alpha_kernel) (default); 1: counting sensor
+                         * model, Eq. (alpha): every training point adds 1 to alpha^{y_i} of the
+                         * voxel floor(x * fp32(1/res)) that contains it (exact FP32 counts below
+                         * 2^24 per voxel and class); length_scale and sigma0 do not enter it.
+                         * Needs accumulate_mode 0; sbki_backward and sbki_grad refuse it */
 } sbki_params;
 
 /* Per-insert counters (all for the last insert). */
@@ -78,9 +85,10 @@ typedef struct sbki_stats {
   int64_t dropped;        /* input points dropped */
   int64_t free_samples;   /* free-space samples generated (Sec. III) */
   int64_t train_points;   /* training points after downsampling */
-  int64_t touched_blocks; /* blocks with at least one in-support pair */
+  int64_t touched_blocks; /* blocks with at least one in-support pair (counting model: holding a point) */
   int64_t new_blocks;     /* blocks allocated by this insert */
-  int64_t pairs;          /* in-support (voxel, training point) pairs, Eq. (alpha_kernel) */
+  int64_t pairs;          /* in-support (voxel, training point) pairs, Eq. (alpha_kernel); counting
+                           * model: training points counted (one voxel each) */
   int64_t touched_voxels; /* voxels whose alpha changed (block-major mode only; 0 otherwise) */
   int64_t total_blocks;   /* blocks allocated in the map after the insert */
 } sbki_stats;
@@ -102,7 +110,8 @@ void sbki_destroy_map(sbki_map* map);
  * counted, not an error.  Free samples lie at distance r - j*free_step from
  * the sensor origin for j >= 1 while positive.  Hits and free samples are
  * grouped per (downsampling cell, label) into centroids, and every centroid
- * adds sigma0 * f(d/l) into class y of every voxel centre with d < l.
+ * adds sigma0 * f(d/l) into class y of every voxel centre with d < l (the
+ * counting model: 1 into class y of its own voxel, Eq. (alpha)).
  * Synchronises the stream before returning (stats may be NULL). */
 sbki_status sbki_insert_scan(sbki_map* map, const float* points, const int32_t* labels, int64_t n,
                              const double sensor_pose[16], sbki_stats* stats);
@@ -280,7 +289,8 @@ sbki_status sbki_grad_add_alpha(sbki_map* map, const int64_t* keys, const float*
  *   grad_xyz[i] = sum_v G sigma0 f'(r) (x_i - c_v)/(l d)   ([p,3], nullable,
  *   host or device; 0 where d = 0).
  * grad_l and grad_sigma0 (host, nullable) are summed in FP64 from FP32 pair
- * terms. */
+ * terms.  A counting-model map (piecewise constant in x, no l or sigma0)
+ * returns SBKI_ERR_INVALID_ARG. */
 sbki_status sbki_backward(sbki_map* map, const float* xyzl, int64_t p, double* grad_l, double* grad_sigma0,
                           float* grad_xyz);
 

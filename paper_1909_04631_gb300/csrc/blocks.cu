@@ -176,6 +176,20 @@ __device__ bool touches(const PointBlocks& pb, int kx, int ky, int kz, const Geo
   return s < g.l2_64;
 }
 
+// The number of blocks a CTA's threads marked touched first, added with one
+// atomic per CTA (every thread of the CTA calls it, outside divergent code).
+__device__ __forceinline__ void add_touched(uint32_t nfirst, DevCounters* dc) {
+  __shared__ uint32_t s_first[8];
+  const uint32_t w = __reduce_add_sync(0xffffffffu, nfirst);
+  if ((threadIdx.x & 31u) == 0) s_first[threadIdx.x >> 5] = w;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t t = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += s_first[k];
+    if (t) atomicAdd(&dc->n_touched, t);
+  }
+}
+
 // Every lane walks the same cube of candidate blocks around the block of its
 // point (warp-uniform trip count, at most 3x3x3), so the warp-wide match that
 // lets one lane insert a block reached by several lanes always sees all 32
@@ -225,17 +239,30 @@ __global__ void __launch_bounds__(256) touch_kernel(TouchArgs a) {
       }
     }
   }
-  if (!kCount) {  // the number of touched blocks: one addition per CTA
-    __shared__ uint32_t s_first[8];
-    const uint32_t w = __reduce_add_sync(0xffffffffu, nfirst);
-    if ((threadIdx.x & 31u) == 0) s_first[threadIdx.x >> 5] = w;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      uint32_t t = 0;
-      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += s_first[k];
-      if (t) atomicAdd(&a.dc->n_touched, t);
+  if (!kCount) add_touched(nfirst, a.dc);
+}
+
+// Counting model, Eq. (alpha): the block of the voxel that holds each training
+// point (the voxel key floor(x fp32(1/res)) of the read-off).  Consecutive
+// training points mostly share a block, so a warp-wide match lets one lane
+// per distinct block insert it.
+__global__ void __launch_bounds__(256) touch_cells_kernel(TouchArgs a) {
+  const Geom& g = a.g;
+  if (a.dc->err != 0) return;
+  const uint32_t P = a.dc->n_train;
+  uint32_t nfirst = 0;
+  for (uint32_t base = blockIdx.x * blockDim.x; base < P; base += gridDim.x * blockDim.x) {  // warp-uniform
+    const uint32_t i = base + threadIdx.x;
+    unsigned long long key = kEmpty;
+    if (i < P) {
+      const float4 p = a.train[i];
+      key = pack_block(floor_i(__fmul_rn(p.x, g.inv_res)) >> g.B_shift, floor_i(__fmul_rn(p.y, g.inv_res)) >> g.B_shift,
+                       floor_i(__fmul_rn(p.z, g.inv_res)) >> g.B_shift, (int)p.w >> kLabelBits);
     }
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    if (key != kEmpty && (unsigned)(__ffs(peers) - 1) == (threadIdx.x & 31u)) insert_block<false>(a, key, &nfirst);
   }
+  add_touched(nfirst, a.dc);
 }
 
 // Same walk as touch_kernel: every (point, touched block) pair takes the next
@@ -392,9 +419,7 @@ __global__ void __launch_bounds__(256) import_alpha_kernel(Geom g, const unsigne
   }
 }
 
-}  // namespace
-
-cudaError_t launch_touch_blocks(MapState& m, const KeyFrame& /*kf*/, int64_t bound) {
+TouchArgs touch_args(MapState& m) {
   TouchArgs a;
   a.g = m.g;
   a.train = m.s.train;
@@ -408,6 +433,22 @@ cudaError_t launch_touch_blocks(MapState& m, const KeyFrame& /*kf*/, int64_t bou
   a.hcur = m.hcur;
   a.blist = m.blist;
   a.dc = m.dc;
+  return a;
+}
+
+}  // namespace
+
+cudaError_t launch_touch_cells(MapState& m, int64_t bound) {
+  const TouchArgs a = touch_args(m);
+  const int64_t blocks =
+      std::max<int64_t>(1, std::min<int64_t>((bound + 255) / 256, (int64_t)m.sm_count * m.tune.touch_ctas_per_sm));
+  touch_cells_kernel<<<(unsigned)blocks, 256, 0, m.stream>>>(a);
+  m.launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_touch_blocks(MapState& m, const KeyFrame& /*kf*/, int64_t bound) {
+  const TouchArgs a = touch_args(m);
   // bound: the training points never exceed the items of the update
   const int64_t blocks =
       std::max<int64_t>(1, std::min<int64_t>((bound + 255) / 256, (int64_t)m.sm_count * m.tune.touch_ctas_per_sm));
@@ -419,19 +460,7 @@ cudaError_t launch_touch_blocks(MapState& m, const KeyFrame& /*kf*/, int64_t bou
 
 // After commit: per touched block the list of training points that touch it.
 cudaError_t launch_bin_points(MapState& m, int64_t bound) {
-  TouchArgs a;
-  a.g = m.g;
-  a.train = m.s.train;
-  a.hkeys = m.hkeys;
-  a.hvals = m.hvals;
-  a.hmark = m.hmark;
-  a.hash_cap = m.hash_cap;
-  a.touched = m.s.touched;
-  a.fresh = m.s.fresh;
-  a.hcnt = m.hcnt;
-  a.hcur = m.hcur;
-  a.blist = m.blist;
-  a.dc = m.dc;
+  const TouchArgs a = touch_args(m);
   // touched blocks never exceed 27 per training point nor the hash size
   const int64_t tb = std::min<int64_t>(m.hash_cap, 27 * std::max<int64_t>(bound, 1));
   bin_counts_kernel<<<(unsigned)std::min<int64_t>((tb + 255) / 256, 4096), 256, 0, m.stream>>>(
@@ -447,19 +476,8 @@ cudaError_t launch_bin_points(MapState& m, int64_t bound) {
 }
 
 cudaError_t launch_import(MapState& m, const int64_t* keys, const float* alpha, int64_t count) {
-  TouchArgs a;
-  a.g = m.g;
+  TouchArgs a = touch_args(m);
   a.train = nullptr;
-  a.hkeys = m.hkeys;
-  a.hvals = m.hvals;
-  a.hmark = m.hmark;
-  a.hash_cap = m.hash_cap;
-  a.touched = m.s.touched;
-  a.fresh = m.s.fresh;
-  a.hcnt = m.hcnt;
-  a.hcur = m.hcur;
-  a.blist = m.blist;
-  a.dc = m.dc;
   const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((count + 255) / 256, (int64_t)m.sm_count * 8));
   import_blocks_kernel<<<blocks, 256, 0, m.stream>>>(a, keys, count, m.active_map);
   cudaError_t e = launch_commit_blocks(m);

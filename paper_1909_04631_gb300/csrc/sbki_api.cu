@@ -160,6 +160,10 @@ sbki_status check_params(const sbki_params* p) {
     return fail(nullptr, SBKI_ERR_INVALID_ARG, "num_maps must be in 1..%d", kMaxMaps);
   if (p->accumulate_mode != 0 && p->accumulate_mode != 1)
     return fail(nullptr, SBKI_ERR_INVALID_ARG, "accumulate_mode must be 0 (point-major) or 1 (block-major)");
+  if (p->sensor_model != 0 && p->sensor_model != 1)
+    return fail(nullptr, SBKI_ERR_INVALID_ARG, "sensor_model must be 0 (kernel inference) or 1 (counting)");
+  if (p->sensor_model == 1 && p->accumulate_mode != 0)
+    return fail(nullptr, SBKI_ERR_INVALID_ARG, "the counting sensor model needs accumulate_mode 0");
   if (p->sample_capacity < 1 || p->sample_capacity > (1ll << 27))
     return fail(nullptr, SBKI_ERR_INVALID_ARG, "sample_capacity must be in 1..2^27");
   // tiles of training points overlapping one dilated block must stay few
@@ -369,6 +373,14 @@ sbki_status run_ingest(MapState& m, const float* points, const int32_t* labels, 
 
 sbki_status run_update(MapState& m, const KeyFrame& kf, int64_t bound) {
   if (m.profiling) CK(&m, cudaEventRecord(m.ev[1], m.stream));
+  if (m.prm.sensor_model == 1) {  // counting model, Eq. (alpha): the block of each point's voxel
+    CK(&m, launch_touch_cells(m, bound));
+    CK(&m, launch_commit_blocks(m));
+    if (m.profiling) CK(&m, cudaEventRecord(m.ev[2], m.stream));
+    CK(&m, launch_accumulate_counts(m, bound));
+    if (m.profiling) CK(&m, cudaEventRecord(m.ev[3], m.stream));
+    return SBKI_OK;
+  }
   CK(&m, launch_touch_blocks(m, kf, bound));
   CK(&m, launch_commit_blocks(m));
   if (m.acc_mode == 1) CK(&m, launch_bin_points(m, bound));
@@ -466,6 +478,7 @@ sbki_status sbki_default_params(sbki_params* p) {
   p->accumulate_mode = 0;
   p->num_maps = 1;
   p->cuda_stream = nullptr;
+  p->sensor_model = 0;
   return SBKI_OK;
 }
 
@@ -1136,6 +1149,8 @@ sbki_status sbki_backward(sbki_map* map, const float* xyzl, int64_t p, double* g
   if (!map) return fail(nullptr, SBKI_ERR_INVALID_ARG, "map is NULL");
   MapState& m = map->st;
   if (p < 0 || (p > 0 && !xyzl)) return fail(&m, SBKI_ERR_INVALID_ARG, "bad arguments");
+  if (m.prm.sensor_model != 0)
+    return fail(&m, SBKI_ERR_INVALID_ARG, "the counting sensor model has no kernel to differentiate");
   DeviceGuard dg(m.device);
   sbki_status st = ensure_grad(m);
   if (st != SBKI_OK) return st;

@@ -301,6 +301,7 @@ cudaError_t launch_train_prepare(MapState& m, const float4* in, int64_t p, const
 
 // blocks.cu
 cudaError_t launch_touch_blocks(MapState& m, const KeyFrame& kf, int64_t bound);
+cudaError_t launch_touch_cells(MapState& m, int64_t bound);  // counting model: the block of each point's voxel
 cudaError_t launch_commit_blocks(MapState& m);
 // blocks of the given voxel keys (selected map), commit, zero-fill, then alpha - alpha0 at the keys
 cudaError_t launch_import(MapState& m, const int64_t* keys, const float* alpha, int64_t count);
@@ -309,6 +310,7 @@ cudaError_t launch_bin_points(MapState& m, int64_t bound);
 // accumulate.cu
 cudaError_t launch_accumulate(MapState& m, const KeyFrame& kf);
 cudaError_t launch_accumulate_points(MapState& m);
+cudaError_t launch_accumulate_counts(MapState& m, int64_t bound);  // counting model, Eq. (alpha)
 cudaError_t launch_fresh_fill(MapState& m);  // zero the blocks created by this update
 cudaError_t build_candidate_tables(MapState& m);
 // backward.cu: held-out log-likelihood (+ dLL/dalpha into grad), upstream gradient at voxel keys,

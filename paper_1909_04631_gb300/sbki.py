@@ -40,7 +40,7 @@ class Params(C.Structure):
                [("num_classes", C.c_int32), ("block_edge", C.c_int32), ("pool_blocks", C.c_int64),
                 ("sample_capacity", C.c_int64), ("track_pairs", C.c_int32), ("device", C.c_int32),
                 ("accumulate_mode", C.c_int32), ("num_maps", C.c_int32),
-                ("cuda_stream", C.c_void_p)]
+                ("cuda_stream", C.c_void_p), ("sensor_model", C.c_int32)]
 
 
 class Scan(C.Structure):
