@@ -19,7 +19,7 @@ import os
 
 from . import sbki as _sb
 
-DEFAULT_CANDIDATES = dict(accumulate_ctas_per_sm=(0, 2, 3), accumulate_chunk=(1, 4, 8, 16),
+DEFAULT_CANDIDATES = dict(accumulate_ctas_per_sm=(0, 2, 3), accumulate_chunk=(4, 10, 20, 30),
                           touch_ctas_per_sm=(4, 8), ingest_ctas_per_sm=(8, 16))
 
 

@@ -58,21 +58,26 @@ struct PtArgs {
   int R;                 // offsets per axis span [-R, R]
   uint32_t recip_na;     // small_recip(2R + 1)
   int chunk;             // consecutive training points per warp (fast set-up form)
+  int32_t sink;          // spare pool block that absent neighbour blocks point at
   DevCounters* dc;
 };
 
 struct WarpTables {
   float2 x[kAxisMax + 1];  // (e_x^2, address part as int bits); entry 2R+1 is the padding row
   float2 yz[kYZMax];
-  float* blk[27];          // alpha + (pool * (K+1) + y_i) * B^3, or null
+  float* blk[27];          // alpha + (pool * (K+1) + y_i) * B^3 (pool = the spare block when absent)
   int32_t* cnt[27];        // pair counts of the block (tracking only)
 };
 
 // One candidate per lane, branch-free except for the (rare, warp-uniform)
 // FP64 re-decision: every lane evaluates the kernel and the reduction is
 // predicated.  Every list entry (padding included) yields a block digit in
-// 0..26, so the block-pointer load is always in range.  Returns 1 for an
-// in-support pair.
+// 0..26, so the block-pointer load is always in range.  A neighbour block
+// that is not in the map holds no voxel within l of any training point of
+// this update (the touched-block pass applies the same membership test and
+// allocated every block that does), so no in-support pair reaches it; its
+// pointer names the spare block after the pool, so the reduction needs no
+// null test.  Returns 1 for an in-support pair.
 template <bool kTrack>
 __device__ __forceinline__ uint32_t candidate(const PtArgs& a, const WarpTables& t, uint32_t ent, const int v0[3],
                                               const float4& p) {
@@ -92,10 +97,9 @@ __device__ __forceinline__ uint32_t candidate(const PtArgs& a, const WarpTables&
   const float d = d2 * rsqrtf(fmaxf(d2, 1e-30f));
   const float u = fmaxf(__fmaf_rn(-d, g.inv_l, 1.0f), 0.0f);
   const float w = u * u;
-  const bool hit = in && base != nullptr;
-  red_add_if(hit, base + (pk >> 8), g.sigma0 * (w * w * u * kernel_q(w)));
-  if (kTrack) red_add_if(hit, t.cnt[pk & 0xff] + (pk >> 8), 1);
-  return hit ? 1u : 0u;
+  red_add_if(in, base + (pk >> 8), g.sigma0 * (w * w * u * kernel_q(w)));
+  if (kTrack) red_add_if(in, t.cnt[pk & 0xff] + (pk >> 8), 1);
+  return in ? 1u : 0u;
 }
 
 // kNit > 0: lists of exactly kNit x 32 entries, unrolled; 0: any length
@@ -147,8 +151,8 @@ __global__ void __launch_bounds__(kThreads, 4) accumulate_points_kernel(PtArgs a
     // blocks the ball can reach: digit (bx, by, bz) in base 3
     if (lane < 27) {
       const int32_t pool = digit_pool(f, lane, map, a.hkeys, a.hvals, a.hash_cap);
-      t.blk[lane] = pool >= 0 ? a.alpha + ((size_t)pool * g.K1 + label) * g.B3 : nullptr;
-      if (kTrack) t.cnt[lane] = pool >= 0 ? a.pairs + (size_t)pool * g.B3 : nullptr;
+      t.blk[lane] = a.alpha + ((size_t)(pool >= 0 ? pool : a.sink) * g.K1 + label) * g.B3;
+      if (kTrack) t.cnt[lane] = a.pairs + (size_t)(pool >= 0 ? pool : a.sink) * g.B3;
     }
     __syncwarp();
     if (kNit > 0) {
@@ -168,94 +172,152 @@ __global__ void __launch_bounds__(kThreads, 4) accumulate_points_kernel(PtArgs a
 }
 
 // The same update with a cheaper per-point set-up, for 2R + 1 <= 8 (l up to
-// about 3 voxels): lanes 0-7, 8-15 and 16-23 each take one axis, form that
-// axis's compensated offsets and address parts for offsets -R..R themselves,
-// and hand the sub-voxel part and block of each axis to the warp by shuffles;
-// Y and Z rows combine into YZ rows by shuffles.  A warp takes kChunk
-// consecutive training points (sorted by tile, so mostly one block) and keeps
-// the pool slots of the 27 blocks around the last point's block, looking them
-// up again only when the block (or map) changes.
+// about 3 voxels).  A warp takes kChunk consecutive training points (sorted by
+// tile, so mostly one block) in groups of up to kGroup.  For a group, three
+// lanes per point (one per axis) form that axis's compensated offsets and
+// address parts for offsets -R..R at once, into per-point rows in shared
+// memory, with the point's sub-voxel part, block and voxel.  Then, point by
+// point, the warp combines the Y and Z rows into YZ rows, refreshes the pool
+// slots of the 27 blocks around the point's block when the block (or map)
+// changed, and sweeps the candidate list with the point's own X rows.
+constexpr int kGroup = 10;  // points whose rows one warp forms at once (3 lanes each)
+constexpr int kFastAxis = 8;  // rows per axis: 2R + 1 <= 7 offsets and the padding row
+
+struct alignas(16) PointRows {
+  float2 r[3][kFastAxis];  // per axis: (e^2, address part) of offset j - R; r[0][2R + 1] is the padding row
+  int pt[4];               // sub-voxel part per axis, label word
+  int blk[4];              // block per axis
+  int v0[4];               // voxel per axis
+};
+
+struct FastTables {
+  PointRows pts[kGroup];
+  float2 yz[kFastAxis * kFastAxis];  // YZ rows of the point being swept
+  float* blk[27];
+  int32_t* cnt[27];
+};
+
+// As candidate(), with the X rows of one point of the group; the point's
+// coordinates are loaded again only on the (rare) FP64 re-decision.
+template <bool kTrack>
+__device__ __forceinline__ uint32_t candidate_rows(const PtArgs& a, const FastTables& t, const PointRows& pr,
+                                                   uint32_t ent, uint32_t i) {
+  const Geom& g = a.g;
+  const float2 ex = *reinterpret_cast<const float2*>(reinterpret_cast<const char*>(pr.r[0]) + (ent & 0xffu));
+  const float2 eyz = *reinterpret_cast<const float2*>(reinterpret_cast<const char*>(t.yz) + ((ent >> 8) & 0x7ffu));
+  const float d2 = __fadd_rn(ex.x, eyz.x);
+  const int pk = __float_as_int(ex.y) + __float_as_int(eyz.y);
+  bool in = d2 < g.l2_lo;
+  const bool band = !in && d2 < g.l2_hi;
+  if (__any_sync(0xffffffffu, band)) {
+    if (band) {
+      const float4 p = a.train[i];
+      in = in_support64_call(pr.v0[0] + (int)((ent & 0xffu) >> 3) - a.R, pr.v0[1] + (int)((ent >> 19) & 15u) - a.R,
+                             pr.v0[2] + (int)((ent >> 23) & 15u) - a.R, p.x, p.y, p.z, g.res64, g.l2_64);
+    }
+  }
+  float* base = t.blk[pk & 0xff];
+  const float d = d2 * rsqrtf(fmaxf(d2, 1e-30f));
+  const float u = fmaxf(__fmaf_rn(-d, g.inv_l, 1.0f), 0.0f);
+  const float w = u * u;
+  red_add_if(in, base + (pk >> 8), g.sigma0 * (w * w * u * kernel_q(w)));
+  if (kTrack) red_add_if(in, t.cnt[pk & 0xff] + (pk >> 8), 1);
+  return in ? 1u : 0u;
+}
 
 template <bool kTrack, int kNit>
 __global__ void __launch_bounds__(kThreads, 4) accumulate_points_fast_kernel(PtArgs a) {
-  __shared__ WarpTables s_tab[kWarps];
+  __shared__ FastTables s_tab[kWarps];
   const Geom& g = a.g;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   const int R = a.R, na = 2 * R + 1, m = g.B - 1;
-  WarpTables& t = s_tab[wid];
+  FastTables& t = s_tab[wid];
   uint32_t npairs = 0;
   if (a.dc->err != 0) return;
   const uint32_t P = a.dc->n_train;
-  if (lane == 0) t.x[na] = make_float2(kFar, __int_as_float(0));
-  const int ax = min(lane >> 3, 2), j = lane & 7;  // this lane's axis and offset index
+  // this lane's point of a group and axis (lanes 30, 31 form no rows)
+  const int gl = lane / 3, ax = lane - 3 * (lane / 3);
   const int axshift = ax == 0 ? 0 : (ax == 1 ? g.B_shift : 2 * g.B_shift);
   const int dmul = ax == 0 ? 1 : (ax == 1 ? 3 : 9);
   int cb[3] = {INT_MIN, INT_MIN, INT_MIN}, cmap = -1;  // block and map the cached slots belong to
   int32_t pool = -1;                                   // lanes 0..26: slot of block digit `lane`
   const uint32_t chunk = (uint32_t)a.chunk;
   for (uint32_t c = gw; c * chunk < P; c += nw) {
-    for (uint32_t k = 0; k < chunk; ++k) {
-      const uint32_t i = c * chunk + k;
-      if (i >= P) break;  // warp-uniform
-      const float4 p = a.train[i];
-      const int lm = label_of(p.w);
-      const int label = lm & ((1 << kLabelBits) - 1), map = lm >> kLabelBits;
-      // this lane's axis
-      const float xa = ax == 0 ? p.x : (ax == 1 ? p.y : p.z);
-      const int v0 = floor_small(__fmul_rn(xa, g.inv_res));
-      float hi, lo;
-      centre_offset0(v0, xa, g, hi, lo);
-      const float phi = 0.5f - __fmul_rn(__fadd_rn(hi, lo), g.inv_res);
-      const int pt = min(kParts - 1, max(0, floor_small(phi * (float)kParts)));
-      const int b0 = v0 >> g.B_shift;
-      const float e = centre_offset_at(j - R, hi, lo, g);
-      const int v = v0 + j - R;
-      const float sq = __fmul_rn(e, e);
-      const int pk = dmul * ((v >> g.B_shift) - (b0 - 1)) | ((v & m) << (axshift + 8));
-      if (lane < 8 && j < na) t.x[j] = make_float2(sq, __int_as_float(pk));
-      const int part = __shfl_sync(0xffffffffu, pt, 0) +
-                       kParts * (__shfl_sync(0xffffffffu, pt, 8) + kParts * __shfl_sync(0xffffffffu, pt, 16));
-      const int bx = __shfl_sync(0xffffffffu, b0, 0), by = __shfl_sync(0xffffffffu, b0, 8),
-                bz = __shfl_sync(0xffffffffu, b0, 16);
-      const int v0s[3] = {__shfl_sync(0xffffffffu, v0, 0), __shfl_sync(0xffffffffu, v0, 8),
-                          __shfl_sync(0xffffffffu, v0, 16)};
-      for (int q0 = 0; q0 < na * na; q0 += 32) {  // uniform trip count: full-warp shuffles
-        const int q = min(q0 + lane, na * na - 1);
-        const int jy = (int)small_div((uint32_t)q, a.recip_na), jz = q - jy * na;
-        const float sy = __shfl_sync(0xffffffffu, sq, 8 + jy), sz = __shfl_sync(0xffffffffu, sq, 16 + jz);
-        const int py = __shfl_sync(0xffffffffu, pk, 8 + jy), pz = __shfl_sync(0xffffffffu, pk, 16 + jz);
-        if (q0 + lane < na * na) t.yz[q] = make_float2(__fadd_rn(sy, sz), __int_as_float(py + pz));
-      }
-      if (bx != cb[0] || by != cb[1] || bz != cb[2] || map != cmap) {  // warp-uniform
-        cb[0] = bx;
-        cb[1] = by;
-        cb[2] = bz;
-        cmap = map;
-        pool = -1;
-        if (lane < 27)
-          pool = find_pool_slot(a.hkeys, a.hvals, a.hash_cap,
-                                pack_block(bx - 1 + lane % 3, by - 1 + (lane / 3) % 3, bz - 1 + lane / 9, map));
-      }
-      if (lane < 27) {
-        t.blk[lane] = pool >= 0 ? a.alpha + ((size_t)pool * g.K1 + label) * g.B3 : nullptr;
-        if (kTrack) t.cnt[lane] = pool >= 0 ? a.pairs + (size_t)pool * g.B3 : nullptr;
+    const uint32_t c1 = min(P, c * chunk + chunk);
+    for (uint32_t g0 = c * chunk; g0 < c1; g0 += kGroup) {
+      const uint32_t gn = min(c1 - g0, (uint32_t)kGroup);  // warp-uniform
+      // 1. rows of every point of the group, three lanes per point
+      if (gl < (int)gn) {
+        const float4 p = a.train[g0 + gl];
+        const float xa = ax == 0 ? p.x : (ax == 1 ? p.y : p.z);
+        const int v0 = floor_small(__fmul_rn(xa, g.inv_res));
+        float hi, lo;
+        centre_offset0(v0, xa, g, hi, lo);
+        const float phi = 0.5f - __fmul_rn(__fadd_rn(hi, lo), g.inv_res);
+        const int b0 = v0 >> g.B_shift;
+        PointRows& pr = t.pts[gl];
+#pragma unroll
+        for (int j = 0; j < kFastAxis; ++j) {
+          if (j < na) {
+            const float e = centre_offset_at(j - R, hi, lo, g);
+            const int v = v0 + j - R;
+            pr.r[ax][j] = make_float2(__fmul_rn(e, e),
+                                      __int_as_float(dmul * ((v >> g.B_shift) - (b0 - 1)) | ((v & m) << (axshift + 8))));
+          }
+        }
+        if (ax == 0) pr.r[0][na] = make_float2(kFar, __int_as_float(0));
+        pr.pt[ax] = min(kParts - 1, max(0, floor_small(phi * (float)kParts)));
+        pr.blk[ax] = b0;
+        pr.v0[ax] = v0;
+        if (ax == 0) pr.pt[3] = label_of(p.w);
       }
       __syncwarp();
-      const uint32_t* tab = a.ctab + part * a.tpad;
-      const int len = __ldg(a.clen + part);
-      if (kNit > 0) {
-        uint32_t ent[kNit > 0 ? kNit : 1];
+      // 2. point by point: YZ rows, block slots, candidate sweeps
+      for (uint32_t k = 0; k < gn; ++k) {
+        const PointRows& pr = t.pts[k];
+        const int4 ip = *reinterpret_cast<const int4*>(pr.pt);
+        const int4 ib = *reinterpret_cast<const int4*>(pr.blk);
+        const int part = ip.x + kParts * (ip.y + kParts * ip.z);
+        const int label = ip.w & ((1 << kLabelBits) - 1), map = ip.w >> kLabelBits;
+        for (int q0 = 0; q0 < na * na; q0 += 32) {
+          const int q = min(q0 + lane, na * na - 1);
+          const int jy = (int)small_div((uint32_t)q, a.recip_na), jz = q - jy * na;
+          const float2 ry = pr.r[1][jy], rz = pr.r[2][jz];
+          if (q0 + lane < na * na)
+            t.yz[q] = make_float2(__fadd_rn(ry.x, rz.x), __int_as_float(__float_as_int(ry.y) + __float_as_int(rz.y)));
+        }
+        if (ib.x != cb[0] || ib.y != cb[1] || ib.z != cb[2] || map != cmap) {  // warp-uniform
+          cb[0] = ib.x;
+          cb[1] = ib.y;
+          cb[2] = ib.z;
+          cmap = map;
+          pool = -1;
+          if (lane < 27)
+            pool = find_pool_slot(a.hkeys, a.hvals, a.hash_cap,
+                                  pack_block(ib.x - 1 + lane % 3, ib.y - 1 + (lane / 3) % 3, ib.z - 1 + lane / 9, map));
+        }
+        if (lane < 27) {
+          t.blk[lane] = a.alpha + ((size_t)(pool >= 0 ? pool : a.sink) * g.K1 + label) * g.B3;
+          if (kTrack) t.cnt[lane] = a.pairs + (size_t)(pool >= 0 ? pool : a.sink) * g.B3;
+        }
+        __syncwarp();
+        const uint32_t* tab = a.ctab + part * a.tpad;
+        const int len = __ldg(a.clen + part);
+        const uint32_t i = g0 + k;
+        if (kNit > 0) {
+          uint32_t ent[kNit > 0 ? kNit : 1];
 #pragma unroll
-        for (int it = 0; it < kNit; ++it) ent[it] = it * 32 < len ? __ldg(tab + it * 32 + lane) : 0u;
+          for (int it = 0; it < kNit; ++it) ent[it] = it * 32 < len ? __ldg(tab + it * 32 + lane) : 0u;
 #pragma unroll
-        for (int it = 0; it < kNit; ++it)
-          if (it * 32 < len) npairs += candidate<kTrack>(a, t, ent[it], v0s, p);  // warp-uniform
-      } else {
-        for (int q = lane; q - lane < len; q += 32) npairs += candidate<kTrack>(a, t, __ldg(tab + q), v0s, p);
+          for (int it = 0; it < kNit; ++it)
+            if (it * 32 < len) npairs += candidate_rows<kTrack>(a, t, pr, ent[it], i);  // warp-uniform
+        } else {
+          for (int q = lane; q - lane < len; q += 32) npairs += candidate_rows<kTrack>(a, t, pr, __ldg(tab + q), i);
+        }
+        __syncwarp();  // the YZ rows and block pointers are rewritten for the next point
       }
-      __syncwarp();  // the tables are rewritten for the next point
     }
   }
   for (int o = 16; o > 0; o >>= 1) npairs += __shfl_down_sync(0xffffffffu, npairs, o);
@@ -402,6 +464,7 @@ cudaError_t launch_accumulate_points(MapState& m) {
   a.R = m.ctab_R;
   a.recip_na = ((1u << 20) + (uint32_t)(2 * m.ctab_R + 1) - 1u) / (uint32_t)(2 * m.ctab_R + 1);
   a.chunk = std::max(1, std::min(64, m.tune.accumulate_chunk));
+  a.sink = (int32_t)m.pool_blocks;
   a.dc = m.dc;
   m.launches += 2;
   const int cps = m.tune.accumulate_ctas_per_sm;

@@ -521,10 +521,12 @@ sbki_status sbki_create_map(const sbki_params* params, sbki_map** out) {
   if ((ce = dalloc(&m.boff, m.hash_cap + 1)) != cudaSuccess) return bail("block offsets", ce);
   m.list_cap = std::min<int64_t>(4 * params->sample_capacity, (1ll << 31) - 1);
   if ((ce = dalloc(&m.blist, m.list_cap)) != cudaSuccess) return bail("block point lists", ce);
-  if ((ce = dalloc(&m.alpha, (size_t)m.pool_blocks * blk)) != cudaSuccess) return bail("alpha pool", ce);
+  // one spare block after the pool: the point-major accumulation points the
+  // neighbour blocks a point's ball cannot reach at it (nothing reads it)
+  if ((ce = dalloc(&m.alpha, (size_t)(m.pool_blocks + 1) * blk)) != cudaSuccess) return bail("alpha pool", ce);
   if ((ce = dalloc(&m.pool_keys, m.pool_blocks)) != cudaSuccess) return bail("pool keys", ce);
   if (params->track_pairs)
-    if ((ce = dalloc(&m.pairs, (size_t)m.pool_blocks * m.g.B3)) != cudaSuccess) return bail("pair counts", ce);
+    if ((ce = dalloc(&m.pairs, (size_t)(m.pool_blocks + 1) * m.g.B3)) != cudaSuccess) return bail("pair counts", ce);
   if ((ce = dalloc(&m.dc, 1)) != cudaSuccess) return bail("counters", ce);
   if ((ce = cudaMallocHost((void**)&m.hc, sizeof(DevCounters))) != cudaSuccess) return bail("host counters", ce);
   Scratch& s = m.s;
