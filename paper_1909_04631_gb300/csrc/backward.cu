@@ -22,6 +22,7 @@
 // candidate lists, same FP32 test with the FP64 re-decision band), so the
 // backward pass sees exactly the pairs the forward pass added.
 #include <algorithm>
+#include <climits>
 
 #include "kernel_value.cuh"
 #include "point_common.cuh"
@@ -237,6 +238,200 @@ __global__ void __launch_bounds__(kThreads, 3) backward_kernel(BwdArgs a) {
   }
 }
 
+// The same pass for 2R + 1 <= 8 with the set-up of the fast accumulation: a
+// warp takes kBwdChunk consecutive training points in groups of up to
+// kBwdGroup; for a group, three lanes per point (one per axis) form the
+// axis's offset rows (e^2, address part, e) for offsets -R..R at once, with
+// the point's sub-voxel part, block and voxel.  Then, point by point, the
+// warp combines the Y and Z rows into YZ rows, refreshes the pool slots of
+// the 27 blocks around the point's block when the block (or map) changed,
+// and sweeps the candidate list in unrolled rounds of 32.  Rows, tests and
+// kernel arithmetic are the ones of backward_kernel, so both give the same
+// pairs and the same FP32 terms.
+constexpr int kBwdGroup = 10;  // points whose rows one warp forms at once (3 lanes each)
+constexpr int kBwdChunk = 20;  // consecutive training points per warp
+constexpr int kBwdAxis = 8;    // rows per axis: 2R + 1 <= 7 offsets and the padding row
+
+struct alignas(16) BwdRows {
+  float4 r[3][kBwdAxis];  // per axis: (e^2, address part, e, 0) of offset j - R; r[0][2R + 1] is the padding row
+  int pt[4];              // sub-voxel part per axis, label word
+  int blk[4];             // block per axis
+  int v0[4];              // voxel per axis
+};
+
+struct BwdFastTables {
+  BwdRows pts[kBwdGroup];
+  float4 yz[kBwdAxis * kBwdAxis];  // (e_y^2 + e_z^2, address part, e_y, e_z) of the point being swept
+  const float* blk[27];            // gpool + (pool (K+1) + y_i) B^3, or null
+};
+
+// One candidate of one point: the pair's terms added into sf, sl, sx, sy, sz
+// (the point's coordinates are loaded again only on the FP64 re-decision).
+__device__ __forceinline__ void bwd_candidate(const BwdArgs& a, const BwdFastTables& t, const BwdRows& pr,
+                                              uint32_t ent, int64_t i, float& sf, float& sl, float& sx, float& sy,
+                                              float& sz) {
+  const Geom& g = a.g;
+  const float4 ex = *reinterpret_cast<const float4*>(reinterpret_cast<const char*>(pr.r[0]) + 2u * (ent & 0xffu));
+  const float4 eyz = *reinterpret_cast<const float4*>(reinterpret_cast<const char*>(t.yz) + 2u * ((ent >> 8) & 0x7ffu));
+  const float d2 = __fadd_rn(ex.x, eyz.x);
+  const int pk = __float_as_int(ex.y) + __float_as_int(eyz.y);
+  bool in = d2 < g.l2_lo;
+  const bool band = !in && d2 < g.l2_hi;
+  if (__any_sync(0xffffffffu, band)) {
+    if (band) {
+      const float4 p = a.xyzl[i];
+      in = in_support64_call(pr.v0[0] + entry_jx(ent) - a.R, pr.v0[1] + entry_jy(ent) - a.R,
+                             pr.v0[2] + entry_jz(ent) - a.R, p.x, p.y, p.z, g.res64, g.l2_64);
+    }
+  }
+  const float* base = t.blk[pk & 0xff];
+  if (in && base != nullptr) {
+    const float G = __ldg(base + (pk >> 8));
+    const float inv_d = rsqrtf(fmaxf(d2, 1e-30f));
+    const float d = d2 * inv_d;
+    const float u = fmaxf(__fmaf_rn(-d, g.inv_l, 1.0f), 0.0f);
+    const float w = u * u;
+    const float u4 = w * w;
+    const float s = G * u4 * kernel_dq(w);  // -G df/dr
+    sf = __fmaf_rn(G * u4 * u, kernel_q(w), sf);
+    sl = __fmaf_rn(s, d, sl);
+    const float c = s * inv_d;
+    sx = __fmaf_rn(c, ex.z, sx);
+    sy = __fmaf_rn(c, eyz.z, sy);
+    sz = __fmaf_rn(c, eyz.w, sz);
+  }
+}
+
+// kNit > 0: lists of exactly kNit x 32 entries, unrolled; 0: any length
+template <int kNit>
+__global__ void __launch_bounds__(kThreads, 3) backward_fast_kernel(BwdArgs a) {
+  __shared__ BwdFastTables s_tab[kWarps];
+  const Geom& g = a.g;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int R = a.R, na = 2 * R + 1, m = g.B - 1;
+  BwdFastTables& t = s_tab[wid];
+  if (a.dc->err != 0) return;
+  // this lane's point of a group and axis (lanes 30, 31 form no rows)
+  const int gl = lane / 3, ax = lane - 3 * (lane / 3);
+  const int axshift = ax == 0 ? 0 : (ax == 1 ? g.B_shift : 2 * g.B_shift);
+  const int dmul = ax == 0 ? 1 : (ax == 1 ? 3 : 9);
+  int cb[3] = {INT_MIN, INT_MIN, INT_MIN}, cmap = -1;  // block and map the cached slots belong to
+  int32_t pool = -1;                                   // lanes 0..26: slot of block digit `lane`
+  double acc_f = 0.0, acc_l = 0.0;
+  for (int64_t c = gw; c * kBwdChunk < a.p; c += nw) {
+    const int64_t c1 = min(a.p, c * kBwdChunk + kBwdChunk);
+    for (int64_t g0 = c * kBwdChunk; g0 < c1; g0 += kBwdGroup) {
+      const int gn = (int)min(c1 - g0, (int64_t)kBwdGroup);  // warp-uniform
+      // 1. rows of every point of the group, three lanes per point
+      if (gl < gn) {
+        const float4 p = a.xyzl[g0 + gl];
+        const float xa = ax == 0 ? p.x : (ax == 1 ? p.y : p.z);
+        const int v0 = floor_small(__fmul_rn(xa, g.inv_res));
+        float hi, lo;
+        centre_offset0(v0, xa, g, hi, lo);
+        const float phi = 0.5f - __fmul_rn(__fadd_rn(hi, lo), g.inv_res);
+        const int b0 = v0 >> g.B_shift;
+        BwdRows& pr = t.pts[gl];
+#pragma unroll
+        for (int j = 0; j < kBwdAxis; ++j) {
+          if (j < na) {
+            const float e = centre_offset_at(j - R, hi, lo, g);
+            const int v = v0 + j - R;
+            pr.r[ax][j] = make_float4(__fmul_rn(e, e),
+                                      __int_as_float(dmul * ((v >> g.B_shift) - (b0 - 1)) | ((v & m) << (axshift + 8))),
+                                      e, 0.f);
+          }
+        }
+        if (ax == 0) pr.r[0][na] = make_float4(kFar, __int_as_float(0), 0.f, 0.f);
+        pr.pt[ax] = min(kParts - 1, max(0, floor_small(phi * (float)kParts)));
+        pr.blk[ax] = b0;
+        pr.v0[ax] = v0;
+        if (ax == 0) pr.pt[3] = label_of(p.w);
+      }
+      __syncwarp();
+      // 2. point by point: YZ rows, block slots, candidate sweeps, the point's terms
+      for (int k = 0; k < gn; ++k) {
+        const BwdRows& pr = t.pts[k];
+        const int4 ip = *reinterpret_cast<const int4*>(pr.pt);
+        const int4 ib = *reinterpret_cast<const int4*>(pr.blk);
+        const int part = ip.x + kParts * (ip.y + kParts * ip.z);
+        const int label = ip.w & ((1 << kLabelBits) - 1), map = ip.w >> kLabelBits;
+        for (int q0 = 0; q0 < na * na; q0 += 32) {
+          const int q = min(q0 + lane, na * na - 1);
+          const int jy = (int)small_div((uint32_t)q, a.recip_na), jz = q - jy * na;
+          const float4 ry = pr.r[1][jy], rz = pr.r[2][jz];
+          if (q0 + lane < na * na)
+            t.yz[q] = make_float4(__fadd_rn(ry.x, rz.x), __int_as_float(__float_as_int(ry.y) + __float_as_int(rz.y)),
+                                  ry.z, rz.z);
+        }
+        if (ib.x != cb[0] || ib.y != cb[1] || ib.z != cb[2] || map != cmap) {  // warp-uniform
+          cb[0] = ib.x;
+          cb[1] = ib.y;
+          cb[2] = ib.z;
+          cmap = map;
+          pool = -1;
+          if (lane < 27 && map < kMaxMaps)
+            pool = find_pool_slot(a.hkeys, a.hvals, a.hash_cap,
+                                  pack_block(ib.x - 1 + lane % 3, ib.y - 1 + (lane / 3) % 3, ib.z - 1 + lane / 9, map));
+        }
+        if (lane < 27)
+          t.blk[lane] = (pool >= 0 && label < g.K1) ? a.gpool + ((size_t)pool * g.K1 + label) * g.B3 : nullptr;
+        __syncwarp();
+        const uint32_t* tab = a.ctab + part * a.tpad;
+        const int len = __ldg(a.clen + part);
+        const int64_t i = g0 + k;
+        float sf = 0.f, sl = 0.f, sx = 0.f, sy = 0.f, sz = 0.f;
+        if (kNit > 0) {
+          uint32_t ent[kNit > 0 ? kNit : 1];
+#pragma unroll
+          for (int it = 0; it < kNit; ++it) ent[it] = it * 32 < len ? __ldg(tab + it * 32 + lane) : 0u;
+#pragma unroll
+          for (int it = 0; it < kNit; ++it)
+            if (it * 32 < len) bwd_candidate(a, t, pr, ent[it], i, sf, sl, sx, sy, sz);  // warp-uniform
+        } else {
+          for (int q = lane; q - lane < len; q += 32) bwd_candidate(a, t, pr, __ldg(tab + q), i, sf, sl, sx, sy, sz);
+        }
+        acc_f += (double)sf;
+        acc_l += (double)sl;
+        if (a.grad_xyz) {
+          for (int o = 16; o > 0; o >>= 1) {
+            sx += __shfl_down_sync(0xffffffffu, sx, o);
+            sy += __shfl_down_sync(0xffffffffu, sy, o);
+            sz += __shfl_down_sync(0xffffffffu, sz, o);
+          }
+          if (lane == 0) {
+            a.grad_xyz[3 * i] = sx * a.xyz_scale;
+            a.grad_xyz[3 * i + 1] = sy * a.xyz_scale;
+            a.grad_xyz[3 * i + 2] = sz * a.xyz_scale;
+          }
+        }
+        __syncwarp();  // the YZ rows and block pointers are rewritten for the next point
+      }
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    acc_f += __shfl_down_sync(0xffffffffu, acc_f, o);
+    acc_l += __shfl_down_sync(0xffffffffu, acc_l, o);
+  }
+  if (lane == 0) {
+    atomicAdd(&a.acc[0], acc_f);
+    atomicAdd(&a.acc[1], acc_l);
+  }
+}
+
+template <int kNit>
+cudaError_t launch_backward_fast(const BwdArgs& a, int sm_count, cudaStream_t st) {
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, backward_fast_kernel<kNit>, kThreads, 0);
+  if (e != cudaSuccess) return e;
+  const int64_t want = (a.p + (int64_t)kWarps * kBwdChunk - 1) / ((int64_t)kWarps * kBwdChunk);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)std::max(1, per_sm) * sm_count));
+  backward_fast_kernel<kNit><<<grid, kThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_heldout(const MapState& m, const float* xyz, const int32_t* labels, int64_t h, float* grad,
@@ -289,6 +484,16 @@ cudaError_t launch_backward(const MapState& m, const float4* xyzl, int64_t p, co
   a.grad_xyz = grad_xyz;
   a.xyz_scale = (float)(m.prm.sigma0 / m.prm.length_scale);
   a.dc = m.dc;
+  if (2 * a.R + 1 <= kBwdAxis - 1) {
+    switch (a.tpad / 32) {  // unrolled sweeps for the common list lengths
+      case 2: return launch_backward_fast<2>(a, m.sm_count, m.stream);
+      case 3: return launch_backward_fast<3>(a, m.sm_count, m.stream);
+      case 4: return launch_backward_fast<4>(a, m.sm_count, m.stream);
+      case 5: return launch_backward_fast<5>(a, m.sm_count, m.stream);
+      case 6: return launch_backward_fast<6>(a, m.sm_count, m.stream);
+      default: return launch_backward_fast<0>(a, m.sm_count, m.stream);
+    }
+  }
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, backward_kernel, kThreads, 0);
   if (e != cudaSuccess) return e;

@@ -148,3 +148,18 @@ def test_counting_model_refuses_backward_and_block_major(sb):
     with pytest.raises(sb.SbkiError) as e:
         sb.Map(_params(sb, prm, accumulate_mode=1))
     assert e.value.status == sb.ERR_INVALID_ARG
+
+
+def test_counting_full_street_scan_matches_oracle(sb, orc):
+    """One full 64 x 2048 LiDAR street scan (about 130k hits, 2.9M free samples)
+    in the benchmark's map configuration: the whole counting map, every voxel
+    of every block, equals the oracle's."""
+    sc = next(scenes.street_sequence(1, first=5))
+    prm = dict(scenes.STREET_PARAMS)
+    m = sb.Map(_params(sb, prm, pool_blocks=1 << 18, sample_capacity=1 << 23))
+    st = m.insert_scan(sc["points"], sc["labels"], sc["pose"])
+    om = orc.OracleMap(_orc_params(orc, prm))
+    ost = om.insert_scan(sc["points"], sc["labels"], sc["pose"])
+    assert (st["hits"], st["free_samples"], st["train_points"]) == (ost["hits"], ost["free"], ost["train"])
+    assert st["pairs"] == ost["train"] and st["touched_blocks"] == len(om.block_keys())
+    _assert_counts_equal(m, om, prm["alpha0"])
