@@ -42,7 +42,7 @@ KERNEL_SOURCES = ["paper_1909_04631_gb300/csrc/accumulate_points.cu", "paper_190
 
 def _gen(args):
     first, count = args
-    return [dict(points=s["points"], labels=s["labels"], pose=s["pose"])
+    return [dict(points=s["points"], labels=s["labels"], clean_labels=s["clean_labels"], pose=s["pose"])
             for s in scenes.street_sequence(count, first=first)]
 
 
@@ -429,6 +429,27 @@ def counting_model(sb, torch, stream, p, dpts, dlab, poses, warmup, steps):
                            "frac": bytes_alg / acc_s / 1e9 / bw, "peak_source": "hbm_gbs of %s peaks" % src}}
 
 
+def map_quality_form(sb, stream, p, scans, n=20):
+    """Both sensor models on the first n street scans, scored on those scans
+    against the generator's clean labels (before the label noise): IoU of the
+    map's labels at the hits and AUC of p_occ, hits against points the beams
+    passed through (every 16th beam).  Not timed."""
+    from paper_1909_04631_gb300 import evaluate as ev
+    out = {"workload": "street scans 0..%d inserted, then scored on their own hits and beams" % (n - 1),
+           "ground_truth": "clean labels of the generator (before the 10 % label noise)"}
+    K = scenes.STREET_PARAMS["num_classes"]
+    for name, model in (("s_bki", 0), ("s_csm", 1)):
+        with sb.Map(p, stream=stream, sensor_model=model) as m:
+            for sc in scans[:n]:
+                m.insert_scan(sc["points"], sc["labels"], sc["pose"])
+            q = ev.map_quality(lambda x: m.query(x, var=False, mode=False, state=False), scans[:n], K,
+                               scenes.STREET_PARAMS["free_step"], stride=16)
+        fin = lambda v: None if v != v else v  # noqa: E731  (NaN: a class neither present nor predicted)
+        out[name] = {"miou": fin(q["miou"]), "auc": fin(q["auc"]), "iou": [fin(round(v, 4)) for v in q["iou"]]}
+        out["hits"], out["free_probes"] = q["hits"], q["free_probes"]
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_1909_04631_gb300 as sb
@@ -587,6 +608,7 @@ def run_ours(args, rank, world, local_rank):
         line["differentiable"] = differentiable_form(sb, torch, dev, stream, forms_input[1], reps=3)
         line["other_workloads"] = other_workloads(sb, torch, dev, stream, forms_input[2], forms_input[3])
         line["counting_model"] = counting_model(sb, torch, stream, p, dpts, dlab, poses, args.warmup, args.steps)
+        line["map_quality"] = map_quality_form(sb, stream, p, scans, n=min(20, len(scans)))
     print(json.dumps(line), flush=True)
     return 0
 

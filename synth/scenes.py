@@ -486,7 +486,8 @@ def street_sequence(n_scans=100, seed=1, n_beams=64, n_az=2048, range_sigma=0.03
     """LiDAR-shaped scans along the street: poses 1 m apart along x at y = -1.75,
     sensor height 1.73 m, yaw ~ N(0, 1 deg); beams evenly over +2 to -24.8 degrees.
 
-    Yields dicts (points [n,3] float32 sensor frame, labels [n] int32 in 1..19, pose 4x4).
+    Yields dicts (points [n,3] float32 sensor frame, labels [n] int32 in 1..19 with label
+    noise, clean_labels [n] the same points' labels before the noise, pose 4x4).
     Scan i depends only on (seed, i), so any sub-range can be generated alone."""
     sc = street_scene(seed) if scene is None else scene
     dirs = lidar_dirs(n_beams, n_az, 2.0, -24.8)
@@ -494,9 +495,9 @@ def street_sequence(n_scans=100, seed=1, n_beams=64, n_az=2048, range_sigma=0.03
         rng = np.random.default_rng([seed, 7919, i])
         yaw = math.radians(rng.normal(0.0, 1.0))
         pose = pose_matrix([float(i), -1.75, 1.73], yaw=yaw)
-        pts, lab = _scan(sc, pose, dirs, STREET_PARAMS["max_range"], range_sigma, rng)
-        lab = _label_noise(rng, lab, label_noise, sc.num_classes)
-        yield dict(points=pts, labels=lab, pose=pose, num_classes=sc.num_classes)
+        pts, clean = _scan(sc, pose, dirs, STREET_PARAMS["max_range"], range_sigma, rng)
+        lab = _label_noise(rng, clean, label_noise, sc.num_classes)
+        yield dict(points=pts, labels=lab, clean_labels=clean, pose=pose, num_classes=sc.num_classes)
 
 
 # --------------------------------------------------------------------------
