@@ -33,16 +33,23 @@ def build(force: bool = False) -> str:
 class OrcParams(C.Structure):
     _fields_ = [(n, C.c_double) for n in ("res", "length_scale", "sigma0", "alpha0", "free_step", "ds_res",
                                           "min_range", "max_range", "free_thresh", "occ_thresh")] + \
-               [("num_classes", C.c_int32), ("block_edge", C.c_int32), ("sensor_model", C.c_int32)]
+               [("num_classes", C.c_int32), ("block_edge", C.c_int32), ("sensor_model", C.c_int32),
+                ("sigma0_scale", C.c_double * 32)]
 
 
 def params(res=0.1, length_scale=0.3, sigma0=0.1, alpha0=0.001, free_step=0.3, ds_res=None, min_range=0.0,
            max_range=1e30, free_thresh=0.47, occ_thresh=0.6, num_classes=10, block_edge=8, sensor_model=0,
-           **_ignored):
+           sigma0_scale=None, **_ignored):
     """Parameter block; defaults follow Table (parameters) and Sec. V-A of the paper.
-    sensor_model 0: kernel inference, Eq. (alpha_kernel); 1: counting model, Eq. (alpha)."""
+    sensor_model 0: kernel inference, Eq. (alpha_kernel); 1: counting model, Eq. (alpha).
+    sigma0_scale: per-class multipliers of sigma0 (classes 0..K; default all 1)."""
+    sc = [1.0] * 32
+    if sigma0_scale is not None:
+        for k, v in enumerate(sigma0_scale):
+            sc[k] = float(v)
     return OrcParams(res, length_scale, sigma0, alpha0, free_step, res if ds_res is None else ds_res, min_range,
-                     max_range, free_thresh, occ_thresh, num_classes, block_edge, sensor_model)
+                     max_range, free_thresh, occ_thresh, num_classes, block_edge, sensor_model,
+                     (C.c_double * 32)(*sc))
 
 
 _P = C.POINTER
@@ -84,6 +91,8 @@ def lib():
             L.orc_map_query.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp]
             L.orc_heldout_grad.restype = f64
             L.orc_heldout_grad.argtypes = [_P(OrcParams), vp, vp, i64, vp, vp, i64, vp, vp, vp]
+            L.orc_heldout_grad_scale.restype = f64
+            L.orc_heldout_grad_scale.argtypes = [_P(OrcParams), vp, vp, i64, vp, vp, i64, vp]
             L.orc_heldout_ll.restype = f64
             L.orc_heldout_ll.argtypes = [_P(OrcParams), vp, vp, i64, vp, vp, i64]
             _lib = L
@@ -185,6 +194,16 @@ def heldout_grad(p, xyz64, labels, held_xyz, held_labels):
     ll = lib().orc_heldout_grad(C.byref(p), _ptr(xyz64), _ptr(lab), len(xyz64), _ptr(hx), _ptr(hl), len(hx),
                                 C.byref(gl), C.byref(gs), _ptr(gx))
     return ll, gl.value, gs.value, gx
+
+
+def heldout_grad_scale(p, xyz64, labels, held_xyz, held_labels):
+    """(LL, dLL/d sigma0_scale[k] for k = 0..K) in FP64."""
+    xyz64, lab = _f64(xyz64).reshape(-1, 3), _i32(labels)
+    hx, hl = _f32(held_xyz).reshape(-1, 3), _i32(held_labels)
+    gsc = np.zeros(p.num_classes + 1)
+    ll = lib().orc_heldout_grad_scale(C.byref(p), _ptr(xyz64), _ptr(lab), len(xyz64), _ptr(hx), _ptr(hl), len(hx),
+                                      _ptr(gsc))
+    return ll, gsc
 
 
 class OracleMap:

@@ -39,6 +39,9 @@
 //       are the training points of steps a1..a3, each of weight 1 (as in K4),
 //       and "x_i in cell j" is the voxel key of K6.  Every counted point leaves
 //       one (voxel, point) pair, so the pair count of a voxel is its count.
+//   K13 Per-class kernel scale (the paper names class-dependent signal
+//       variance as the way to let sigma0 matter): class k's kernel is
+//       sigma0 * sigma0_scale[k] * f(d/l); all scales 1 is Eq. (kernel) as printed.
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -56,6 +59,7 @@ struct Params {
   int32_t num_classes;  // K occupied classes; alpha has K+1 entries
   int32_t block_edge;
   int32_t sensor_model;  // 0: kernel inference, Eq. (alpha_kernel); 1: counting, Eq. (alpha)
+  double sigma0_scale[32];  // reading K13: class k's kernel scale is sigma0 * sigma0_scale[k]
 };
 
 const double kPi = 3.14159265358979323846;
@@ -312,7 +316,7 @@ void accumulate(Map& m, const std::vector<Sample>& train) {
           d2 = d2 + ey * ey;
           d2 = d2 + ez * ez;
           if (!(d2 < l2)) continue;
-          double kval = p.sigma0 * kernel_f(std::sqrt(d2) / l);
+          double kval = p.sigma0 * p.sigma0_scale[s.label] * kernel_f(std::sqrt(d2) / l);
           Key3 bk = {floor_div(vx, B), floor_div(vy, B), floor_div(vz, B)};
           Block& blk = m.blocks[bk];
           if (blk.inc.empty()) {
@@ -398,6 +402,7 @@ extern "C" {
 typedef struct {
   double res, length_scale, sigma0, alpha0, free_step, ds_res, min_range, max_range, free_thresh, occ_thresh;
   int32_t num_classes, block_edge, sensor_model;
+  double sigma0_scale[32];
 } orc_params;
 
 static Params conv(const orc_params* q) {
@@ -581,7 +586,7 @@ void orc_alpha_bruteforce(const orc_params* q, const float* xyz, const int32_t* 
       d2 = d2 + ey * ey;
       d2 = d2 + ez * ez;
       if (!(d2 < l2)) continue;
-      alpha[v * K1 + lab[i]] += p.sigma0 * kernel_f(std::sqrt(d2) / l);
+      alpha[v * K1 + lab[i]] += p.sigma0 * p.sigma0_scale[lab[i]] * kernel_f(std::sqrt(d2) / l);
       ++pc;
     }
     if (pairs) pairs[v] = pc;
@@ -638,10 +643,11 @@ void orc_map_query(void* h, const float* xyz, int64_t nq, double* probs, double*
 // Training coordinates are FP64 here so that finite differences can move them
 // by less than an FP32 ulp; the stencil centre is the voxel of (float)x.
 // held_xyz are world coordinates; v(h) is the voxel containing the point.
-// Returns LL; grad_l, grad_sigma0, grad_xyz ([n,3]) are nullable.
-double orc_heldout_grad(const orc_params* q, const double* xyz, const int32_t* lab, int64_t n,
-                        const float* held_xyz, const int32_t* held_lab, int64_t nh, double* grad_l,
-                        double* grad_sigma0, double* grad_xyz) {
+// Returns LL; grad_l, grad_sigma0, grad_xyz ([n,3]) and grad_scale (dLL/d
+// sigma0_scale[k], [K+1]) are nullable.
+static double heldout_grad(const orc_params* q, const double* xyz, const int32_t* lab, int64_t n,
+                           const float* held_xyz, const int32_t* held_lab, int64_t nh, double* grad_l,
+                           double* grad_sigma0, double* grad_xyz, double* grad_scale) {
   Params p = conv(q);
   const int K1 = nclass(p);
   const float inv_res = (float)(1.0 / p.res);
@@ -667,7 +673,7 @@ double orc_heldout_grad(const orc_params* q, const double* xyz, const int32_t* l
           if (!(d2 < l2)) continue;
           std::vector<double>& a = inc[v];
           if (a.empty()) a.assign((size_t)K1, 0.0);
-          a[(size_t)lab[i]] += p.sigma0 * kernel_f(std::sqrt(d2) / l);
+          a[(size_t)lab[i]] += p.sigma0 * p.sigma0_scale[lab[i]] * kernel_f(std::sqrt(d2) / l);
         }
   }
 
@@ -691,10 +697,12 @@ double orc_heldout_grad(const orc_params* q, const double* xyz, const int32_t* l
     for (int c = 0; c < K1; ++c) gv[c] -= 1.0 / S;
     gv[y] += 1.0 / a[y];
   }
-  if (!grad_l && !grad_sigma0 && !grad_xyz) return LL;
+  if (!grad_l && !grad_sigma0 && !grad_xyz && !grad_scale) return LL;
 
-  // 3. chain rule through every in-support pair (Eq. kernel)
+  // 3. chain rule through every in-support pair (Eq. kernel); class k's kernel
+  //    is s sigma0 f with s = sigma0_scale[k]
   double gl = 0.0, gs = 0.0;
+  std::vector<double> gsc((size_t)K1, 0.0);
   for (int64_t i = 0; i < n; ++i) {
     double x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
     int64_t kx = voxel_index((float)x, inv_res), ky = voxel_index((float)y, inv_res),
@@ -714,13 +722,15 @@ double orc_heldout_grad(const orc_params* q, const double* xyz, const int32_t* l
           auto it = g.find(v);
           if (it == g.end()) continue;
           double G = it->second[(size_t)lab[i]];
+          const double sc = p.sigma0_scale[lab[i]];
           double d = std::sqrt(d2), r = d / l;
           double df = kernel_df(r);
-          gs += G * kernel_f(r);
-          gl += G * p.sigma0 * df * (-d / l2);
+          gs += G * sc * kernel_f(r);
+          gsc[(size_t)lab[i]] += G * p.sigma0 * kernel_f(r);
+          gl += G * sc * p.sigma0 * df * (-d / l2);
           if (d > 0.0) {
             // d = |c - x|, so dd/dx = (x - c)/d = -e/d
-            double coef = G * p.sigma0 * df / (l * d);
+            double coef = G * sc * p.sigma0 * df / (l * d);
             gx -= coef * ex;
             gy -= coef * ey;
             gz -= coef * ez;
@@ -734,14 +744,28 @@ double orc_heldout_grad(const orc_params* q, const double* xyz, const int32_t* l
   }
   if (grad_l) *grad_l = gl;
   if (grad_sigma0) *grad_sigma0 = gs;
+  if (grad_scale)
+    for (int c = 0; c < K1; ++c) grad_scale[c] = gsc[(size_t)c];
   return LL;
+}
+
+double orc_heldout_grad(const orc_params* q, const double* xyz, const int32_t* lab, int64_t n,
+                        const float* held_xyz, const int32_t* held_lab, int64_t nh, double* grad_l,
+                        double* grad_sigma0, double* grad_xyz) {
+  return heldout_grad(q, xyz, lab, n, held_xyz, held_lab, nh, grad_l, grad_sigma0, grad_xyz, nullptr);
+}
+
+// dLL/d sigma0_scale[k] for every class k ([K+1]); returns LL.
+double orc_heldout_grad_scale(const orc_params* q, const double* xyz, const int32_t* lab, int64_t n,
+                              const float* held_xyz, const int32_t* held_lab, int64_t nh, double* grad_scale) {
+  return heldout_grad(q, xyz, lab, n, held_xyz, held_lab, nh, nullptr, nullptr, nullptr, grad_scale);
 }
 
 // Held-out log-likelihood alone (same definition as orc_heldout_grad), for
 // the finite-difference checks.
 double orc_heldout_ll(const orc_params* q, const double* xyz, const int32_t* lab, int64_t n, const float* held_xyz,
                       const int32_t* held_lab, int64_t nh) {
-  return orc_heldout_grad(q, xyz, lab, n, held_xyz, held_lab, nh, nullptr, nullptr, nullptr);
+  return heldout_grad(q, xyz, lab, n, held_xyz, held_lab, nh, nullptr, nullptr, nullptr, nullptr);
 }
 
 }  // extern "C"

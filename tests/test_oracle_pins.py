@@ -466,6 +466,47 @@ def test_gradient_matches_central_differences(orc):
             assert gx[i, d] == pytest.approx(fd, rel=1e-3, abs=1e-6)
 
 
+def test_class_scales_against_bruteforce(orc):
+    """Reading K13: class k's kernel is sigma0 * sigma0_scale[k] * f; a numpy
+    all-pairs sum with distinct per-class scales fixes which scale each
+    training point takes."""
+    rng = np.random.default_rng(29)
+    xyz = rng.uniform(-0.4, 0.4, size=(80, 3)).astype(np.float32)
+    lab = rng.integers(0, 5, size=80).astype(np.int32)
+    scale = np.array([0.5, 1.0, 2.0, 3.5, 0.25])
+    p = orc.params(res=0.1, length_scale=0.3, sigma0=0.6, num_classes=4, sigma0_scale=scale)
+    m = orc.OracleMap(p)
+    m.insert_training(xyz, lab)
+    keys, alpha, pairs = m.export()
+    bf = _bruteforce(orc, orc.params(res=0.1, length_scale=0.3, sigma0=0.6, num_classes=4), xyz, lab)
+    for k, a, n in zip(map(tuple, keys), alpha, pairs):
+        want = bf.get(k, [np.zeros(5), 0])
+        np.testing.assert_allclose(a - p.alpha0, want[0] * scale, rtol=1e-12, atol=1e-15)
+        assert n == want[1]
+    got, _ = orc.alpha_bruteforce(p, xyz, lab, keys[:50])
+    np.testing.assert_allclose(got, alpha[:50], rtol=1e-12)
+
+
+def test_gradient_in_class_scales(orc):
+    """dLL/d sigma0_scale[k] against central differences, and the scaling
+    identity sum_k s_k dLL/ds_k = sigma0 dLL/dsigma0 (alpha increments are
+    linear in sigma0 s_k)."""
+    xyz, lab, held, hl = _grad_case(orc)
+    scale = [0.7, 1.3, 1.0, 2.2]
+    base = dict(res=0.1, length_scale=0.3, sigma0=0.8, num_classes=3, sigma0_scale=scale)
+    ll, gsc = orc.heldout_grad_scale(orc.params(**base), xyz, lab, held, hl)
+    h = 1e-5
+    for k in range(4):
+        up, dn = list(scale), list(scale)
+        up[k] += h
+        dn[k] -= h
+        fd = (orc.heldout_ll(orc.params(**{**base, "sigma0_scale": up}), xyz, lab, held, hl) -
+              orc.heldout_ll(orc.params(**{**base, "sigma0_scale": dn}), xyz, lab, held, hl)) / (2 * h)
+        assert gsc[k] == pytest.approx(fd, rel=1e-4, abs=1e-8)
+    _, _, gs, _ = orc.heldout_grad(orc.params(**base), xyz, lab, held, hl)
+    assert float(np.dot(scale, gsc)) == pytest.approx(0.8 * gs, rel=1e-10)
+
+
 def test_gradient_sigma0_and_euler_identities(orc):
     """alpha - alpha0 is linear in sigma0; alpha_v depends on (x_i - c_v)/l only,
     so l dLL/dl + sum_i (x_i - c_v) . dLL/dx_i = 0 when every held-out point is
