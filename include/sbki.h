@@ -77,6 +77,10 @@ typedef struct sbki_params {
                          * voxel floor(x * fp32(1/res)) that contains it (exact FP32 counts below
                          * 2^24 per voxel and class); length_scale and sigma0 do not enter it.
                          * Needs accumulate_mode 0; sbki_backward and sbki_grad refuse it */
+  double sigma0_scale[32]; /* per-class kernel scale: class k's kernel is sigma0 * sigma0_scale[k]
+                            * * f(d/l) (the paper's class-dependent signal variance, Sec. V);
+                            * entries 0..K must be finite and > 0; sbki_default_params sets 1,
+                            * which is Eq. (kernel) as printed.  Unused by the counting model */
 } sbki_params;
 
 /* Per-insert counters (all for the last insert). */
@@ -293,6 +297,12 @@ sbki_status sbki_grad_add_alpha(sbki_map* map, const int64_t* keys, const float*
  * returns SBKI_ERR_INVALID_ARG. */
 sbki_status sbki_backward(sbki_map* map, const float* xyzl, int64_t p, double* grad_l, double* grad_sigma0,
                           float* grad_xyz);
+
+/* The same pass for the per-class kernel scales: grad_scale[k] = dL/d
+ * sigma0_scale[k] = sum over the in-support pairs of class-k points of
+ * G sigma0 f(r) (host, [K+1], summed in FP64 from FP32 pair terms).  Same
+ * inputs and errors as sbki_backward. */
+sbki_status sbki_backward_scales(sbki_map* map, const float* xyzl, int64_t p, double* grad_scale);
 
 /* Stateless forms (they create and destroy a map of `params` inside the call,
  * so they allocate): alpha of a training set at every voxel of the blocks it

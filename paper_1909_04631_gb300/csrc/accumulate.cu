@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(kThreads, 2) accumulate_kernel(AccArgs a) {
             if (in) {
               const float d = d2 > 0.0f ? d2 * rsqrtf(d2) : 0.0f;
               const float u = __fmul_rn(__fsub_rn(g.l, d), g.inv_l);
-              atomicAdd(&asum[abase + i], g.sigma0 * kernel_f_poly_u(u));
+              atomicAdd(&asum[abase + i], g.sigma0_k[packed & 31u] * kernel_f_poly_u(u));
               ++npairs;
               if (kTrack) atomicAdd(&pcnt[vbase + i], 1);
             }

@@ -77,10 +77,11 @@ struct WarpTables {
 // this update (the touched-block pass applies the same membership test and
 // allocated every block that does), so no in-support pair reaches it; its
 // pointer names the spare block after the pool, so the reduction needs no
-// null test.  Returns 1 for an in-support pair.
+// null test.  s0 is the point's class scale sigma0 * sigma0_scale[y_i].
+// Returns 1 for an in-support pair.
 template <bool kTrack>
 __device__ __forceinline__ uint32_t candidate(const PtArgs& a, const WarpTables& t, uint32_t ent, const int v0[3],
-                                              const float4& p) {
+                                              const float4& p, float s0) {
   const Geom& g = a.g;
   const float2 ex = *reinterpret_cast<const float2*>(reinterpret_cast<const char*>(t.x) + (ent & 0xffu));
   const float2 eyz = *reinterpret_cast<const float2*>(reinterpret_cast<const char*>(t.yz) + ((ent >> 8) & 0x7ffu));
@@ -97,7 +98,7 @@ __device__ __forceinline__ uint32_t candidate(const PtArgs& a, const WarpTables&
   const float d = d2 * rsqrtf(fmaxf(d2, 1e-30f));
   const float u = fmaxf(__fmaf_rn(-d, g.inv_l, 1.0f), 0.0f);
   const float w = u * u;
-  red_add_if(in, base + (pk >> 8), g.sigma0 * (w * w * u * kernel_q(w)));
+  red_add_if(in, base + (pk >> 8), s0 * (w * w * u * kernel_q(w)));
   if (kTrack) red_add_if(in, t.cnt[pk & 0xff] + (pk >> 8), 1);
   return in ? 1u : 0u;
 }
@@ -122,6 +123,7 @@ __global__ void __launch_bounds__(kThreads, 4) accumulate_points_kernel(PtArgs a
     if (i + nw < P) pnext = a.train[i + nw];  // in flight while this point is processed
     const int lm = label_of(p.w);  // label + 32 * map
     const int label = lm & ((1 << kLabelBits) - 1), map = lm >> kLabelBits;
+    const float s0 = g.sigma0_k[label];  // class label's kernel scale
     const PointFrame f = point_frame(p.x, p.y, p.z, R, g);
     const uint32_t* tab = a.ctab + f.part * a.tpad;
     const int len = __ldg(a.clen + f.part);
@@ -161,9 +163,9 @@ __global__ void __launch_bounds__(kThreads, 4) accumulate_points_kernel(PtArgs a
       for (int it = 0; it < kNit; ++it) ent[it] = it * 32 < len ? __ldg(tab + it * 32 + lane) : 0u;
 #pragma unroll
       for (int it = 0; it < kNit; ++it)
-        if (it * 32 < len) npairs += candidate<kTrack>(a, t, ent[it], f.v0, p);  // warp-uniform
+        if (it * 32 < len) npairs += candidate<kTrack>(a, t, ent[it], f.v0, p, s0);  // warp-uniform
     } else {
-      for (int k = lane; k - lane < len; k += 32) npairs += candidate<kTrack>(a, t, __ldg(tab + k), f.v0, p);
+      for (int k = lane; k - lane < len; k += 32) npairs += candidate<kTrack>(a, t, __ldg(tab + k), f.v0, p, s0);
     }
     __syncwarp();  // the tables are rewritten for the next point
   }
@@ -201,7 +203,7 @@ struct FastTables {
 // coordinates are loaded again only on the (rare) FP64 re-decision.
 template <bool kTrack>
 __device__ __forceinline__ uint32_t candidate_rows(const PtArgs& a, const FastTables& t, const PointRows& pr,
-                                                   uint32_t ent, uint32_t i) {
+                                                   uint32_t ent, uint32_t i, float s0) {
   const Geom& g = a.g;
   const float2 ex = *reinterpret_cast<const float2*>(reinterpret_cast<const char*>(pr.r[0]) + (ent & 0xffu));
   const float2 eyz = *reinterpret_cast<const float2*>(reinterpret_cast<const char*>(t.yz) + ((ent >> 8) & 0x7ffu));
@@ -220,7 +222,7 @@ __device__ __forceinline__ uint32_t candidate_rows(const PtArgs& a, const FastTa
   const float d = d2 * rsqrtf(fmaxf(d2, 1e-30f));
   const float u = fmaxf(__fmaf_rn(-d, g.inv_l, 1.0f), 0.0f);
   const float w = u * u;
-  red_add_if(in, base + (pk >> 8), g.sigma0 * (w * w * u * kernel_q(w)));
+  red_add_if(in, base + (pk >> 8), s0 * (w * w * u * kernel_q(w)));
   if (kTrack) red_add_if(in, t.cnt[pk & 0xff] + (pk >> 8), 1);
   return in ? 1u : 0u;
 }
@@ -281,6 +283,7 @@ __global__ void __launch_bounds__(kThreads, 4) accumulate_points_fast_kernel(PtA
         const int4 ib = *reinterpret_cast<const int4*>(pr.blk);
         const int part = ip.x + kParts * (ip.y + kParts * ip.z);
         const int label = ip.w & ((1 << kLabelBits) - 1), map = ip.w >> kLabelBits;
+        const float s0 = g.sigma0_k[label];  // class label's kernel scale
         for (int q0 = 0; q0 < na * na; q0 += 32) {
           const int q = min(q0 + lane, na * na - 1);
           const int jy = (int)small_div((uint32_t)q, a.recip_na), jz = q - jy * na;
@@ -312,9 +315,10 @@ __global__ void __launch_bounds__(kThreads, 4) accumulate_points_fast_kernel(PtA
           for (int it = 0; it < kNit; ++it) ent[it] = it * 32 < len ? __ldg(tab + it * 32 + lane) : 0u;
 #pragma unroll
           for (int it = 0; it < kNit; ++it)
-            if (it * 32 < len) npairs += candidate_rows<kTrack>(a, t, pr, ent[it], i);  // warp-uniform
+            if (it * 32 < len) npairs += candidate_rows<kTrack>(a, t, pr, ent[it], i, s0);  // warp-uniform
         } else {
-          for (int q = lane; q - lane < len; q += 32) npairs += candidate_rows<kTrack>(a, t, pr, __ldg(tab + q), i);
+          for (int q = lane; q - lane < len; q += 32)
+            npairs += candidate_rows<kTrack>(a, t, pr, __ldg(tab + q), i, s0);
         }
         __syncwarp();  // the YZ rows and block pointers are rewritten for the next point
       }

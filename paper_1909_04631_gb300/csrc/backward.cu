@@ -10,7 +10,9 @@
 //   dL/dx_i    += G sigma0 f'(r) (x_i - c_v) / (l d)
 // with r = d/l, f' = df/dr = -u^4 D(u^2), u = 1 - r (kernel_poly.cuh); the
 // x_i term is written with the unit vector (x_i - c_v)/d, which stays bounded
-// as d -> 0 (f'(0) = 0).
+// as d -> 0 (f'(0) = 0).  With per-class kernel scales (class k's kernel is
+// sigma0 s_k f) every term of a class-k point carries s_k, applied once per
+// point, and dL/ds_k = sigma0 sum_{pairs of class-k points} G f.
 //
 // The held-out log-likelihood of the differentiable form scores held-out
 // labelled points at the voxel containing them:
@@ -132,7 +134,8 @@ struct BwdArgs {
   const int32_t* clen;
   int tpad, R;
   uint32_t recip_na;
-  double* acc;         // [2]: sum G f, sum G u^4 D d
+  double* acc;         // [2]: sum s G f, sum s G u^4 D d (s: the point's class scale)
+  double* acc_class;   // nullable [32]: per class of the point, sum G f
   float* grad_xyz;     // nullable [p][3]: (sigma0 / l) sum G u^4 D (c_v - x)/d
   float xyz_scale;     // sigma0 / l
   DevCounters* dc;
@@ -144,6 +147,13 @@ struct BwdTables {
   const float* blk[27];    // gpool + (pool (K+1) + y_i) B^3, or null
 };
 
+// Adds the warp's sum of one point's lane terms v into the warp's class row
+// (lane 0 writes; every lane of the warp calls it).
+__device__ __forceinline__ void add_class_sum(double* row, int label, float v, int lane) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (lane == 0 && label < 32) row[label] += (double)v;
+}
+
 __global__ void __launch_bounds__(kThreads, 3) backward_kernel(BwdArgs a) {
   __shared__ BwdTables s_tab[kWarps];
   const Geom& g = a.g;
@@ -152,8 +162,10 @@ __global__ void __launch_bounds__(kThreads, 3) backward_kernel(BwdArgs a) {
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int R = a.R, na = 2 * R + 1;
   BwdTables& t = s_tab[wid];
+  __shared__ double s_cls[kWarps][32];  // per warp: sum G f by class (only with acc_class)
   if (a.dc->err != 0) return;
   if (lane == 0) t.x[na] = make_float4(kFar, __int_as_float(0), 0.f, 0.f);
+  s_cls[wid][lane] = 0.0;
   double acc_f = 0.0, acc_l = 0.0;
   for (int64_t i = gw; i < a.p; i += nw) {
     const float4 p = a.xyzl[i];
@@ -212,8 +224,10 @@ __global__ void __launch_bounds__(kThreads, 3) backward_kernel(BwdArgs a) {
         sz = __fmaf_rn(c, eyz.w, sz);
       }
     }
-    acc_f += (double)sf;
-    acc_l += (double)sl;
+    const float s = label < g.K1 ? g.scale_k[label] : 0.f;  // the class's kernel scale
+    acc_f += (double)s * (double)sf;
+    acc_l += (double)s * (double)sl;
+    if (a.acc_class) add_class_sum(s_cls[wid], label, sf, lane);
     if (a.grad_xyz) {
       for (int o = 16; o > 0; o >>= 1) {
         sx += __shfl_down_sync(0xffffffffu, sx, o);
@@ -221,9 +235,9 @@ __global__ void __launch_bounds__(kThreads, 3) backward_kernel(BwdArgs a) {
         sz += __shfl_down_sync(0xffffffffu, sz, o);
       }
       if (lane == 0) {
-        a.grad_xyz[3 * i] = sx * a.xyz_scale;
-        a.grad_xyz[3 * i + 1] = sy * a.xyz_scale;
-        a.grad_xyz[3 * i + 2] = sz * a.xyz_scale;
+        a.grad_xyz[3 * i] = sx * (s * a.xyz_scale);
+        a.grad_xyz[3 * i + 1] = sy * (s * a.xyz_scale);
+        a.grad_xyz[3 * i + 2] = sz * (s * a.xyz_scale);
       }
     }
     __syncwarp();  // the tables are rewritten for the next point
@@ -235,6 +249,10 @@ __global__ void __launch_bounds__(kThreads, 3) backward_kernel(BwdArgs a) {
   if (lane == 0) {
     atomicAdd(&a.acc[0], acc_f);
     atomicAdd(&a.acc[1], acc_l);
+  }
+  if (a.acc_class) {
+    __syncwarp();
+    if (s_cls[wid][lane] != 0.0) atomicAdd(&a.acc_class[lane], s_cls[wid][lane]);
   }
 }
 
@@ -312,7 +330,9 @@ __global__ void __launch_bounds__(kThreads, 3) backward_fast_kernel(BwdArgs a) {
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int R = a.R, na = 2 * R + 1, m = g.B - 1;
   BwdFastTables& t = s_tab[wid];
+  __shared__ double s_cls[kWarps][32];  // per warp: sum G f by class (only with acc_class)
   if (a.dc->err != 0) return;
+  s_cls[wid][lane] = 0.0;
   // this lane's point of a group and axis (lanes 30, 31 form no rows)
   const int gl = lane / 3, ax = lane - 3 * (lane / 3);
   const int axshift = ax == 0 ? 0 : (ax == 1 ? g.B_shift : 2 * g.B_shift);
@@ -393,8 +413,10 @@ __global__ void __launch_bounds__(kThreads, 3) backward_fast_kernel(BwdArgs a) {
         } else {
           for (int q = lane; q - lane < len; q += 32) bwd_candidate(a, t, pr, __ldg(tab + q), i, sf, sl, sx, sy, sz);
         }
-        acc_f += (double)sf;
-        acc_l += (double)sl;
+        const float s = label < g.K1 ? g.scale_k[label] : 0.f;  // the class's kernel scale
+        acc_f += (double)s * (double)sf;
+        acc_l += (double)s * (double)sl;
+        if (a.acc_class) add_class_sum(s_cls[wid], label, sf, lane);
         if (a.grad_xyz) {
           for (int o = 16; o > 0; o >>= 1) {
             sx += __shfl_down_sync(0xffffffffu, sx, o);
@@ -402,9 +424,9 @@ __global__ void __launch_bounds__(kThreads, 3) backward_fast_kernel(BwdArgs a) {
             sz += __shfl_down_sync(0xffffffffu, sz, o);
           }
           if (lane == 0) {
-            a.grad_xyz[3 * i] = sx * a.xyz_scale;
-            a.grad_xyz[3 * i + 1] = sy * a.xyz_scale;
-            a.grad_xyz[3 * i + 2] = sz * a.xyz_scale;
+            a.grad_xyz[3 * i] = sx * (s * a.xyz_scale);
+            a.grad_xyz[3 * i + 1] = sy * (s * a.xyz_scale);
+            a.grad_xyz[3 * i + 2] = sz * (s * a.xyz_scale);
           }
         }
         __syncwarp();  // the YZ rows and block pointers are rewritten for the next point
@@ -418,6 +440,10 @@ __global__ void __launch_bounds__(kThreads, 3) backward_fast_kernel(BwdArgs a) {
   if (lane == 0) {
     atomicAdd(&a.acc[0], acc_f);
     atomicAdd(&a.acc[1], acc_l);
+  }
+  if (a.acc_class) {
+    __syncwarp();
+    if (s_cls[wid][lane] != 0.0) atomicAdd(&a.acc_class[lane], s_cls[wid][lane]);
   }
 }
 
@@ -465,7 +491,7 @@ cudaError_t launch_grad_scatter(const MapState& m, const int64_t* keys, const fl
 }
 
 cudaError_t launch_backward(const MapState& m, const float4* xyzl, int64_t p, const float* gpool, double* acc_dev,
-                            float* grad_xyz) {
+                            float* grad_xyz, double* acc_class) {
   if (p <= 0) return cudaSuccess;
   BwdArgs a;
   a.g = m.g;
@@ -482,6 +508,7 @@ cudaError_t launch_backward(const MapState& m, const float4* xyzl, int64_t p, co
   a.recip_na = ((1u << 20) + (uint32_t)(2 * m.ctab_R + 1) - 1u) / (uint32_t)(2 * m.ctab_R + 1);
   a.acc = acc_dev;
   a.grad_xyz = grad_xyz;
+  a.acc_class = acc_class;
   a.xyz_scale = (float)(m.prm.sigma0 / m.prm.length_scale);
   a.dc = m.dc;
   if (2 * a.R + 1 <= kBwdAxis - 1) {

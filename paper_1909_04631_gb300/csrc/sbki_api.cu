@@ -164,6 +164,9 @@ sbki_status check_params(const sbki_params* p) {
     return fail(nullptr, SBKI_ERR_INVALID_ARG, "sensor_model must be 0 (kernel inference) or 1 (counting)");
   if (p->sensor_model == 1 && p->accumulate_mode != 0)
     return fail(nullptr, SBKI_ERR_INVALID_ARG, "the counting sensor model needs accumulate_mode 0");
+  for (int k = 0; k <= p->num_classes; ++k)
+    if (!(p->sigma0_scale[k] > 0) || !std::isfinite(p->sigma0_scale[k]))
+      return fail(nullptr, SBKI_ERR_INVALID_ARG, "sigma0_scale[%d] must be finite and > 0", k);
   if (p->sample_capacity < 1 || p->sample_capacity > (1ll << 27))
     return fail(nullptr, SBKI_ERR_INVALID_ARG, "sample_capacity must be in 1..2^27");
   // tiles of training points overlapping one dilated block must stay few
@@ -194,6 +197,11 @@ Geom make_geom(const sbki_params& p) {
   g.l2_lo = (float)(p.length_scale * p.length_scale * (1.0 - band));
   g.l2_hi = (float)(p.length_scale * p.length_scale * (1.0 + band));
   g.sigma0 = (float)p.sigma0;
+  for (int k = 0; k < 32; ++k) {
+    const bool used = k <= p.num_classes;
+    g.sigma0_k[k] = used ? (float)(p.sigma0 * p.sigma0_scale[k]) : 0.f;
+    g.scale_k[k] = used ? (float)p.sigma0_scale[k] : 0.f;
+  }
   g.step = (float)p.free_step;
   g.fast_lim = (float)(2.5 * ds);
   g.res64 = p.res;
@@ -479,6 +487,7 @@ sbki_status sbki_default_params(sbki_params* p) {
   p->num_maps = 1;
   p->cuda_stream = nullptr;
   p->sensor_model = 0;
+  for (int k = 0; k < 32; ++k) p->sigma0_scale[k] = 1.0;
   return SBKI_OK;
 }
 
@@ -1041,7 +1050,7 @@ namespace {
 sbki_status ensure_grad(MapState& m) {
   if (m.gpool) return SBKI_OK;
   CK(&m, dalloc(&m.gpool, (size_t)m.pool_blocks * m.g.K1 * m.g.B3));
-  CK(&m, dalloc(&m.dacc, 4));
+  CK(&m, dalloc(&m.dacc, 4 + 32));
   CK(&m, cudaMemsetAsync(m.gpool, 0, sizeof(float) * (size_t)m.pool_blocks * m.g.K1 * m.g.B3, m.stream));
   return SBKI_OK;
 }
@@ -1146,8 +1155,8 @@ sbki_status sbki_grad_add_alpha(sbki_map* map, const int64_t* keys, const float*
   return SBKI_OK;
 }
 
-sbki_status sbki_backward(sbki_map* map, const float* xyzl, int64_t p, double* grad_l, double* grad_sigma0,
-                          float* grad_xyz) {
+static sbki_status backward_impl(sbki_map* map, const float* xyzl, int64_t p, double* grad_l, double* grad_sigma0,
+                          float* grad_xyz, double* grad_scale) {
   if (!map) return fail(nullptr, SBKI_ERR_INVALID_ARG, "map is NULL");
   MapState& m = map->st;
   if (p < 0 || (p > 0 && !xyzl)) return fail(&m, SBKI_ERR_INVALID_ARG, "bad arguments");
@@ -1171,9 +1180,11 @@ sbki_status sbki_backward(sbki_map* map, const float* xyzl, int64_t p, double* g
     dgx = static_cast<float*>(tf.p[2]);
   }
   CK(&m, cudaMemsetAsync(m.dacc + 1, 0, 2 * sizeof(double), m.stream));
-  CK(&m, launch_backward(m, reinterpret_cast<const float4*>(dxyzl), p, m.gpool, m.dacc + 1, dgx));
+  if (grad_scale) CK(&m, cudaMemsetAsync(m.dacc + 4, 0, 32 * sizeof(double), m.stream));
+  CK(&m, launch_backward(m, reinterpret_cast<const float4*>(dxyzl), p, m.gpool, m.dacc + 1, dgx,
+                         grad_scale ? m.dacc + 4 : nullptr));
   m.launches += 1;
-  double acc[2] = {0.0, 0.0};
+  double acc[2 + 1 + 32] = {};  // sums of G terms, the missed-key word, the per-class sums
   CK(&m, cudaMemcpyAsync(acc, m.dacc + 1, sizeof(acc), cudaMemcpyDeviceToHost, m.stream));
   if (grad_xyz && dgx != grad_xyz && p > 0)
     CK(&m, cudaMemcpyAsync(grad_xyz, dgx, sizeof(float) * 3 * p, cudaMemcpyDeviceToHost, m.stream));
@@ -1183,7 +1194,19 @@ sbki_status sbki_backward(sbki_map* map, const float* xyzl, int64_t p, double* g
   const double l = m.prm.length_scale;
   if (grad_sigma0) *grad_sigma0 = acc[0];
   if (grad_l) *grad_l = m.prm.sigma0 * acc[1] / (l * l);
+  if (grad_scale)
+    for (int k = 0; k < m.g.K1; ++k) grad_scale[k] = m.prm.sigma0 * acc[3 + k];
   return SBKI_OK;
+}
+
+sbki_status sbki_backward(sbki_map* map, const float* xyzl, int64_t p, double* grad_l, double* grad_sigma0,
+                          float* grad_xyz) {
+  return backward_impl(map, xyzl, p, grad_l, grad_sigma0, grad_xyz, nullptr);
+}
+
+sbki_status sbki_backward_scales(sbki_map* map, const float* xyzl, int64_t p, double* grad_scale) {
+  if (!grad_scale) return fail(map ? &map->st : nullptr, SBKI_ERR_INVALID_ARG, "grad_scale is NULL");
+  return backward_impl(map, xyzl, p, nullptr, nullptr, nullptr, grad_scale);
 }
 
 sbki_status sbki_forward_alpha(const sbki_params* params, const float* xyzl, int64_t p, int64_t* keys_out,

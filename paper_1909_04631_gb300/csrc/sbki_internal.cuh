@@ -62,6 +62,8 @@ struct Geom {
   float l, inv_l, l2;      // length scale, 1/l, fp32(l*l)
   float l2_lo, l2_hi;      // l2 (1 -/+ band): outside, the fp32 test decides
   float sigma0;
+  float sigma0_k[32];      // per class: fp32(sigma0 * sigma0_scale[k]) (0 past K)
+  float scale_k[32];       // per class: fp32(sigma0_scale[k]) (0 past K)
   float step;              // fp32(free_step)
   float fast_lim;          // 2.5 ds: cells with |x| above it take the single-pass exact mean
   double res64, l64, l2_64, min_range, max_range;
@@ -165,7 +167,8 @@ struct MapState {
   uint32_t* ctab = nullptr;             // point-major candidate lists [kParts^3][ctab_pad]
   int32_t* clen = nullptr;              // [kParts^3] entries of each list
   float* gpool = nullptr;               // dL/dalpha [pool_blocks][K1][B3] (differentiable form, on first use)
-  double* dacc = nullptr;               // [4]: held-out LL, sum G f, sum G u^4 D d, keys missed (as u64)
+  double* dacc = nullptr;               // [4 + 32]: held-out LL, sum s G f, sum s G u^4 D d, keys missed (as
+                                        // u64), then sum G f per class
   int ctab_pad = 0, ctab_R = 0;
   bool profiling = false;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -320,7 +323,7 @@ cudaError_t launch_heldout(const MapState& m, const float* xyz, const int32_t* l
 cudaError_t launch_grad_scatter(const MapState& m, const int64_t* keys, const float* grad, int64_t count, float* gpool,
                                 unsigned long long* missed_dev);
 cudaError_t launch_backward(const MapState& m, const float4* xyzl, int64_t p, const float* gpool, double* acc_dev,
-                            float* grad_xyz);
+                            float* grad_xyz, double* acc_class);
 size_t accumulate_smem_bytes(const Geom& g);
 
 // readoff.cu

@@ -25,7 +25,7 @@ EXPORTED = ["sbki_default_params", "sbki_create_map", "sbki_destroy_map", "sbki_
             "sbki_voxel_count", "sbki_export", "sbki_profile", "sbki_profile_read", "sbki_kernel_values", "sbki_last_error", "sbki_status_string",
             "sbki_training_set_noalloc", "sbki_grad_clear", "sbki_heldout_loglik", "sbki_grad_add_alpha",
             "sbki_backward", "sbki_forward_alpha", "sbki_grad", "sbki_insert_batch", "sbki_select_map",
-            "sbki_get_tuning", "sbki_set_tuning", "sbki_import", "sbki_selftest_bounded_wait"]
+            "sbki_get_tuning", "sbki_set_tuning", "sbki_import", "sbki_selftest_bounded_wait", "sbki_backward_scales"]
 
 
 class SbkiError(RuntimeError):
@@ -40,7 +40,7 @@ class Params(C.Structure):
                [("num_classes", C.c_int32), ("block_edge", C.c_int32), ("pool_blocks", C.c_int64),
                 ("sample_capacity", C.c_int64), ("track_pairs", C.c_int32), ("device", C.c_int32),
                 ("accumulate_mode", C.c_int32), ("num_maps", C.c_int32),
-                ("cuda_stream", C.c_void_p), ("sensor_model", C.c_int32)]
+                ("cuda_stream", C.c_void_p), ("sensor_model", C.c_int32), ("sigma0_scale", C.c_double * 32)]
 
 
 class Scan(C.Structure):
@@ -114,6 +114,7 @@ def load(build_if_missing: bool = True):
         L.sbki_heldout_loglik.argtypes = [vp, vp, vp, i64, i32, P(C.c_double)]
         L.sbki_grad_add_alpha.argtypes = [vp, vp, vp, i64, P(i64)]
         L.sbki_backward.argtypes = [vp, vp, i64, P(C.c_double), P(C.c_double), vp]
+        L.sbki_backward_scales.argtypes = [vp, vp, i64, vp]
         L.sbki_forward_alpha.argtypes = [P(Params), vp, i64, vp, vp, i64, P(i64)]
         L.sbki_grad.argtypes = [P(Params), vp, i64, vp, vp, i64, P(C.c_double), P(C.c_double), vp]
         L.sbki_voxel_count.argtypes = [vp, P(i64)]
@@ -133,19 +134,32 @@ def load(build_if_missing: bool = True):
                   "sbki_export", "sbki_training_set_noalloc", "sbki_grad_clear", "sbki_heldout_loglik",
                   "sbki_grad_add_alpha", "sbki_backward", "sbki_forward_alpha", "sbki_grad", "sbki_insert_batch",
                   "sbki_select_map", "sbki_get_tuning", "sbki_set_tuning", "sbki_import",
-                  "sbki_selftest_bounded_wait"):
+                  "sbki_selftest_bounded_wait", "sbki_backward_scales"):
             getattr(L, f).restype = C.c_int
         _lib = L
         return L
+
+
+def set_param(p: Params, k: str, v) -> None:
+    """p.k = v; sigma0_scale takes a sequence of per-class scales (classes
+    0..len-1; the remaining entries keep their values)."""
+    if not hasattr(p, k):
+        raise TypeError("unknown parameter %r" % k)
+    if k == "sigma0_scale":
+        vals = [float(x) for x in v]
+        if len(vals) > 32:
+            raise ValueError("at most 32 classes")
+        for i, x in enumerate(vals):
+            p.sigma0_scale[i] = x
+        return
+    setattr(p, k, v)
 
 
 def default_params(**kw) -> Params:
     p = Params()
     load().sbki_default_params(C.byref(p))
     for k, v in kw.items():
-        if not hasattr(p, k):
-            raise TypeError("unknown parameter %r" % k)
-        setattr(p, k, v)
+        set_param(p, k, v)
     return p
 
 
@@ -270,7 +284,7 @@ class Map:
         self.params = Params.from_buffer_copy(params) if params is not None else default_params(**kw)
         if params is not None and kw:
             for k, v in kw.items():
-                setattr(self.params, k, v)
+                set_param(self.params, k, v)
         if stream is not None:
             self.params.cuda_stream = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
         self.K1 = self.params.num_classes + 1
@@ -483,6 +497,15 @@ class Map:
         if gx is not None and not hasattr(gx, "data_ptr"):
             gx = gx[:p]
         return gl.value, gs.value, gx
+
+    def backward_scales(self, xyzl):
+        """dL/d sigma0_scale[k] for k = 0..K (numpy float64) for the inserted
+        training set xyzl [p,4]."""
+        x = _as(xyzl, np.float32, 4)
+        xp, keep = _ptr(x)
+        out = np.zeros(32, np.float64)
+        self._check(self._L.sbki_backward_scales(self._h, xp, x.shape[0], out.ctypes.data_as(C.c_void_p)))
+        return out[: self.K1].copy()
 
     def import_(self, keys, alpha):
         """Restore exported contents (keys [n,3], alpha [n,K+1] with prior) into the selected map."""

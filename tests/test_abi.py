@@ -85,7 +85,8 @@ def test_create_map_rejects_bad_params():
     from paper_1909_04631_gb300 import sbki
     for bad in (dict(res=0.0), dict(block_edge=6), dict(num_classes=40), dict(max_range=float("inf")),
                 dict(length_scale=5.0), dict(alpha0=0.0), dict(sensor_model=2),
-                dict(sensor_model=1, accumulate_mode=1)):
+                dict(sensor_model=1, accumulate_mode=1), dict(sigma0_scale=[1.0, 0.0]),
+                dict(sigma0_scale=[1.0, float("nan")])):
         with pytest.raises(sbki.SbkiError) as e:
             sbki.Map(sbki.default_params(**bad))
         assert e.value.status == sbki.ERR_INVALID_ARG

@@ -170,3 +170,34 @@ def test_autograd_functions(sb, diff_case):
     (w * alpha).sum().backward()
     expect = float(((w.double() * (alpha.double() - c["prm"]["alpha0"])).sum()) / c["prm"]["sigma0"])
     assert abs(float(s2.grad) - expect) <= 1e-4 * float((w.abs().double() * alpha.double()).sum())
+
+
+def test_gradient_with_class_scales_matches_oracle(sb, orc, diff_case):
+    """Per-class kernel scales (class k's kernel sigma0 s_k f): LL, dLL/dl,
+    dLL/dsigma0, dLL/dxyz and dLL/ds_k against the oracle."""
+    c = diff_case
+    K1 = c["prm"]["num_classes"] + 1
+    scale = [0.6 + 0.15 * k for k in range(K1)]
+    p = _params(sb, c["prm"])
+    sb.set_param(p, "sigma0_scale", scale)
+    xyzl = np.concatenate([c["xyz"], c["lab"][:, None].astype(np.float32)], 1)
+    with sb.Map(p) as m:
+        m.insert_training(c["xyz"], c["lab"])
+        m.grad_clear()
+        ll = m.heldout_loglik(c["held"], c["held_lab"], grad=True)
+        gl, gs, gx = m.backward(xyzl)
+        gsc = m.backward_scales(xyzl)
+    op = orc.params(**dict(c["prm"], sigma0_scale=scale))
+    x64 = c["xyz"].astype(np.float64)
+    oll, ogl, ogs, ogx = orc.heldout_grad(op, x64, c["lab"], c["held"], c["held_lab"])
+    _, ogsc = orc.heldout_grad_scale(op, x64, c["lab"], c["held"], c["held_lab"])
+    assert abs(ll - oll) <= 1e-5 * abs(oll)
+    assert abs(gl - ogl) <= 1e-4 * abs(ogl) and abs(gs - ogs) <= 1e-4 * abs(ogs)
+    err = np.abs(gx.astype(np.float64) - ogx)
+    assert np.linalg.norm(err) <= 1e-4 * np.linalg.norm(ogx)
+    used = np.abs(ogsc) > 0
+    assert used.sum() >= 3
+    np.testing.assert_allclose(gsc[used], ogsc[used], rtol=1e-4)
+    assert np.all(gsc[~used] == 0)
+    # the scaling identity holds on the GPU too
+    assert float(np.dot(scale, gsc)) == pytest.approx(c["prm"]["sigma0"] * gs, rel=1e-6)
