@@ -89,6 +89,8 @@ def oracle_rate(scans, n_steps, nsec=8, progress=None):
         m.insert_scan(pts, lab, sc["pose"])
         t_total += time.perf_counter() - t0
     _, _, pc = m.export()
+    if t_total <= 0.0:
+        return 0.0, 0.0, 0.0
     return (n_steps / nsec) / t_total, float(pc.sum()) / t_total, t_total
 
 
@@ -373,7 +375,8 @@ def run_reference(args, rank, world):
     scans = generate_scans(0, max(1, math.ceil((args.warmup + args.steps) / 8)), args.workers)
     nsec = 8
     # warm-up steps (untimed) then timed steps, each one azimuth sector (1/8 scan)
-    oracle_rate(scans, args.warmup, nsec)
+    if args.warmup > 0:
+        oracle_rate(scans, args.warmup, nsec)
     rate, prate, secs = oracle_rate(scans, args.steps, nsec)
     cores = 1
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "scans/s", "n_gpus": args.gpus,
