@@ -71,14 +71,18 @@ def destinations(xyz, res: float, length_scale: float, block_edge: int, world: i
 
 
 def exchange(xyzl, dest_point, dest_rank, rank: int, world: int, device="cpu"):
-    """Sends row dest_point[j] of xyzl [n,4] (float32: x, y, z, label) to rank
-    dest_rank[j] and returns every row this rank received, its own included,
-    as a float32 tensor on `device` (the halo all-to-all; "cuda" tensors for
-    the NCCL backend).  Counts go first (one all_gather), then one
-    send/receive pair per peer."""
+    """Sends row dest_point[j] of xyzl [n,w] (float32; training points are
+    x, y, z, label) to rank dest_rank[j] and returns every row this rank
+    received, ordered by source rank and, within a source, by destination
+    order, its own included, as a float32 tensor on `device` (the halo
+    all-to-all; "cuda" tensors for the NCCL backend).  Counts go first (one
+    all_gather), then one send/receive pair per peer."""
     import torch
     import torch.distributed as dist
-    rows = np.asarray(xyzl, np.float32).reshape(-1, 4)
+    rows = np.asarray(xyzl, np.float32)
+    if rows.ndim != 2:
+        raise ValueError("rows must be a 2-D array")
+    width = rows.shape[1]
     order = np.argsort(dest_rank, kind="stable")
     dp, dr = dest_point[order], dest_rank[order]
     counts = np.bincount(dr, minlength=world).astype(np.int64)
@@ -87,7 +91,8 @@ def exchange(xyzl, dest_point, dest_rank, rank: int, world: int, device="cpu"):
                 for r in range(world)]
     all_counts = [torch.zeros(world, dtype=torch.int64, device=device) for _ in range(world)]
     dist.all_gather(all_counts, torch.from_numpy(counts).to(device))
-    incoming = [torch.empty((int(all_counts[r][rank]), 4), dtype=torch.float32, device=device) for r in range(world)]
+    incoming = [torch.empty((int(all_counts[r][rank]), width), dtype=torch.float32, device=device)
+                for r in range(world)]
     incoming[rank] = outgoing[rank]
     reqs = []
     for r in range(world):
@@ -134,6 +139,42 @@ class ShardedMap:
     def owns_voxels(self, keys) -> np.ndarray:
         k = np.asarray(keys, np.int64).reshape(-1, 3)
         return owner(np.floor_divide(k, self.B), self.world) == self.rank
+
+    def query(self, xyz, query_fields=("label", "p_occ")):
+        """Read-off at this rank's world points: each point goes to the owner of
+        its voxel's block, which answers from its map; every rank calls this
+        together (collective).  Returns a dict of the query_fields, float64
+        (labels as integers in float), in the order of xyz."""
+        x = np.asarray(xyz, np.float32).reshape(-1, 3)
+        dr = query_owner(x, self.res, self.B, self.world)
+        dp = np.arange(len(x))
+        tagged = np.concatenate([x, dp[:, None].astype(np.float32)], 1)  # exact below 2^24 points
+        if len(x) >= (1 << 24):
+            raise ValueError("at most 2^24 query points per call")
+        got = exchange(tagged, dp, dr, self.rank, self.world).numpy()
+        # the answers go back to where each point came from
+        src_counts = self._source_counts(len(dp), dr)
+        src = np.repeat(np.arange(self.world), src_counts)
+        ans = self.local.query(got[:, :3]) if len(got) else {f: np.zeros(0) for f in query_fields}
+        back = np.concatenate([got[:, 3:4]] + [np.asarray(ans[f], np.float64).reshape(-1, 1).astype(np.float32)
+                                               for f in query_fields], 1)
+        ret = exchange(back, np.arange(len(back)), src, self.rank, self.world).numpy()
+        out = {}
+        idx = ret[:, 0].astype(np.int64)
+        for j, f in enumerate(query_fields):
+            v = np.empty(len(x))
+            v[idx] = ret[:, 1 + j]
+            out[f] = v
+        return out
+
+    def _source_counts(self, n, dest_rank):
+        """How many query points each rank sent to this one (one all_gather)."""
+        import torch
+        import torch.distributed as dist
+        counts = torch.from_numpy(np.bincount(dest_rank, minlength=self.world).astype(np.int64))
+        every = [torch.zeros(self.world, dtype=torch.int64) for _ in range(self.world)]
+        dist.all_gather(every, counts)
+        return np.array([int(e[self.rank]) for e in every], np.int64)
 
     def export(self):
         """(keys, alpha, pairs) of the voxels of the blocks this rank owns."""

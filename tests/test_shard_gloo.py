@@ -45,6 +45,11 @@ def test_owner_is_a_balanced_function_of_the_block():
         shard.touched_blocks(np.zeros((1, 3)), 0.1, 0.9, 8)
 
 
+def _queries():
+    rng = np.random.default_rng(47)
+    return rng.uniform(-1.5, 1.7, size=(500, 3)).astype(np.float32)
+
+
 def _free_port():
     with socket.socket() as s:
         s.bind(("127.0.0.1", 0))
@@ -63,8 +68,11 @@ def _rank(rank, world, port, out):
                               rank, world)
         received = sm.insert_training(xyz[mine], lab[mine])
         keys, alpha, pairs = sm.export()
+        # read-off at this rank's own query points, answered by the owners (rank 1 asks nothing)
+        q = _queries() if rank == 0 else np.zeros((0, 3), np.float32)
+        ans = sm.query(q)
         parts = [None] * world
-        dist.all_gather_object(parts, (keys, alpha, pairs, received))
+        dist.all_gather_object(parts, (keys, alpha, pairs, received, ans))
         out[rank] = parts if rank == 0 else None
     finally:
         dist.destroy_process_group()
@@ -95,3 +103,9 @@ def test_two_ranks_own_the_single_map(orc):
     np.testing.assert_array_equal(keys, skeys)      # every block owned exactly once
     np.testing.assert_array_equal(pairs, spairs)
     np.testing.assert_allclose(alpha, salpha, rtol=1e-12)  # FP64 sums in another order
+    # routed queries: the owners' answers equal the single map's read-off
+    ans = parts[0][4]
+    want = single.query(_queries())
+    np.testing.assert_array_equal(ans["label"], want["label"])
+    np.testing.assert_allclose(ans["p_occ"], want["p_occ"].astype(np.float32), rtol=1e-6)
+    assert len(parts[1][4]["label"]) == 0
