@@ -34,22 +34,23 @@ class OrcParams(C.Structure):
     _fields_ = [(n, C.c_double) for n in ("res", "length_scale", "sigma0", "alpha0", "free_step", "ds_res",
                                           "min_range", "max_range", "free_thresh", "occ_thresh")] + \
                [("num_classes", C.c_int32), ("block_edge", C.c_int32), ("sensor_model", C.c_int32),
-                ("sigma0_scale", C.c_double * 32)]
+                ("sigma0_scale", C.c_double * 32), ("association", C.c_int32)]
 
 
 def params(res=0.1, length_scale=0.3, sigma0=0.1, alpha0=0.001, free_step=0.3, ds_res=None, min_range=0.0,
            max_range=1e30, free_thresh=0.47, occ_thresh=0.6, num_classes=10, block_edge=8, sensor_model=0,
-           sigma0_scale=None, **_ignored):
+           sigma0_scale=None, association=0, **_ignored):
     """Parameter block; defaults follow Table (parameters) and Sec. V-A of the paper.
     sensor_model 0: kernel inference, Eq. (alpha_kernel); 1: counting model, Eq. (alpha).
-    sigma0_scale: per-class multipliers of sigma0 (classes 0..K; default all 1)."""
+    sigma0_scale: per-class multipliers of sigma0 (classes 0..K; default all 1).
+    association 0: every voxel within l (exact); 1: the extended block (reading K14)."""
     sc = [1.0] * 32
     if sigma0_scale is not None:
         for k, v in enumerate(sigma0_scale):
             sc[k] = float(v)
     return OrcParams(res, length_scale, sigma0, alpha0, free_step, res if ds_res is None else ds_res, min_range,
                      max_range, free_thresh, occ_thresh, num_classes, block_edge, sensor_model,
-                     (C.c_double * 32)(*sc))
+                     (C.c_double * 32)(*sc), association)
 
 
 _P = C.POINTER
@@ -89,6 +90,7 @@ def lib():
             L.orc_map_alpha_at.argtypes = [vp, vp, i64, vp, vp]
             L.orc_alpha_bruteforce.argtypes = [_P(OrcParams), vp, vp, i64, vp, i64, vp, vp]
             L.orc_map_query.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp]
+            L.orc_alpha_at_points.argtypes = [_P(OrcParams), vp, vp, i64, vp, i64, vp]
             L.orc_heldout_grad.restype = f64
             L.orc_heldout_grad.argtypes = [_P(OrcParams), vp, vp, i64, vp, vp, i64, vp, vp, vp]
             L.orc_heldout_grad_scale.restype = f64
@@ -176,6 +178,15 @@ def alpha_bruteforce(p, xyz, labels, keys):
     lib().orc_alpha_bruteforce(C.byref(p), _ptr(xyz), _ptr(lab), len(xyz), _ptr(keys), len(keys), _ptr(alpha),
                                _ptr(pairs))
     return alpha, pairs
+
+
+def alpha_at_points(p, xyz, labels, pts):
+    """Eq. (alpha_kernel) at arbitrary world points pts [q,3] (FP64) from a training set: alpha [q,K+1]."""
+    xyz, lab = _f32(xyz).reshape(-1, 3), _i32(labels)
+    pts = _f64(pts).reshape(-1, 3)
+    alpha = np.empty((len(pts), p.num_classes + 1), np.float64)
+    lib().orc_alpha_at_points(C.byref(p), _ptr(xyz), _ptr(lab), len(xyz), _ptr(pts), len(pts), _ptr(alpha))
+    return alpha
 
 
 def heldout_ll(p, xyz64, labels, held_xyz, held_labels):

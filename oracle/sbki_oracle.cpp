@@ -42,10 +42,16 @@
 //   K13 Per-class kernel scale (the paper names class-dependent signal
 //       variance as the way to let sigma0 matter): class k's kernel is
 //       sigma0 * sigma0_scale[k] * f(d/l); all scales 1 is Eq. (kernel) as printed.
+//   K14 Extended-block association (Sec. IV, the paper's software): a voxel of
+//       block b takes the training points whose own voxel (K6 key) lies in b
+//       or in one of b's six face neighbours; pairs from edge or corner
+//       neighbours are left out even when d < l.  association = 0 is the
+//       exact rule K5, 1 this one.
 #include <algorithm>
 #include <array>
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <unordered_map>
@@ -60,6 +66,7 @@ struct Params {
   int32_t block_edge;
   int32_t sensor_model;  // 0: kernel inference, Eq. (alpha_kernel); 1: counting, Eq. (alpha)
   double sigma0_scale[32];  // reading K13: class k's kernel scale is sigma0 * sigma0_scale[k]
+  int32_t association;      // reading K14: 0 exact (K5), 1 extended block (face neighbours)
 };
 
 const double kPi = 3.14159265358979323846;
@@ -304,6 +311,7 @@ void accumulate(Map& m, const std::vector<Sample>& train) {
   const int64_t R = (int64_t)std::ceil(l / p.res) + 1;
   for (const Sample& s : train) {
     int64_t kx = voxel_index(s.x, inv_res), ky = voxel_index(s.y, inv_res), kz = voxel_index(s.z, inv_res);
+    const Key3 pb = {floor_div(kx, B), floor_div(ky, B), floor_div(kz, B)};  // the point's block (K14)
     for (int64_t a = -R; a <= R; ++a)
       for (int64_t b = -R; b <= R; ++b)
         for (int64_t c = -R; c <= R; ++c) {
@@ -316,8 +324,11 @@ void accumulate(Map& m, const std::vector<Sample>& train) {
           d2 = d2 + ey * ey;
           d2 = d2 + ez * ez;
           if (!(d2 < l2)) continue;
-          double kval = p.sigma0 * p.sigma0_scale[s.label] * kernel_f(std::sqrt(d2) / l);
           Key3 bk = {floor_div(vx, B), floor_div(vy, B), floor_div(vz, B)};
+          if (p.association == 1 &&
+              std::llabs(bk[0] - pb[0]) + std::llabs(bk[1] - pb[1]) + std::llabs(bk[2] - pb[2]) > 1)
+            continue;  // K14: only the voxel's own block and its face neighbours
+          double kval = p.sigma0 * p.sigma0_scale[s.label] * kernel_f(std::sqrt(d2) / l);
           Block& blk = m.blocks[bk];
           if (blk.inc.empty()) {
             blk.inc.assign((size_t)(B * B * B * K1), 0.0);
@@ -403,6 +414,7 @@ typedef struct {
   double res, length_scale, sigma0, alpha0, free_step, ds_res, min_range, max_range, free_thresh, occ_thresh;
   int32_t num_classes, block_edge, sensor_model;
   double sigma0_scale[32];
+  int32_t association;
 } orc_params;
 
 static Params conv(const orc_params* q) {
@@ -590,6 +602,28 @@ void orc_alpha_bruteforce(const orc_params* q, const float* xyz, const int32_t* 
       ++pc;
     }
     if (pairs) pairs[v] = pc;
+  }
+}
+
+// Eq. (alpha_kernel) at arbitrary query points (Sec. IV: the continuous model
+// can be queried at any resolution): alpha [nq,K+1] = alpha_0 + sum over all
+// training points within l of sigma0 s_k f(d/l) (exact association).
+void orc_alpha_at_points(const orc_params* q, const float* xyz, const int32_t* lab, int64_t n, const double* pts,
+                         int64_t nq, double* alpha) {
+  Params p = conv(q);
+  const int K1 = nclass(p);
+  const double l = p.length_scale, l2 = l * l;
+  for (int64_t v = 0; v < nq; ++v) {
+    for (int c = 0; c < K1; ++c) alpha[v * K1 + c] = p.alpha0;
+    for (int64_t i = 0; i < n; ++i) {
+      double ex = pts[3 * v] - (double)xyz[3 * i], ey = pts[3 * v + 1] - (double)xyz[3 * i + 1],
+             ez = pts[3 * v + 2] - (double)xyz[3 * i + 2];
+      double d2 = ex * ex;
+      d2 = d2 + ey * ey;
+      d2 = d2 + ez * ez;
+      if (!(d2 < l2)) continue;
+      alpha[v * K1 + lab[i]] += p.sigma0 * p.sigma0_scale[lab[i]] * kernel_f(std::sqrt(d2) / l);
+    }
   }
 }
 

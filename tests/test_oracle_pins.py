@@ -507,6 +507,72 @@ def test_gradient_in_class_scales(orc):
     assert float(np.dot(scale, gsc)) == pytest.approx(0.8 * gs, rel=1e-10)
 
 
+def test_extended_block_association_against_bruteforce(orc):
+    """Reading K14: with association 1 a voxel takes only the points whose
+    voxel lies in its block or a face neighbour; a numpy all-pairs sum with
+    that rule, and the exact map minus the left-out (edge and corner
+    neighbour) pairs."""
+    rng = np.random.default_rng(31)
+    B, res, l = 4, 0.1, 0.3
+    xyz = (np.round(rng.uniform(-0.6, 0.6, size=(120, 3)) / (B * res)) * (B * res)
+           + rng.uniform(-0.12, 0.12, size=(120, 3))).astype(np.float32)  # around block corners and edges
+    lab = rng.integers(0, 3, size=120).astype(np.int32)
+    base = dict(res=res, length_scale=l, sigma0=0.5, num_classes=2, block_edge=B)
+    ext = orc.OracleMap(orc.params(**base, association=1))
+    ext.insert_training(xyz, lab)
+    keys, alpha, pairs = ext.export()
+    vox = np.floor(xyz * np.float32(1 / res)).astype(np.int64)
+    pblk = np.floor_divide(vox, B)
+    c = (keys + 0.5) * res
+    kb = np.floor_divide(keys, B)
+    x64 = xyz.astype(np.float64)
+    want = np.zeros((len(keys), 3))
+    npairs = np.zeros(len(keys), np.int64)
+    for i in range(len(xyz)):
+        e = c - x64[i]
+        d2 = (e[:, 0] * e[:, 0] + e[:, 1] * e[:, 1]) + e[:, 2] * e[:, 2]
+        face = np.abs(kb - pblk[i]).sum(1) <= 1
+        sel = (d2 < l * l) & face
+        want[sel, lab[i]] += 0.5 * np.array([orc.kernel_f(math.sqrt(v) / l) for v in d2[sel]])
+        npairs[sel] += 1
+    np.testing.assert_allclose(alpha - 0.001, want, rtol=1e-12, atol=1e-15)
+    np.testing.assert_array_equal(pairs, npairs)
+    # the exact map has every pair; the extended one drops some here (points near edges and corners)
+    exact = orc.OracleMap(orc.params(**base))
+    exact.insert_training(xyz, lab)
+    ea, ep = exact.alpha_at(keys)
+    assert np.all(ep >= pairs) and ep.sum() > pairs.sum()
+
+
+def test_point_queries_against_bruteforce_and_voxel_centres(orc):
+    """Eq. (alpha_kernel) at arbitrary points: a numpy all-pairs sum; at voxel
+    centres it equals the map's alpha; it is continuous (f has zero slope at
+    r = 1, so alpha is Lipschitz in the query point)."""
+    rng = np.random.default_rng(33)
+    xyz = rng.uniform(-0.5, 0.5, size=(90, 3)).astype(np.float32)
+    lab = rng.integers(0, 4, size=90).astype(np.int32)
+    scale = [1.0, 0.5, 2.0, 1.5]
+    p = orc.params(res=0.1, length_scale=0.3, sigma0=0.9, num_classes=3, sigma0_scale=scale)
+    pts = rng.uniform(-0.7, 0.7, size=(40, 3))
+    got = orc.alpha_at_points(p, xyz, lab, pts)
+    x64 = xyz.astype(np.float64)
+    for q in range(len(pts)):
+        e = pts[q] - x64
+        d = np.sqrt((e[:, 0] * e[:, 0] + e[:, 1] * e[:, 1]) + e[:, 2] * e[:, 2])
+        want = np.full(4, p.alpha0)
+        for i in np.nonzero(d < 0.3)[0]:
+            want[lab[i]] += 0.9 * scale[lab[i]] * orc.kernel_f(d[i] / 0.3)
+        np.testing.assert_allclose(got[q], want, rtol=1e-12)
+    m = orc.OracleMap(p)
+    m.insert_training(xyz, lab)
+    keys, alpha, _ = m.export()
+    sel = rng.choice(len(keys), size=60, replace=False)
+    np.testing.assert_allclose(orc.alpha_at_points(p, xyz, lab, (keys[sel] + 0.5) * 0.1), alpha[sel], rtol=1e-12)
+    step = 1e-6 * rng.normal(size=pts.shape)
+    diff = np.abs(orc.alpha_at_points(p, xyz, lab, pts + step) - got).sum(1)
+    assert np.all(diff <= 90 * 0.9 * 2.0 * 4.0 / 0.3 * np.linalg.norm(step, axis=1))
+
+
 def test_gradient_sigma0_and_euler_identities(orc):
     """alpha - alpha0 is linear in sigma0; alpha_v depends on (x_i - c_v)/l only,
     so l dLL/dl + sum_i (x_i - c_v) . dLL/dx_i = 0 when every held-out point is
