@@ -91,6 +91,12 @@ def lib():
             L.orc_alpha_bruteforce.argtypes = [_P(OrcParams), vp, vp, i64, vp, i64, vp, vp]
             L.orc_map_query.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp, vp]
             L.orc_alpha_at_points.argtypes = [_P(OrcParams), vp, vp, i64, vp, i64, vp]
+            L.orc_soft_training_set.restype = i64
+            L.orc_soft_training_set.argtypes = [_P(OrcParams), vp, vp, i64, vp, vp, vp, i64, vp]
+            L.orc_map_insert_training_soft.restype = C.c_int
+            L.orc_map_insert_training_soft.argtypes = [vp, vp, vp, i64]
+            L.orc_map_insert_scan_soft.restype = C.c_int
+            L.orc_map_insert_scan_soft.argtypes = [vp, vp, vp, i64, vp, vp]
             L.orc_heldout_grad.restype = f64
             L.orc_heldout_grad.argtypes = [_P(OrcParams), vp, vp, i64, vp, vp, i64, vp, vp, vp]
             L.orc_heldout_grad_scale.restype = f64
@@ -180,6 +186,19 @@ def alpha_bruteforce(p, xyz, labels, keys):
     return alpha, pairs
 
 
+def soft_training_set(p, points, probs, pose):
+    """Steps a1..a3 with soft labels (reading K15): probs [n,K] over classes 1..K.
+    Returns (xyz float32 [P,3], weights float32 [P,K+1], stats dict)."""
+    pts, pr, T = _f32(points).reshape(-1, 3), _f32(probs).reshape(len(points), -1), _f64(pose).reshape(16)
+    K1 = p.num_classes + 1
+    st = np.zeros(3, np.int64)
+    n = lib().orc_soft_training_set(C.byref(p), _ptr(pts), _ptr(pr), len(pts), _ptr(T), None, None, 0, _ptr(st))
+    xyz = np.empty((max(n, 1), 3), np.float32)
+    w = np.empty((max(n, 1), K1), np.float32)
+    lib().orc_soft_training_set(C.byref(p), _ptr(pts), _ptr(pr), len(pts), _ptr(T), _ptr(xyz), _ptr(w), n, _ptr(st))
+    return xyz[:n], w[:n], dict(hits=int(st[0]), free=int(st[1]), train=int(st[2]))
+
+
 def alpha_at_points(p, xyz, labels, pts):
     """Eq. (alpha_kernel) at arbitrary world points pts [q,3] (FP64) from a training set: alpha [q,K+1]."""
     xyz, lab = _f32(xyz).reshape(-1, 3), _i32(labels)
@@ -241,6 +260,19 @@ class OracleMap:
         xyz, lab = _f32(xyz).reshape(-1, 3), _i32(labels)
         if lib().orc_map_insert_training(self._h, _ptr(xyz), _ptr(lab), len(xyz)) != 0:
             raise ValueError("label out of range")
+
+    def insert_training_soft(self, xyz, weights):
+        """Eq. (alpha_kernel) with weight vectors (reading K15): xyz [n,3], weights [n,K+1]."""
+        xyz, w = _f32(xyz).reshape(-1, 3), _f32(weights).reshape(-1, self.K1)
+        lib().orc_map_insert_training_soft(self._h, _ptr(xyz), _ptr(w), len(xyz))
+
+    def insert_scan_soft(self, points, probs, pose):
+        """A scan with soft labels (reading K15): probs [n,K] over classes 1..K."""
+        pts, T = _f32(points).reshape(-1, 3), _f64(pose).reshape(16)
+        pr = _f32(probs).reshape(len(pts), self.K1 - 1)
+        st = np.zeros(3, np.int64)
+        lib().orc_map_insert_scan_soft(self._h, _ptr(pts), _ptr(pr), len(pts), _ptr(T), _ptr(st))
+        return dict(hits=int(st[0]), free=int(st[1]), train=int(st[2]))
 
     def block_keys(self):
         n = lib().orc_map_num_blocks(self._h)

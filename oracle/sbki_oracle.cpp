@@ -47,6 +47,13 @@
 //       or in one of b's six face neighbours; pairs from edge or corner
 //       neighbours are left out even when d < l.  association = 0 is the
 //       exact rule K5, 1 this one.
+//   K15 Soft labels (next row f1): a hit carries a probability vector over the
+//       occupied classes 1..K instead of one label (free samples stay class 0).
+//       Downsampling groups by (cell, most probable class, ties to the lowest),
+//       so one-hot vectors give the groups of K4; the representative is the K4
+//       centroid with, per class, the exact mean of the members' weights
+//       rounded once to FP32.  A training point adds sigma0 s_k f(d/l) w^k into
+//       every class k (Eq. alpha_kernel with y_i = w).
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -371,6 +378,105 @@ void update(Map& m, const std::vector<Sample>& train) {
     accumulate(m, train);
 }
 
+// ---------------------------------------------------------------- soft labels (reading K15)
+struct SoftSample {
+  float x, y, z;
+  std::vector<float> w;  // K+1 class weights
+};
+
+int argmax_lowest(const std::vector<float>& w) {
+  int best = 0;
+  for (int c = 1; c < (int)w.size(); ++c)
+    if (w[c] > w[best]) best = c;
+  return best;
+}
+
+// Steps a1-a3 with probability vectors probs [n, K] over the occupied classes.
+void soft_training_set(const Params& p, const float* pts, const float* probs, int64_t n, const double* T,
+                       std::vector<SoftSample>& train, int64_t* stats) {
+  const int K1 = nclass(p);
+  std::vector<std::array<float, 3>> world;
+  std::vector<int64_t> kept;
+  transform_validate(p, pts, n, T, world, kept);
+  // a2 on one-label samples (the sample positions do not depend on the label),
+  // then the weights: the hit's vector for hits, class 0 for free samples
+  std::vector<int32_t> idx(kept.size());
+  for (size_t i = 0; i < kept.size(); ++i) idx[i] = (int32_t)i + 1;  // a stand-in label > 0 marks hits
+  std::vector<Sample> samples;
+  int64_t nf = 0;
+  build_samples(p, world, idx, T, samples, &nf);
+  const float inv_ds = (float)(1.0 / p.ds_res);
+  struct Members {
+    std::vector<float> x, y, z;
+    std::vector<std::vector<float>> w;  // per class
+  };
+  std::map<std::array<int64_t, 4>, Members> cells;
+  for (const Sample& s : samples) {
+    std::vector<float> w((size_t)K1, 0.0f);
+    if (s.label > 0) {
+      const int64_t src = kept[(size_t)(s.label - 1)];
+      for (int c = 1; c < K1; ++c) w[c] = probs[src * (K1 - 1) + (c - 1)];
+    } else {
+      w[0] = 1.0f;
+    }
+    std::array<int64_t, 4> k = {voxel_index(s.x, inv_ds), voxel_index(s.y, inv_ds), voxel_index(s.z, inv_ds),
+                                (int64_t)argmax_lowest(w)};
+    Members& m = cells[k];
+    m.x.push_back(s.x);
+    m.y.push_back(s.y);
+    m.z.push_back(s.z);
+    if (m.w.empty()) m.w.assign((size_t)K1, {});
+    for (int c = 0; c < K1; ++c) m.w[c].push_back(w[c]);
+  }
+  for (auto& kv : cells) {
+    const Members& m = kv.second;
+    SoftSample t{exact_mean_f32(m.x), exact_mean_f32(m.y), exact_mean_f32(m.z), std::vector<float>((size_t)K1)};
+    for (int c = 0; c < K1; ++c) t.w[c] = exact_mean_f32(m.w[c]);
+    train.push_back(t);
+  }
+  if (stats) {
+    stats[0] = (int64_t)kept.size();
+    stats[1] = nf;
+    stats[2] = (int64_t)train.size();
+  }
+}
+
+// Step a5 with weight vectors: every class k gets sigma0 s_k f(d/l) w^k.
+void accumulate_soft(Map& m, const std::vector<SoftSample>& train) {
+  const Params& p = m.p;
+  const int K1 = nclass(p);
+  const int64_t B = p.block_edge;
+  const float inv_res = (float)(1.0 / p.res);
+  const double l = p.length_scale, l2 = l * l;
+  const int64_t R = (int64_t)std::ceil(l / p.res) + 1;
+  for (const SoftSample& s : train) {
+    int64_t kx = voxel_index(s.x, inv_res), ky = voxel_index(s.y, inv_res), kz = voxel_index(s.z, inv_res);
+    for (int64_t a = -R; a <= R; ++a)
+      for (int64_t b = -R; b <= R; ++b)
+        for (int64_t c = -R; c <= R; ++c) {
+          int64_t vx = kx + a, vy = ky + b, vz = kz + c;
+          double ex = ((double)vx + 0.5) * p.res - (double)s.x;
+          double ey = ((double)vy + 0.5) * p.res - (double)s.y;
+          double ez = ((double)vz + 0.5) * p.res - (double)s.z;
+          double d2 = ex * ex;
+          d2 = d2 + ey * ey;
+          d2 = d2 + ez * ez;
+          if (!(d2 < l2)) continue;
+          const double f = kernel_f(std::sqrt(d2) / l);
+          Key3 bk = {floor_div(vx, B), floor_div(vy, B), floor_div(vz, B)};
+          Block& blk = m.blocks[bk];
+          if (blk.inc.empty()) {
+            blk.inc.assign((size_t)(B * B * B * K1), 0.0);
+            blk.pairs.assign((size_t)(B * B * B), 0);
+          }
+          int64_t li = ((vz - bk[2] * B) * B + (vy - bk[1] * B)) * B + (vx - bk[0] * B);
+          for (int k = 0; k < K1; ++k)
+            if (s.w[k] != 0.0f) blk.inc[(size_t)(li * K1 + k)] += p.sigma0 * p.sigma0_scale[k] * f * (double)s.w[k];
+          blk.pairs[(size_t)li] += 1;
+        }
+  }
+}
+
 bool labels_ok(const Params& p, const int32_t* labels, int64_t n) {
   for (int64_t i = 0; i < n; ++i)
     if (labels[i] < 1 || labels[i] > p.num_classes) return false;
@@ -519,6 +625,45 @@ int orc_map_insert_scan(void* h, const float* pts, const int32_t* labels, int64_
   std::vector<Sample> train;
   training_set(m->p, pts, labels, n, T, train, stats);
   update(*m, train);
+  return 0;
+}
+
+// Reading K15: the soft training set of a scan (probs [n,K] over classes 1..K):
+// xyz_out [cap,3], w_out [cap,K+1]; returns the count (writes at most cap).
+int64_t orc_soft_training_set(const orc_params* q, const float* pts, const float* probs, int64_t n, const double* T,
+                              float* xyz_out, float* w_out, int64_t cap, int64_t* stats) {
+  Params p = conv(q);
+  const int K1 = nclass(p);
+  std::vector<SoftSample> train;
+  soft_training_set(p, pts, probs, n, T, train, stats);
+  const int64_t c = std::min<int64_t>(cap, (int64_t)train.size());
+  for (int64_t i = 0; i < c; ++i) {
+    xyz_out[3 * i] = train[i].x;
+    xyz_out[3 * i + 1] = train[i].y;
+    xyz_out[3 * i + 2] = train[i].z;
+    for (int k = 0; k < K1; ++k) w_out[i * K1 + k] = train[i].w[k];
+  }
+  return (int64_t)train.size();
+}
+
+// a5 on a soft training set: xyz [n,3], w [n,K+1].
+int orc_map_insert_training_soft(void* h, const float* xyz, const float* w, int64_t n) {
+  Map* m = (Map*)h;
+  const int K1 = nclass(m->p);
+  std::vector<SoftSample> train((size_t)n);
+  for (int64_t i = 0; i < n; ++i)
+    train[i] = {xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2], std::vector<float>(w + i * K1, w + (i + 1) * K1)};
+  accumulate_soft(*m, train);
+  return 0;
+}
+
+// Whole per-scan update with soft labels (a1..a5).  stats as orc_map_insert_scan.
+int orc_map_insert_scan_soft(void* h, const float* pts, const float* probs, int64_t n, const double* T,
+                             int64_t* stats) {
+  Map* m = (Map*)h;
+  std::vector<SoftSample> train;
+  soft_training_set(m->p, pts, probs, n, T, train, stats);
+  accumulate_soft(*m, train);
   return 0;
 }
 

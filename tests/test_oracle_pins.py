@@ -573,6 +573,52 @@ def test_point_queries_against_bruteforce_and_voxel_centres(orc):
     assert np.all(diff <= 90 * 0.9 * 2.0 * 4.0 / 0.3 * np.linalg.norm(step, axis=1))
 
 
+def test_soft_labels_grouping_and_weights(orc):
+    """Reading K15: hits grouped by (cell, most probable class); per class the
+    exact mean of the members' weights.  Three hits of one cell, K = 2."""
+    p = orc.params(res=1.0, free_step=100.0, num_classes=2)  # no free samples: every r < s
+    pts = np.array([[0.25, 0.5, 0.5], [0.75, 0.5, 0.5], [0.5, 0.25, 0.5]], np.float32)
+    probs = np.array([[0.75, 0.25], [0.625, 0.375], [0.25, 0.75]], np.float32)
+    xyz, w, st = orc.soft_training_set(p, pts, probs, np.eye(4))
+    assert st == dict(hits=3, free=0, train=2)
+    got = {int(np.argmax(wi)): (tuple(x), tuple(wi)) for x, wi in zip(xyz, w)}
+    assert got[1] == ((0.5, 0.5, 0.5), (0.0, 0.6875, 0.3125))
+    assert got[2] == ((0.5, 0.25, 0.5), (0.0, 0.25, 0.75))
+
+
+def test_soft_labels_reduce_to_hard_labels_and_are_linear(orc):
+    """One-hot probability vectors give the hard-label map exactly (same groups,
+    centroids and kernel sums); weights a e_j + b e_k give a times the class-j
+    map plus b times the class-k map."""
+    sc = scenes.small_region_scan(1, n_az=30, n_el=20)
+    prm = dict(scenes.SMALL_SCENE_PARAMS)
+    K = prm["num_classes"]
+    hard = orc.OracleMap(orc.params(**prm))
+    st_hard = hard.insert_scan(sc["points"], sc["labels"], sc["pose"])
+    soft = orc.OracleMap(orc.params(**prm))
+    onehot = np.eye(K, dtype=np.float32)[sc["labels"] - 1]
+    assert soft.insert_scan_soft(sc["points"], onehot, sc["pose"]) == st_hard
+    for a, b in zip(soft.export(), hard.export()):
+        np.testing.assert_array_equal(a, b)
+    rng = np.random.default_rng(35)
+    xyz = rng.uniform(-0.4, 0.4, size=(50, 3)).astype(np.float32)
+    w = np.zeros((50, K + 1), np.float32)
+    w[:, 2], w[:, 5] = 0.25, 0.75
+    mix = orc.OracleMap(orc.params(**prm))
+    mix.insert_training_soft(xyz, w)
+    parts = []
+    for c in (2, 5):
+        m = orc.OracleMap(orc.params(**prm))
+        m.insert_training(xyz, np.full(50, c, np.int32))
+        parts.append(m.export())
+    keys, alpha, pairs = mix.export()
+    np.testing.assert_array_equal(keys, parts[0][0])
+    np.testing.assert_array_equal(pairs, parts[0][2])
+    a0 = prm["alpha0"]
+    want = 0.25 * (parts[0][1] - a0) + 0.75 * (parts[1][1] - a0)
+    np.testing.assert_allclose(alpha - a0, want, rtol=1e-12, atol=1e-15)
+
+
 def test_gradient_sigma0_and_euler_identities(orc):
     """alpha - alpha0 is linear in sigma0; alpha_v depends on (x_i - c_v)/l only,
     so l dLL/dl + sum_i (x_i - c_v) . dLL/dx_i = 0 when every held-out point is
