@@ -34,23 +34,28 @@ class OrcParams(C.Structure):
     _fields_ = [(n, C.c_double) for n in ("res", "length_scale", "sigma0", "alpha0", "free_step", "ds_res",
                                           "min_range", "max_range", "free_thresh", "occ_thresh")] + \
                [("num_classes", C.c_int32), ("block_edge", C.c_int32), ("sensor_model", C.c_int32),
-                ("sigma0_scale", C.c_double * 32), ("association", C.c_int32)]
+                ("sigma0_scale", C.c_double * 32), ("association", C.c_int32), ("l_scale", C.c_double * 32)]
 
 
 def params(res=0.1, length_scale=0.3, sigma0=0.1, alpha0=0.001, free_step=0.3, ds_res=None, min_range=0.0,
            max_range=1e30, free_thresh=0.47, occ_thresh=0.6, num_classes=10, block_edge=8, sensor_model=0,
-           sigma0_scale=None, association=0, **_ignored):
+           sigma0_scale=None, association=0, l_scale=None, **_ignored):
     """Parameter block; defaults follow Table (parameters) and Sec. V-A of the paper.
     sensor_model 0: kernel inference, Eq. (alpha_kernel); 1: counting model, Eq. (alpha).
     sigma0_scale: per-class multipliers of sigma0 (classes 0..K; default all 1).
-    association 0: every voxel within l (exact); 1: the extended block (reading K14)."""
+    association 0: every voxel within l (exact); 1: the extended block (reading K14).
+    l_scale: per-class multipliers of the length scale (reading K16; default all 1)."""
     sc = [1.0] * 32
     if sigma0_scale is not None:
         for k, v in enumerate(sigma0_scale):
             sc[k] = float(v)
+    ls = [1.0] * 32
+    if l_scale is not None:
+        for k, v in enumerate(l_scale):
+            ls[k] = float(v)
     return OrcParams(res, length_scale, sigma0, alpha0, free_step, res if ds_res is None else ds_res, min_range,
                      max_range, free_thresh, occ_thresh, num_classes, block_edge, sensor_model,
-                     (C.c_double * 32)(*sc), association)
+                     (C.c_double * 32)(*sc), association, (C.c_double * 32)(*ls))
 
 
 _P = C.POINTER

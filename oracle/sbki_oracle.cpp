@@ -54,6 +54,10 @@
 //       centroid with, per class, the exact mean of the members' weights
 //       rounded once to FP32.  A training point adds sigma0 s_k f(d/l) w^k into
 //       every class k (Eq. alpha_kernel with y_i = w).
+//   K16 Per-class support (the rest of next row f1): class k's kernel has the
+//       length scale l_k = length_scale * l_scale[k]; a pair counts for class k
+//       when d < l_k.  All l_scale 1 is the common l.  The differentiable form
+//       takes the common l.
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -74,6 +78,7 @@ struct Params {
   int32_t sensor_model;  // 0: kernel inference, Eq. (alpha_kernel); 1: counting, Eq. (alpha)
   double sigma0_scale[32];  // reading K13: class k's kernel scale is sigma0 * sigma0_scale[k]
   int32_t association;      // reading K14: 0 exact (K5), 1 extended block (face neighbours)
+  double l_scale[32];       // reading K16: class k's length scale is length_scale * l_scale[k]
 };
 
 const double kPi = 3.14159265358979323846;
@@ -308,15 +313,22 @@ void downsample(const Params& p, const std::vector<Sample>& in, std::vector<Samp
   }
 }
 
+// Largest per-class length scale (K16): the stencil must reach every class's support.
+double max_length_scale(const Params& p) {
+  double lm = 0.0;
+  for (int c = 0; c < p.num_classes + 1; ++c) lm = std::max(lm, p.length_scale * p.l_scale[c]);
+  return lm;
+}
+
 // Step a5, Eq. (alpha_kernel) with Eq. (kernel): stencil enumeration per point.
 void accumulate(Map& m, const std::vector<Sample>& train) {
   const Params& p = m.p;
   const int K1 = nclass(p);
   const int64_t B = p.block_edge;
   const float inv_res = (float)(1.0 / p.res);
-  const double l = p.length_scale, l2 = l * l;
-  const int64_t R = (int64_t)std::ceil(l / p.res) + 1;
+  const int64_t R = (int64_t)std::ceil(max_length_scale(p) / p.res) + 1;
   for (const Sample& s : train) {
+    const double l = p.length_scale * p.l_scale[s.label], l2 = l * l;  // K16
     int64_t kx = voxel_index(s.x, inv_res), ky = voxel_index(s.y, inv_res), kz = voxel_index(s.z, inv_res);
     const Key3 pb = {floor_div(kx, B), floor_div(ky, B), floor_div(kz, B)};  // the point's block (K14)
     for (int64_t a = -R; a <= R; ++a)
@@ -447,8 +459,7 @@ void accumulate_soft(Map& m, const std::vector<SoftSample>& train) {
   const int K1 = nclass(p);
   const int64_t B = p.block_edge;
   const float inv_res = (float)(1.0 / p.res);
-  const double l = p.length_scale, l2 = l * l;
-  const int64_t R = (int64_t)std::ceil(l / p.res) + 1;
+  const int64_t R = (int64_t)std::ceil(max_length_scale(p) / p.res) + 1;
   for (const SoftSample& s : train) {
     int64_t kx = voxel_index(s.x, inv_res), ky = voxel_index(s.y, inv_res), kz = voxel_index(s.z, inv_res);
     for (int64_t a = -R; a <= R; ++a)
@@ -461,8 +472,12 @@ void accumulate_soft(Map& m, const std::vector<SoftSample>& train) {
           double d2 = ex * ex;
           d2 = d2 + ey * ey;
           d2 = d2 + ez * ez;
-          if (!(d2 < l2)) continue;
-          const double f = kernel_f(std::sqrt(d2) / l);
+          bool any = false;  // a class with weight whose support (K16) holds the voxel
+          for (int k = 0; k < K1; ++k) {
+            const double lk = p.length_scale * p.l_scale[k];
+            any = any || (s.w[k] != 0.0f && d2 < lk * lk);
+          }
+          if (!any) continue;
           Key3 bk = {floor_div(vx, B), floor_div(vy, B), floor_div(vz, B)};
           Block& blk = m.blocks[bk];
           if (blk.inc.empty()) {
@@ -470,8 +485,12 @@ void accumulate_soft(Map& m, const std::vector<SoftSample>& train) {
             blk.pairs.assign((size_t)(B * B * B), 0);
           }
           int64_t li = ((vz - bk[2] * B) * B + (vy - bk[1] * B)) * B + (vx - bk[0] * B);
-          for (int k = 0; k < K1; ++k)
-            if (s.w[k] != 0.0f) blk.inc[(size_t)(li * K1 + k)] += p.sigma0 * p.sigma0_scale[k] * f * (double)s.w[k];
+          for (int k = 0; k < K1; ++k) {
+            const double lk = p.length_scale * p.l_scale[k];
+            if (s.w[k] != 0.0f && d2 < lk * lk)
+              blk.inc[(size_t)(li * K1 + k)] += p.sigma0 * p.sigma0_scale[k] * kernel_f(std::sqrt(d2) / lk) *
+                                                (double)s.w[k];
+          }
           blk.pairs[(size_t)li] += 1;
         }
   }
@@ -521,6 +540,7 @@ typedef struct {
   int32_t num_classes, block_edge, sensor_model;
   double sigma0_scale[32];
   int32_t association;
+  double l_scale[32];
 } orc_params;
 
 static Params conv(const orc_params* q) {
@@ -730,7 +750,6 @@ void orc_alpha_bruteforce(const orc_params* q, const float* xyz, const int32_t* 
                           const int64_t* keys, int64_t nq, double* alpha, int64_t* pairs) {
   Params p = conv(q);
   const int K1 = nclass(p);
-  const double l = p.length_scale, l2 = l * l;
   for (int64_t v = 0; v < nq; ++v) {
     double cx = ((double)keys[3 * v] + 0.5) * p.res;
     double cy = ((double)keys[3 * v + 1] + 0.5) * p.res;
@@ -742,6 +761,7 @@ void orc_alpha_bruteforce(const orc_params* q, const float* xyz, const int32_t* 
       double d2 = ex * ex;
       d2 = d2 + ey * ey;
       d2 = d2 + ez * ez;
+      const double l = p.length_scale * p.l_scale[lab[i]], l2 = l * l;  // K16
       if (!(d2 < l2)) continue;
       alpha[v * K1 + lab[i]] += p.sigma0 * p.sigma0_scale[lab[i]] * kernel_f(std::sqrt(d2) / l);
       ++pc;
@@ -757,7 +777,6 @@ void orc_alpha_at_points(const orc_params* q, const float* xyz, const int32_t* l
                          int64_t nq, double* alpha) {
   Params p = conv(q);
   const int K1 = nclass(p);
-  const double l = p.length_scale, l2 = l * l;
   for (int64_t v = 0; v < nq; ++v) {
     for (int c = 0; c < K1; ++c) alpha[v * K1 + c] = p.alpha0;
     for (int64_t i = 0; i < n; ++i) {
@@ -766,6 +785,7 @@ void orc_alpha_at_points(const orc_params* q, const float* xyz, const int32_t* l
       double d2 = ex * ex;
       d2 = d2 + ey * ey;
       d2 = d2 + ez * ez;
+      const double l = p.length_scale * p.l_scale[lab[i]], l2 = l * l;  // K16
       if (!(d2 < l2)) continue;
       alpha[v * K1 + lab[i]] += p.sigma0 * p.sigma0_scale[lab[i]] * kernel_f(std::sqrt(d2) / l);
     }

@@ -619,6 +619,40 @@ def test_soft_labels_reduce_to_hard_labels_and_are_linear(orc):
     np.testing.assert_allclose(alpha - a0, want, rtol=1e-12, atol=1e-15)
 
 
+def test_per_class_support_against_bruteforce(orc):
+    """Reading K16: class k's kernel has support l_k = l * l_scale[k]; a numpy
+    all-pairs sum with per-class supports for hard labels, and the soft path
+    with one-hot weights giving the same map."""
+    rng = np.random.default_rng(39)
+    xyz = rng.uniform(-0.35, 0.35, size=(70, 3)).astype(np.float32)
+    lab = rng.integers(0, 4, size=70).astype(np.int32)
+    ls = np.array([1.0, 0.5, 1.6, 0.8])
+    base = dict(res=0.1, length_scale=0.25, sigma0=0.6, num_classes=3, l_scale=ls)
+    m = orc.OracleMap(orc.params(**base))
+    m.insert_training(xyz, lab)
+    keys, alpha, pairs = m.export()
+    c = (keys + 0.5) * 0.1
+    want = np.zeros((len(keys), 4))
+    npairs = np.zeros(len(keys), np.int64)
+    x64 = xyz.astype(np.float64)
+    for i in range(len(xyz)):
+        lk = 0.25 * ls[lab[i]]
+        e = c - x64[i]
+        d2 = (e[:, 0] * e[:, 0] + e[:, 1] * e[:, 1]) + e[:, 2] * e[:, 2]
+        sel = d2 < lk * lk
+        want[sel, lab[i]] += 0.6 * np.array([orc.kernel_f(math.sqrt(v) / lk) for v in d2[sel]])
+        npairs[sel] += 1
+    np.testing.assert_allclose(alpha - 0.001, want, rtol=1e-12, atol=1e-15)
+    np.testing.assert_array_equal(pairs, npairs)
+    got, gp = orc.alpha_bruteforce(orc.params(**base), xyz, lab, keys)
+    np.testing.assert_allclose(got, alpha, rtol=1e-12)
+    np.testing.assert_array_equal(gp, pairs)
+    soft = orc.OracleMap(orc.params(**base))
+    soft.insert_training_soft(xyz, np.eye(4, dtype=np.float32)[lab])
+    for a, b in zip(soft.export(), m.export()):
+        np.testing.assert_array_equal(a, b)
+
+
 def test_gradient_sigma0_and_euler_identities(orc):
     """alpha - alpha0 is linear in sigma0; alpha_v depends on (x_i - c_v)/l only,
     so l dLL/dl + sum_i (x_i - c_v) . dLL/dx_i = 0 when every held-out point is
