@@ -46,7 +46,8 @@ typedef enum {
 
 /* Parameters.  Defaults (sbki_default_params) follow Table (parameters):
  * l = 0.3 m, sigma0 = 0.1, alpha0 = 0.001; Sec. V-A: res = 0.1 m, free and
- * occupied thresholds 0.47 and 0.6. */
+ * occupied thresholds 0.47 and 0.6.  Start from sbki_default_params and
+ * override fields: a zeroed struct is refused (sigma0_scale must be > 0). */
 typedef struct sbki_params {
   double res;          /* voxel edge [m] */
   double length_scale; /* kernel support l [m], Eq. (kernel); 0 < l <= 0.75 * block edge * res */
@@ -76,7 +77,8 @@ typedef struct sbki_params {
                          * model, Eq. (alpha): every training point adds 1 to alpha^{y_i} of the
                          * voxel floor(x * fp32(1/res)) that contains it (exact FP32 counts below
                          * 2^24 per voxel and class); length_scale and sigma0 do not enter it.
-                         * Needs accumulate_mode 0; sbki_backward and sbki_grad refuse it */
+                         * Needs accumulate_mode 0; sbki_backward, sbki_backward_scales and
+                         * sbki_grad refuse it */
   double sigma0_scale[32]; /* per-class kernel scale: class k's kernel is sigma0 * sigma0_scale[k]
                             * * f(d/l) (the paper's class-dependent signal variance, Sec. V);
                             * entries 0..K must be finite and > 0; sbki_default_params sets 1,
