@@ -90,3 +90,18 @@ def test_create_map_rejects_bad_params():
         with pytest.raises(sbki.SbkiError) as e:
             sbki.Map(sbki.default_params(**bad))
         assert e.value.status == sbki.ERR_INVALID_ARG
+
+
+def test_set_param_fills_class_arrays_and_rejects_unknown_names():
+    from paper_1909_04631_gb300 import sbki
+    p = sbki.Params()
+    for k in range(32):
+        p.sigma0_scale[k] = 1.0
+    sbki.set_param(p, "sigma0_scale", [0.5, 2.0])
+    assert list(p.sigma0_scale[:3]) == [0.5, 2.0, 1.0]
+    sbki.set_param(p, "num_classes", 7)
+    assert p.num_classes == 7
+    with pytest.raises(TypeError):
+        sbki.set_param(p, "no_such_field", 1)
+    with pytest.raises(ValueError):
+        sbki.set_param(p, "sigma0_scale", [1.0] * 33)
