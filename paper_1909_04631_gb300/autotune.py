@@ -25,7 +25,7 @@ DEFAULT_CANDIDATES = dict(accumulate_ctas_per_sm=(0, 2, 3), accumulate_chunk=(4,
 
 def _key(params, scans, device_name):
     geo = [params.res, params.length_scale, params.free_step, params.ds_res, params.max_range, params.num_classes,
-           params.block_edge, params.accumulate_mode]
+           params.block_edge, params.accumulate_mode, params.sensor_model]
     shape = [len(scans), int(sum(len(s["points"]) for s in scans) // 10000)]
     return hashlib.sha1(json.dumps([device_name, geo, shape]).encode()).hexdigest()[:16]
 
