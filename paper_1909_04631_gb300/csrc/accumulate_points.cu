@@ -43,6 +43,7 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kAxisMax = 15;             // offsets per axis: 2R + 1 <= 15
 constexpr int kYZMax = kAxisMax * kAxisMax;
 constexpr float kFar = 1.0e30f;          // d^2 of the padding row
+constexpr int kFastParts = 16;           // fast form: sub-voxel parts per axis of its candidate lists
 
 struct PtArgs {
   Geom g;
@@ -57,8 +58,11 @@ struct PtArgs {
   int tpad;              // entries per list (multiple of 32)
   int R;                 // offsets per axis span [-R, R]
   uint32_t recip_na;     // small_recip(2R + 1)
-  int chunk;             // consecutive training points per warp (fast set-up form)
+  int chunk;             // consecutive training points per warp (fast form)
   int32_t sink;          // spare pool block that absent neighbour blocks point at
+  const uint32_t* ftab;  // fast form: [kFastParts^3][ftpad] (X | Y << 8 | Z << 16 row byte offsets in a slot)
+  const int32_t* flen;   // [kFastParts^3] entries of each list
+  int ftpad;             // entries per fast list (multiple of 32, at most 32 kFastEntries)
   DevCounters* dc;
 };
 
@@ -173,84 +177,114 @@ __global__ void __launch_bounds__(kThreads, 4) accumulate_points_kernel(PtArgs a
   if (lane == 0) atomicAdd(&a.dc->pairs, (unsigned long long)npairs);
 }
 
-// The same update with a cheaper per-point set-up, for 2R + 1 <= 8 (l up to
-// about 3 voxels).  A warp takes kChunk consecutive training points (sorted by
-// tile, so mostly one block) in groups of up to kGroup.  For a group, three
-// lanes per point (one per axis) form that axis's compensated offsets and
-// address parts for offsets -R..R at once, into per-point rows in shared
-// memory, with the point's sub-voxel part, block and voxel.  Then, point by
-// point, the warp combines the Y and Z rows into YZ rows, refreshes the pool
-// slots of the 27 blocks around the point's block when the block (or map)
-// changed, and sweeps the candidate list with the point's own X rows.
-constexpr int kGroup = 10;  // points whose rows one warp forms at once (3 lanes each)
-constexpr int kFastAxis = 8;  // rows per axis: 2R + 1 <= 7 offsets and the padding row
+// The same update for 2R + 1 <= 7 (l up to about 3 voxels), shaped for the
+// instruction issue rate, which bounds this loop.
+//
+// A warp takes a chunk of consecutive training points (sorted by tile, so
+// mostly one block) from a work queue and forms their rows in groups of up to
+// kGroup: three lanes per point (one per axis) write, for offsets j = 0..2R of
+// their axis, the row (e_j^2, address part) into the point's 256-byte slot in
+// shared memory (X rows at bytes 0..63, Y rows at 64..127, Z rows at 128..191,
+// the point's scalars at 192..255).  An address part holds the block digit of
+// the offset (base 3 per axis, times 4: a byte offset into the block table) in
+// its top byte and the voxel's in-block index below it (the X part also
+// carries the point's class row, label * B^3), so the three parts of a
+// candidate add up to (4 digit) << 24 | (label B^3 + in-block index).
+//
+// A candidate list entry holds the byte offsets of the candidate's X, Y and Z
+// rows inside a slot (bytes 0, 1, 2), so with the slot at a 256-byte aligned
+// shared address each row address is one byte permute.  Each lane takes two
+// entries at a time and evaluates their kernels with packed FP32 instructions
+// (two values per instruction).  The block table holds, per digit, the first
+// alpha element of the block (the pool slot times (K+1) B^3) minus the digit's
+// top byte, so table entry + summed address parts is the alpha element: one
+// shared load and one add per candidate.  Tables change only when the point's
+// block (or map) changes.  Lists come from a table with kFastParts^3 sub-voxel
+// parts; the next point's entries are loaded while the current one is swept.
+constexpr int kGroup = 10;         // points whose rows one warp forms at once (3 lanes each)
+constexpr int kFastAxis = 8;       // rows per axis: 2R + 1 <= 7 offsets and the X padding row
+constexpr int kSlotBytes = 256;    // one point's rows and scalars
+constexpr int kFastEntries = 5;    // list entries per lane (lists of at most 160)
+constexpr uint32_t kPadEntry = 8u * (kFastAxis - 1) | (64u << 8) | (128u << 16);  // X padding row, Y row 0, Z row 0
 
-struct alignas(16) PointRows {
-  float2 r[3][kFastAxis];  // per axis: (e^2, address part) of offset j - R; r[0][2R + 1] is the padding row
-  int pt[4];               // sub-voxel part per axis, label word
-  int blk[4];              // block per axis
-  int v0[4];               // voxel per axis
+struct __align__(256) FastWarp {
+  float2 rows[kGroup][kSlotBytes / 8];  // per point: X, Y, Z rows (8 each), scalars (int view, below)
+  uint32_t btab[64];                    // alpha element base per block digit (27 used)
+  uint32_t ptab[64];                    // pair-count element base per block digit (kTrack)
 };
+// scalars of a slot (int index into its last 64 bytes)
+constexpr int kScPart = 0, kScLabel = 1, kScS0 = 2, kScBlk = 4, kScV0 = 8;
 
-struct FastTables {
-  PointRows pts[kGroup];
-  float2 yz[kFastAxis * kFastAxis];  // YZ rows of the point being swept
-  float* blk[27];
-  int32_t* cnt[27];
-};
-
-// As candidate(), with the X rows of one point of the group; the point's
-// coordinates are loaded again only on the (rare) FP64 re-decision.
-template <bool kTrack>
-__device__ __forceinline__ uint32_t candidate_rows(const PtArgs& a, const FastTables& t, const PointRows& pr,
-                                                   uint32_t ent, uint32_t i, float s0) {
-  const Geom& g = a.g;
-  const float2 ex = *reinterpret_cast<const float2*>(reinterpret_cast<const char*>(pr.r[0]) + (ent & 0xffu));
-  const float2 eyz = *reinterpret_cast<const float2*>(reinterpret_cast<const char*>(t.yz) + ((ent >> 8) & 0x7ffu));
-  const float d2 = __fadd_rn(ex.x, eyz.x);
-  const int pk = __float_as_int(ex.y) + __float_as_int(eyz.y);
-  bool in = d2 < g.l2_lo;
-  const bool band = !in && d2 < g.l2_hi;
-  if (__any_sync(0xffffffffu, band)) {
-    if (band) {
-      const float4 p = a.train[i];
-      in = in_support64_call(pr.v0[0] + (int)((ent & 0xffu) >> 3) - a.R, pr.v0[1] + (int)((ent >> 19) & 15u) - a.R,
-                             pr.v0[2] + (int)((ent >> 23) & 15u) - a.R, p.x, p.y, p.z, g.res64, g.l2_64);
-    }
-  }
-  float* base = t.blk[pk & 0xff];
-  const float d = d2 * rsqrtf(fmaxf(d2, 1e-30f));
-  const float u = fmaxf(__fmaf_rn(-d, g.inv_l, 1.0f), 0.0f);
-  const float w = u * u;
-  red_add_if(in, base + (pk >> 8), s0 * (w * w * u * kernel_q(w)));
-  if (kTrack) red_add_if(in, t.cnt[pk & 0xff] + (pk >> 8), 1);
-  return in ? 1u : 0u;
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ float2 lds_f2(uint32_t a) {
+  float2 v;
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ uint32_t lds_u32(uint32_t a) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
 }
 
-template <bool kTrack, int kNit>
+// d^2 and summed address part of a candidate of the point whose slot starts at `slot`
+__device__ __forceinline__ void candidate_rows2(uint32_t e, uint32_t slot, float& d2, uint32_t& pk) {
+  const float2 rx = lds_f2(__byte_perm(e, slot, 0x7650));
+  const float2 ry = lds_f2(__byte_perm(e, slot, 0x7651));
+  const float2 rz = lds_f2(__byte_perm(e, slot, 0x7652));
+  d2 = __fadd_rn(__fadd_rn(rx.x, ry.x), rz.x);
+  pk = __float_as_uint(rx.y) + __float_as_uint(ry.y) + __float_as_uint(rz.y);
+}
+
+// FP64 re-decision of a candidate in the band around l^2 (rare; point loaded again)
+__device__ __forceinline__ bool band_decide(uint32_t e, const int* sc, const float4* train, uint32_t i, int R,
+                                         double res64, double l2_64) {
+  const float4 p = train[i];
+  const int jx = (int)((e & 0xffu) >> 3), jy = (int)(((e >> 8) & 0xffu) - 64u) >> 3,
+            jz = (int)(((e >> 16) & 0xffu) - 128u) >> 3;
+  return in_support64_call(sc[kScV0] + jx - R, sc[kScV0 + 1] + jy - R, sc[kScV0 + 2] + jz - R, p.x, p.y, p.z, res64,
+                           l2_64);
+}
+
+template <bool kTrack>
 __global__ void __launch_bounds__(kThreads, 4) accumulate_points_fast_kernel(PtArgs a) {
-  __shared__ FastTables s_tab[kWarps];
+  __shared__ FastWarp s_w[kWarps];
   const Geom& g = a.g;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  FastWarp& W = s_w[wid];
   const int R = a.R, na = 2 * R + 1, m = g.B - 1;
-  FastTables& t = s_tab[wid];
-  uint32_t npairs = 0;
   if (a.dc->err != 0) return;
+  if ((smem_addr(&W) & 255u) != 0u) {  // the byte permutes need 256-byte aligned slots
+    if (lane == 0) set_error(a.dc, SBKI_ERR_CUDA);
+    return;
+  }
   const uint32_t P = a.dc->n_train;
+  const uint32_t rows0 = smem_addr(&W.rows[0][0]);
+  const uint32_t btab = smem_addr(&W.btab[0]), ptab = smem_addr(&W.ptab[0]);
   // this lane's point of a group and axis (lanes 30, 31 form no rows)
-  const int gl = lane / 3, ax = lane - 3 * (lane / 3);
+  const int gl = lane / 3, ax = lane - 3 * gl;
   const int axshift = ax == 0 ? 0 : (ax == 1 ? g.B_shift : 2 * g.B_shift);
-  const int dmul = ax == 0 ? 1 : (ax == 1 ? 3 : 9);
-  int cb[3] = {INT_MIN, INT_MIN, INT_MIN}, cmap = -1;  // block and map the cached slots belong to
-  int32_t pool = -1;                                   // lanes 0..26: slot of block digit `lane`
+  const uint32_t dmul = ax == 0 ? 4u : (ax == 1 ? 12u : 36u);
+  const float2 neg_inv_l = make_float2(-g.inv_l, -g.inv_l), one2 = make_float2(1.0f, 1.0f);
+  int cb0 = INT_MIN, cb1 = INT_MIN, cb2 = INT_MIN, cmap = -1;  // block and map the tables belong to
+  uint32_t npairs = 0;
   const uint32_t chunk = (uint32_t)a.chunk;
-  for (uint32_t c = gw; c * chunk < P; c += nw) {
+  uint32_t c = 0;
+  if (lane == 0) c = atomicAdd(&a.dc->acc_next, 1u);
+  c = __shfl_sync(0xffffffffu, c, 0);
+  while (c * chunk < P) {
+    uint32_t cn = 0;  // next chunk, fetched while this one is processed
+    if (lane == 0) cn = atomicAdd(&a.dc->acc_next, 1u);
     const uint32_t c1 = min(P, c * chunk + chunk);
     for (uint32_t g0 = c * chunk; g0 < c1; g0 += kGroup) {
       const uint32_t gn = min(c1 - g0, (uint32_t)kGroup);  // warp-uniform
       // 1. rows of every point of the group, three lanes per point
+      int pt = 0;
       if (gl < (int)gn) {
         const float4 p = a.train[g0 + gl];
         const float xa = ax == 0 ? p.x : (ax == 1 ? p.y : p.z);
@@ -258,71 +292,121 @@ __global__ void __launch_bounds__(kThreads, 4) accumulate_points_fast_kernel(PtA
         float hi, lo;
         centre_offset0(v0, xa, g, hi, lo);
         const float phi = 0.5f - __fmul_rn(__fadd_rn(hi, lo), g.inv_res);
+        pt = min(kFastParts - 1, max(0, floor_small(phi * (float)kFastParts)));
         const int b0 = v0 >> g.B_shift;
-        PointRows& pr = t.pts[gl];
+        const int lw = label_of(p.w);
+        const uint32_t cls = ax == 0 ? (uint32_t)((lw & ((1 << kLabelBits) - 1)) * g.B3) : 0u;
+        float2* r = W.rows[gl] + kFastAxis * ax;
+        // offsets in a lane-dependent order, so the lanes of one store spread over the banks
+        int j = gl % na;
 #pragma unroll
-        for (int j = 0; j < kFastAxis; ++j) {
-          if (j < na) {
+        for (int t = 0; t < kFastAxis - 1; ++t) {
+          if (t < na) {
             const float e = centre_offset_at(j - R, hi, lo, g);
             const int v = v0 + j - R;
-            pr.r[ax][j] = make_float2(__fmul_rn(e, e),
-                                      __int_as_float(dmul * ((v >> g.B_shift) - (b0 - 1)) | ((v & m) << (axshift + 8))));
+            const uint32_t part = (dmul * (uint32_t)((v >> g.B_shift) - b0 + 1)) << 24 | (((uint32_t)(v & m) << axshift) + cls);
+            r[j] = make_float2(__fmul_rn(e, e), __uint_as_float(part));
+            j = j + 1 == na ? 0 : j + 1;
           }
         }
-        if (ax == 0) pr.r[0][na] = make_float2(kFar, __int_as_float(0));
-        pr.pt[ax] = min(kParts - 1, max(0, floor_small(phi * (float)kParts)));
-        pr.blk[ax] = b0;
-        pr.v0[ax] = v0;
-        if (ax == 0) pr.pt[3] = label_of(p.w);
+        if (ax == 0) r[kFastAxis - 1] = make_float2(kFar, 0.0f);
+        int* sc = reinterpret_cast<int*>(W.rows[gl] + 3 * kFastAxis);
+        sc[kScBlk + ax] = b0;
+        sc[kScV0 + ax] = v0;
+        if (ax == 0) {
+          sc[kScLabel] = lw;
+          sc[kScS0] = __float_as_int(g.sigma0_k[lw & ((1 << kLabelBits) - 1)]);
+        }
       }
+      const int pty = __shfl_sync(0xffffffffu, pt, min(lane + 1, 31));
+      const int ptz = __shfl_sync(0xffffffffu, pt, min(lane + 2, 31));
+      if (ax == 0 && gl < (int)gn)
+        reinterpret_cast<int*>(W.rows[gl] + 3 * kFastAxis)[kScPart] = pt + kFastParts * (pty + kFastParts * ptz);
       __syncwarp();
-      // 2. point by point: YZ rows, block slots, candidate sweeps
-      for (uint32_t k = 0; k < gn; ++k) {
-        const PointRows& pr = t.pts[k];
-        const int4 ip = *reinterpret_cast<const int4*>(pr.pt);
-        const int4 ib = *reinterpret_cast<const int4*>(pr.blk);
-        const int part = ip.x + kParts * (ip.y + kParts * ip.z);
-        const int label = ip.w & ((1 << kLabelBits) - 1), map = ip.w >> kLabelBits;
-        const float s0 = g.sigma0_k[label];  // class label's kernel scale
-        for (int q0 = 0; q0 < na * na; q0 += 32) {
-          const int q = min(q0 + lane, na * na - 1);
-          const int jy = (int)small_div((uint32_t)q, a.recip_na), jz = q - jy * na;
-          const float2 ry = pr.r[1][jy], rz = pr.r[2][jz];
-          if (q0 + lane < na * na)
-            t.yz[q] = make_float2(__fadd_rn(ry.x, rz.x), __int_as_float(__float_as_int(ry.y) + __float_as_int(rz.y)));
-        }
-        if (ib.x != cb[0] || ib.y != cb[1] || ib.z != cb[2] || map != cmap) {  // warp-uniform
-          cb[0] = ib.x;
-          cb[1] = ib.y;
-          cb[2] = ib.z;
-          cmap = map;
-          pool = -1;
-          if (lane < 27)
-            pool = find_pool_slot(a.hkeys, a.hvals, a.hash_cap,
-                                  pack_block(ib.x - 1 + lane % 3, ib.y - 1 + (lane / 3) % 3, ib.z - 1 + lane / 9, map));
-        }
-        if (lane < 27) {
-          t.blk[lane] = a.alpha + ((size_t)(pool >= 0 ? pool : a.sink) * g.K1 + label) * g.B3;
-          if (kTrack) t.cnt[lane] = a.pairs + (size_t)(pool >= 0 ? pool : a.sink) * g.B3;
-        }
-        __syncwarp();
-        const uint32_t* tab = a.ctab + part * a.tpad;
-        const int len = __ldg(a.clen + part);
-        const uint32_t i = g0 + k;
-        if (kNit > 0) {
-          uint32_t ent[kNit > 0 ? kNit : 1];
+      // 2. point by point: block tables (when the block changes), candidate sweeps
+      uint32_t ent[kFastEntries];
+      int len = 0;
+      {
+        const int part = reinterpret_cast<const int*>(W.rows[0] + 3 * kFastAxis)[kScPart];
+        const uint32_t* tab = a.ftab + (size_t)part * a.ftpad;
+        len = __ldg(a.flen + part);
 #pragma unroll
-          for (int it = 0; it < kNit; ++it) ent[it] = it * 32 < len ? __ldg(tab + it * 32 + lane) : 0u;
-#pragma unroll
-          for (int it = 0; it < kNit; ++it)
-            if (it * 32 < len) npairs += candidate_rows<kTrack>(a, t, pr, ent[it], i, s0);  // warp-uniform
-        } else {
-          for (int q = lane; q - lane < len; q += 32)
-            npairs += candidate_rows<kTrack>(a, t, pr, __ldg(tab + q), i, s0);
-        }
-        __syncwarp();  // the YZ rows and block pointers are rewritten for the next point
+        for (int it = 0; it < kFastEntries; ++it) ent[it] = it * 32 < len ? __ldg(tab + it * 32 + lane) : kPadEntry;
       }
+      for (uint32_t k = 0; k < gn; ++k) {
+        const int* sc = reinterpret_cast<const int*>(W.rows[k] + 3 * kFastAxis);
+        const int4 sb = *reinterpret_cast<const int4*>(sc + kScBlk);
+        const int lw = sc[kScLabel];
+        const float s0 = __int_as_float(sc[kScS0]);
+        const int map = lw >> kLabelBits;
+        // the next point's list, in flight while this one is swept
+        uint32_t nent[kFastEntries];
+        int nlen = 0;
+        if (k + 1 < gn) {
+          const int part = reinterpret_cast<const int*>(W.rows[k + 1] + 3 * kFastAxis)[kScPart];
+          const uint32_t* tab = a.ftab + (size_t)part * a.ftpad;
+          nlen = __ldg(a.flen + part);
+#pragma unroll
+          for (int it = 0; it < kFastEntries; ++it)
+            nent[it] = it * 32 < nlen ? __ldg(tab + it * 32 + lane) : kPadEntry;
+        }
+        if (sb.x != cb0 || sb.y != cb1 || sb.z != cb2 || map != cmap) {  // warp-uniform
+          cb0 = sb.x;
+          cb1 = sb.y;
+          cb2 = sb.z;
+          cmap = map;
+          __syncwarp();  // every lane is done with the old tables
+          if (lane < 27) {
+            const int32_t pool = find_pool_slot(a.hkeys, a.hvals, a.hash_cap,
+                                                pack_block(sb.x - 1 + lane % 3, sb.y - 1 + (lane / 3) % 3,
+                                                           sb.z - 1 + lane / 9, map));
+            const uint32_t pb = (uint32_t)(pool >= 0 ? pool : a.sink);
+            W.btab[lane] = pb * (uint32_t)(g.K1 * g.B3) - ((4u * (uint32_t)lane) << 24);
+            if (kTrack) W.ptab[lane] = pb * (uint32_t)g.B3 - ((4u * (uint32_t)lane) << 24);
+          }
+          __syncwarp();
+        }
+        const uint32_t slot = rows0 + (uint32_t)k * kSlotBytes;
+        const float2 s02 = make_float2(s0, s0);
+        const uint32_t cls = (uint32_t)((lw & ((1 << kLabelBits) - 1)) * g.B3);
+#pragma unroll
+        for (int jp = 0; jp < (kFastEntries + 1) / 2; ++jp) {
+          if (jp * 64 < len) {  // warp-uniform
+            const uint32_t ea = ent[2 * jp], eb = 2 * jp + 1 < kFastEntries ? ent[2 * jp + 1] : kPadEntry;
+            float d2a, d2b;
+            uint32_t pka, pkb;
+            candidate_rows2(ea, slot, d2a, pka);
+            candidate_rows2(eb, slot, d2b, pkb);
+            bool ina = d2a < g.l2_lo, inb = d2b < g.l2_lo;
+            const bool bnda = !ina && d2a < g.l2_hi, bndb = !inb && d2b < g.l2_hi;
+            if (__any_sync(0xffffffffu, bnda || bndb)) {
+              if (bnda) ina = band_decide(ea, sc, a.train, g0 + k, R, g.res64, g.l2_64);
+              if (bndb) inb = band_decide(eb, sc, a.train, g0 + k, R, g.res64, g.l2_64);
+            }
+            // kernel of both candidates: f = u^5 Q(u^2), u = 1 - d / l, times sigma0 s_k
+            const float2 d = make_float2(sqrt_approx(d2a), sqrt_approx(d2b));
+            const float2 u = __ffma2_rn(d, neg_inv_l, one2);
+            const float2 w = __fmul2_rn(u, u);
+            const float2 q = kernel_q2(w);
+            const float2 v = __fmul2_rn(__fmul2_rn(__fmul2_rn(__fmul2_rn(w, w), u), q), s02);
+            const uint32_t elema = lds_u32(__byte_perm(pka, btab, 0x7653)) + pka;
+            const uint32_t elemb = lds_u32(__byte_perm(pkb, btab, 0x7653)) + pkb;
+            red_add_if(ina, a.alpha + elema, v.x);
+            red_add_if(inb, a.alpha + elemb, v.y);
+            if (kTrack) {
+              red_add_if(ina, a.pairs + (lds_u32(__byte_perm(pka, ptab, 0x7653)) + pka - cls), 1);
+              red_add_if(inb, a.pairs + (lds_u32(__byte_perm(pkb, ptab, 0x7653)) + pkb - cls), 1);
+            }
+            npairs += (ina ? 1u : 0u) + (inb ? 1u : 0u);
+          }
+        }
+#pragma unroll
+        for (int it = 0; it < kFastEntries; ++it) ent[it] = nent[it];
+        len = nlen;
+      }
+      __syncwarp();  // the slots are rewritten by the next group
     }
+    c = __shfl_sync(0xffffffffu, cn, 0);
   }
   for (int o = 16; o > 0; o >>= 1) npairs += __shfl_down_sync(0xffffffffu, npairs, o);
   if (lane == 0) atomicAdd(&a.dc->pairs, (unsigned long long)npairs);
@@ -332,6 +416,7 @@ __global__ void __launch_bounds__(kThreads, 4) accumulate_points_fast_kernel(PtA
 __global__ void fresh_fill_kernel(const uint32_t* fresh, const int32_t* hvals, float* alpha, int32_t* pairs, int K1B3,
                                   int B3, DevCounters* dc) {
   if (dc->err != 0) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) dc->acc_next = 0;  // work queue of the accumulation launched next
   const uint32_t n_new = dc->n_new;
   for (uint32_t f = blockIdx.x; f < n_new; f += gridDim.x) {
     const int32_t pl = hvals[fresh[f]];
@@ -349,19 +434,18 @@ double min_axis_distance(int d, double lo, double hi) {
   return std::min(std::fabs(c - lo), std::fabs(c - hi));
 }
 
-}  // namespace
-
-// Candidate lists of the kParts^3 sub-voxel parts (host, once per map).  The
-// parts are widened by delta = 1e-3 voxel, far above the FP32 error of the
-// sub-voxel position (~1e-6 voxel), so a point's list always holds its ball.
-cudaError_t build_candidate_tables(MapState& m) {
-  const double lr = m.prm.length_scale / m.prm.res, delta = 1e-3;
+// Candidate offsets of each of parts^3 sub-voxel parts: every (dx, dy, dz) whose
+// voxel centre can lie within l of some position in the part, the part widened
+// by delta = 1e-3 voxel on every side (far above the FP32 error of the sub-voxel
+// position, ~1e-6 voxel), so a point's list always holds its ball.  Offsets are
+// packed as (dx + R) | (dy + R) << 4 | (dz + R) << 8; returns R.
+int candidate_lists(double lr, int parts, std::vector<std::vector<int32_t>>& lists) {
+  const double delta = 1e-3;
   const int R = (int)std::ceil(lr + 0.5 + delta);
-  constexpr int kLists = kParts * kParts * kParts;
-  std::vector<std::vector<int32_t>> lists(kLists);
-  size_t longest = 0;
-  for (int t = 0; t < kLists; ++t) {
-    const int pt[3] = {t % kParts, (t / kParts) % kParts, t / (kParts * kParts)};
+  const int n = parts * parts * parts;
+  lists.assign(n, {});
+  for (int t = 0; t < n; ++t) {
+    const int pt[3] = {t % parts, (t / parts) % parts, t / (parts * parts)};
     for (int dz = -R; dz <= R; ++dz)
       for (int dy = -R; dy <= R; ++dy)
         for (int dx = -R; dx <= R; ++dx) {
@@ -369,18 +453,42 @@ cudaError_t build_candidate_tables(MapState& m) {
           double m2 = 0.0;
           for (int a = 0; a < 3; ++a) {
             const double md =
-                min_axis_distance(d[a], (double)pt[a] / kParts - delta, (double)(pt[a] + 1) / kParts + delta);
+                min_axis_distance(d[a], (double)pt[a] / parts - delta, (double)(pt[a] + 1) / parts + delta);
             m2 += md * md;
           }
-          if (m2 < lr * lr * (1.0 + 1e-5))
-            lists[t].push_back((dx + R) | ((dy + R) << 4) | ((dz + R) << 8));
+          if (m2 < lr * lr * (1.0 + 1e-5)) lists[t].push_back((dx + R) | ((dy + R) << 4) | ((dz + R) << 8));
         }
-    longest = std::max(longest, lists[t].size());
   }
+  return R;
+}
+
+cudaError_t upload_lists(const std::vector<uint32_t>& flat, const std::vector<int32_t>& len, uint32_t** tab,
+                         int32_t** lens) {
+  cudaError_t e = cudaMalloc(tab, sizeof(uint32_t) * flat.size());
+  if (e != cudaSuccess) return e;
+  e = cudaMalloc(lens, sizeof(int32_t) * len.size());
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpy(*lens, len.data(), sizeof(int32_t) * len.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*tab, flat.data(), sizeof(uint32_t) * flat.size(), cudaMemcpyHostToDevice);
+}
+
+}  // namespace
+
+// Candidate lists (host, once per map): kParts^3 lists in the general form and,
+// when 2R + 1 <= 7, kFastParts^3 lists in the fast form's entry format.
+cudaError_t build_candidate_tables(MapState& m) {
+  const double lr = m.prm.length_scale / m.prm.res;
+  std::vector<std::vector<int32_t>> lists;
+  const int R = candidate_lists(lr, kParts, lists);
+  const int kLists = (int)lists.size();
+  size_t longest = 0;
   int maxd = 0;  // offsets actually used
-  for (auto& L : lists)
+  for (auto& L : lists) {
+    longest = std::max(longest, L.size());
     for (int32_t e : L)
       for (int a = 0; a < 3; ++a) maxd = std::max(maxd, std::abs(((e >> (4 * a)) & 15) - R));
+  }
   // re-pack with the tight R (the lookups hold 2R + 1 <= 15 entries per axis):
   // X row jx at byte offset 8 jx, YZ row (jy, jz) at byte offset 8 (jy (2R+1) + jz);
   // padding entries point at X row 2R + 1 (d^2 = 1e30) and YZ row 0
@@ -397,48 +505,59 @@ cudaError_t build_candidate_tables(MapState& m) {
                      jz = (uint32_t)(((e >> 8) & 15) - R + Rt);
       flat[(size_t)t * tpad + k] = (8u * jx) | ((8u * (jy * na + jz)) << 8) | (jy << 19) | (jz << 23);
     }
-  cudaError_t e = cudaMalloc(&m.ctab, sizeof(uint32_t) * flat.size());
-  if (e != cudaSuccess) return e;
-  e = cudaMalloc(&m.clen, sizeof(int32_t) * len.size());
+  cudaError_t e = upload_lists(flat, len, &m.ctab, &m.clen);
   if (e != cudaSuccess) return e;
   m.ctab_pad = tpad;
   m.ctab_R = Rt;
-  e = cudaMemcpy(m.clen, len.data(), sizeof(int32_t) * len.size(), cudaMemcpyHostToDevice);
+  if (na > kFastAxis - 1) return cudaSuccess;  // the fast form needs 2R + 1 <= 7
+  // fast form: entry = X row byte offset 8 jx | (64 + 8 jy) << 8 | (128 + 8 jz) << 16
+  // inside a point's slot; padding entries name the X padding row
+  const int Rf = candidate_lists(lr, kFastParts, lists);
+  const int nf = (int)lists.size();
+  longest = 0;
+  for (auto& L : lists) longest = std::max(longest, L.size());
+  const int fpad = (int)((longest + 31) / 32 * 32);
+  if (fpad > 32 * kFastEntries) return cudaSuccess;
+  std::vector<uint32_t> ff((size_t)nf * fpad, kPadEntry);
+  std::vector<int32_t> fl(nf);
+  for (int t = 0; t < nf; ++t) {
+    fl[t] = (int32_t)lists[t].size();
+    for (size_t k = 0; k < lists[t].size(); ++k) {
+      const int32_t e = lists[t][k];
+      const uint32_t jx = (uint32_t)((e & 15) - Rf + Rt), jy = (uint32_t)(((e >> 4) & 15) - Rf + Rt),
+                     jz = (uint32_t)(((e >> 8) & 15) - Rf + Rt);
+      if (jx >= (uint32_t)na || jy >= (uint32_t)na || jz >= (uint32_t)na) return cudaErrorInvalidValue;
+      ff[(size_t)t * fpad + k] = (8u * jx) | ((64u + 8u * jy) << 8) | ((128u + 8u * jz) << 16);
+    }
+  }
+  e = upload_lists(ff, fl, &m.ftab, &m.flen);
   if (e != cudaSuccess) return e;
-  return cudaMemcpy(m.ctab, flat.data(), sizeof(uint32_t) * flat.size(), cudaMemcpyHostToDevice);
+  m.ftab_pad = fpad;
+  return cudaSuccess;
 }
 
 namespace {
 
 // ctas_per_sm: 0 = as many as fit
-template <bool kTrack, int kNit>
-cudaError_t launch_points(const PtArgs& a, int sm_count, int ctas_per_sm, cudaStream_t st) {
+template <typename Kernel>
+cudaError_t launch_persistent(Kernel kern, const PtArgs& a, int sm_count, int ctas_per_sm, cudaStream_t st) {
   int per_sm = 0;
-  cudaError_t e;
-  if (2 * a.R + 1 <= 8) {
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, accumulate_points_fast_kernel<kTrack, kNit>, kThreads,
-                                                      0);
-    if (e != cudaSuccess) return e;
-    if (ctas_per_sm > 0) per_sm = std::min(per_sm, ctas_per_sm);
-    accumulate_points_fast_kernel<kTrack, kNit><<<std::max(1, per_sm) * sm_count, kThreads, 0, st>>>(a);
-  } else {
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, accumulate_points_kernel<kTrack, kNit>, kThreads, 0);
-    if (e != cudaSuccess) return e;
-    if (ctas_per_sm > 0) per_sm = std::min(per_sm, ctas_per_sm);
-    accumulate_points_kernel<kTrack, kNit><<<std::max(1, per_sm) * sm_count, kThreads, 0, st>>>(a);
-  }
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0);
+  if (e != cudaSuccess) return e;
+  if (ctas_per_sm > 0) per_sm = std::min(per_sm, ctas_per_sm);
+  kern<<<std::max(1, per_sm) * sm_count, kThreads, 0, st>>>(a);
   return cudaGetLastError();
 }
 
 template <bool kTrack>
-cudaError_t launch_points_nit(const PtArgs& a, int sm_count, int ctas_per_sm, cudaStream_t st) {
+cudaError_t launch_general(const PtArgs& a, int sm_count, int ctas_per_sm, cudaStream_t st) {
   switch (a.tpad / 32) {  // unrolled sweeps for the common list lengths
-    case 2: return launch_points<kTrack, 2>(a, sm_count, ctas_per_sm, st);
-    case 3: return launch_points<kTrack, 3>(a, sm_count, ctas_per_sm, st);
-    case 4: return launch_points<kTrack, 4>(a, sm_count, ctas_per_sm, st);
-    case 5: return launch_points<kTrack, 5>(a, sm_count, ctas_per_sm, st);
-    case 6: return launch_points<kTrack, 6>(a, sm_count, ctas_per_sm, st);
-    default: return launch_points<kTrack, 0>(a, sm_count, ctas_per_sm, st);
+    case 2: return launch_persistent(accumulate_points_kernel<kTrack, 2>, a, sm_count, ctas_per_sm, st);
+    case 3: return launch_persistent(accumulate_points_kernel<kTrack, 3>, a, sm_count, ctas_per_sm, st);
+    case 4: return launch_persistent(accumulate_points_kernel<kTrack, 4>, a, sm_count, ctas_per_sm, st);
+    case 5: return launch_persistent(accumulate_points_kernel<kTrack, 5>, a, sm_count, ctas_per_sm, st);
+    case 6: return launch_persistent(accumulate_points_kernel<kTrack, 6>, a, sm_count, ctas_per_sm, st);
+    default: return launch_persistent(accumulate_points_kernel<kTrack, 0>, a, sm_count, ctas_per_sm, st);
   }
 }
 
@@ -469,11 +588,19 @@ cudaError_t launch_accumulate_points(MapState& m) {
   a.recip_na = ((1u << 20) + (uint32_t)(2 * m.ctab_R + 1) - 1u) / (uint32_t)(2 * m.ctab_R + 1);
   a.chunk = std::max(1, std::min(64, m.tune.accumulate_chunk));
   a.sink = (int32_t)m.pool_blocks;
+  a.ftab = m.ftab;
+  a.flen = m.flen;
+  a.ftpad = m.ftab_pad;
   a.dc = m.dc;
   m.launches += 2;
   const int cps = m.tune.accumulate_ctas_per_sm;
-  return m.pairs ? launch_points_nit<true>(a, m.sm_count, cps, m.stream)
-                 : launch_points_nit<false>(a, m.sm_count, cps, m.stream);
+  // the fast form addresses alpha and the pair counts with 32-bit element indices
+  const bool fast = m.ftab != nullptr && (uint64_t)(m.pool_blocks + 1) * (uint64_t)(m.g.K1 * m.g.B3) <= (1ull << 32);
+  if (fast)
+    return m.pairs ? launch_persistent(accumulate_points_fast_kernel<true>, a, m.sm_count, cps, m.stream)
+                   : launch_persistent(accumulate_points_fast_kernel<false>, a, m.sm_count, cps, m.stream);
+  return m.pairs ? launch_general<true>(a, m.sm_count, cps, m.stream)
+                 : launch_general<false>(a, m.sm_count, cps, m.stream);
 }
 
 }  // namespace sbki

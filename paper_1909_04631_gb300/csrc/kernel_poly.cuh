@@ -6,21 +6,33 @@
 
 namespace sbki {
 
-constexpr int kPolyDegree = 9;
+constexpr int kPolyDegree = 7;
 constexpr int kSlopeDegree = 10;
-// Q(w), degree 9
+// Q(w), degree 7
 __device__ __forceinline__ float kernel_q(float w) {
   const float x = __fmaf_rn(2.0f, w, -1.0f);
-  float acc = -1.271203416e-07f;
-  acc = __fmaf_rn(acc, x, 2.851444719e-06f);
-  acc = __fmaf_rn(acc, x, -5.188967920e-05f);
-  acc = __fmaf_rn(acc, x, 7.551263435e-04f);
-  acc = __fmaf_rn(acc, x, -8.489830386e-03f);
-  acc = __fmaf_rn(acc, x, 7.085110312e-02f);
-  acc = __fmaf_rn(acc, x, -4.154038182e-01f);
-  acc = __fmaf_rn(acc, x, 1.578207132e+00f);
-  acc = __fmaf_rn(acc, x, -3.405347269e+00f);
-  acc = __fmaf_rn(acc, x, 3.179476721e+00f);
+  float acc = -5.214391041e-05f;
+  acc = __fmaf_rn(acc, x, 7.608289382e-04f);
+  acc = __fmaf_rn(acc, x, -8.489671500e-03f);
+  acc = __fmaf_rn(acc, x, 7.084753925e-02f);
+  acc = __fmaf_rn(acc, x, -4.154038500e-01f);
+  acc = __fmaf_rn(acc, x, 1.578207845e+00f);
+  acc = __fmaf_rn(acc, x, -3.405347268e+00f);
+  acc = __fmaf_rn(acc, x, 3.179476699e+00f);
+  return acc;
+}
+
+// Q(w), degree 7, two arguments at once (packed FP32)
+__device__ __forceinline__ float2 kernel_q2(float2 w) {
+  const float2 x = __ffma2_rn(make_float2(2.0f, 2.0f), w, make_float2(-1.0f, -1.0f));
+  float2 acc = make_float2(-5.214391041e-05f, -5.214391041e-05f);
+  acc = __ffma2_rn(acc, x, make_float2(7.608289382e-04f, 7.608289382e-04f));
+  acc = __ffma2_rn(acc, x, make_float2(-8.489671500e-03f, -8.489671500e-03f));
+  acc = __ffma2_rn(acc, x, make_float2(7.084753925e-02f, 7.084753925e-02f));
+  acc = __ffma2_rn(acc, x, make_float2(-4.154038500e-01f, -4.154038500e-01f));
+  acc = __ffma2_rn(acc, x, make_float2(1.578207845e+00f, 1.578207845e+00f));
+  acc = __ffma2_rn(acc, x, make_float2(-3.405347268e+00f, -3.405347268e+00f));
+  acc = __ffma2_rn(acc, x, make_float2(3.179476699e+00f, 3.179476699e+00f));
   return acc;
 }
 

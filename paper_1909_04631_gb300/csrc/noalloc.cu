@@ -3,11 +3,11 @@
 // any device allocation.
 //
 // Who needs this: a caller that must not allocate once it is running - a
-// robot's real-time mapping loop that pre-reserves all memory at start-up, a
-// host framework that owns the device heap through its own pool, or code that
-// records work into a CUDA graph (cudaMalloc/cudaFree cannot be captured and
-// may synchronise the whole device).  Such a caller passes device buffers for
-// the inputs and the output; every intermediate buffer of the computation
+// robot's real-time mapping loop that pre-reserves all memory at start-up (a
+// cudaMalloc can stall or fail mid-run), or a host framework that owns the
+// device heap through its own pool and cannot let a library allocate beside
+// it.  Such a caller passes device buffers for the inputs and the output;
+// every intermediate buffer of the computation
 // (transformed points, sample counts, items, radix-sort keys and values,
 // segment tables, scan partials, the scan descriptor, device counters) lives in one
 // file-scope device array of fixed size, so calling this allocates nothing.
@@ -22,7 +22,10 @@
 // work overlaps on the GPU (different streams, or different host threads at
 // once) race on the array: serialise them.  The first call on a device looks
 // up the array's device address (cudaGetSymbolAddress) with that device
-// current; make that first call before any stream capture.
+// current; make that first call before any stream capture.  The call
+// synchronises its stream twice (after counting the items and after the
+// downsampling, to read the counts back).
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -172,11 +175,17 @@ sbki_status run(const sbki_params* params, const float* points, const int32_t* l
     }
   } restore{prev, dev};
 
-  // the counters must start at zero; every other buffer is written before it is read
-  CKN(cudaMemsetAsync(m.dc, 0, sizeof(DevCounters), m.stream));
-  const uint32_t np = (uint32_t)n;
-  CKN(cudaMemcpyAsync(&m.dc->n_points, &np, sizeof(np), cudaMemcpyHostToDevice, m.stream));
-  const KeyFrame kf = frame_of_scan(m, pose);
+  // the counters start cleared (the hits' tile box empty) with this call's point
+  // count; every other buffer is written before it is read
+  DevCounters init;
+  memset(&init, 0, sizeof(init));
+  init.n_points = (uint32_t)n;
+  for (int a = 0; a < 3; ++a) {
+    init.tbox[a] = INT_MAX;
+    init.tbox[3 + a] = INT_MIN;
+  }
+  CKN(cudaMemcpyAsync(m.dc, &init, sizeof(init), cudaMemcpyHostToDevice, m.stream));
+  KeyFrame kf = frame_of_scan(m, pose);
   ScanDesc hd[2];  // this scan, then the end marker holding the point count
   memset(hd, 0, sizeof(hd));
   hd[0].pts = points;
@@ -200,6 +209,10 @@ sbki_status run(const sbki_params* params, const float* points, const int32_t* l
   if (h.err != 0) return fail((sbki_status)h.err, "training set without allocation: device error");
   const int64_t nitems = h.n_items;
   if (nitems > 0) {
+    // sort keys fitted to the hits' tile box, as in sbki_training_set
+    tighten_frame(m.g, h.tbox, pose, kf);
+    for (int r = 0; r < 3; ++r) hd[0].org[r] = kf.org[r];
+    CKN(cudaMemcpyAsync(s.desc, hd, sizeof(hd), cudaMemcpyHostToDevice, m.stream));
     CKN(launch_emit(m, 1, n, kf));
     CKN(launch_downsample_n(m, kf, nitems));
     CKN(cudaMemcpyAsync(&h, m.dc, sizeof(h), cudaMemcpyDeviceToHost, m.stream));

@@ -237,15 +237,14 @@ KeyFrame scan_frame(const MapState& m, const double T[16]) {
 // Key frame of one scan fitted to its tile bounding box (kept hits and the
 // sensor origin, one tile of margin: every free sample lies on a segment
 // between the origin and a hit), so the sort covers fewer key bits.
-void tighten_frame(const MapState& m, const double T[16], KeyFrame& kf) {
-  const int32_t* tb = m.hc->tbox;
+void fit_frame_to_box(const Geom& g, const int32_t tb[6], const double T[16], KeyFrame& kf) {
   for (int a = 0; a < 3; ++a) {
-    const int64_t ot = floor_div64((int64_t)std::floor((float)T[4 * a + 3] * m.g.inv_ds), kTileEdge);
+    const int64_t ot = floor_div64((int64_t)std::floor((float)T[4 * a + 3] * g.inv_ds), kTileEdge);
     const int64_t lo = std::min<int64_t>(tb[a], ot) - 1, hi = std::max<int64_t>(tb[3 + a], ot) + 1;
     kf.org[a] = (int32_t)lo;
     kf.bits[a] = std::max(1, ceil_log2(hi - lo + 1));
   }
-  kf.total_bits = kf.bits[0] + kf.bits[1] + kf.bits[2] + kLocalBits + m.g.label_bits;
+  kf.total_bits = kf.bits[0] + kf.bits[1] + kf.bits[2] + kLocalBits + g.label_bits;
 }
 
 // Descriptor of one scan (device point and label pointers).
@@ -369,7 +368,7 @@ sbki_status run_ingest(MapState& m, const float* points, const int32_t* labels, 
   if (m.hc->err != 0) return status_from_device(m);
   *nitems = m.hc->n_items;
   if (*nitems == 0) return SBKI_OK;
-  tighten_frame(m, T, kf);
+  fit_frame_to_box(m.g, m.hc->tbox, T, kf);
   m.hdesc[0].org[0] = kf.org[0];
   m.hdesc[0].org[1] = kf.org[1];
   m.hdesc[0].org[2] = kf.org[2];
@@ -459,6 +458,9 @@ namespace sbki {
 sbki_status validate_params(const sbki_params* p) { return check_params(p); }
 Geom geometry_of(const sbki_params& p) { return make_geom(p); }
 KeyFrame frame_of_scan(const MapState& m, const double T[16]) { return scan_frame(m, T); }
+void tighten_frame(const Geom& g, const int32_t tbox[6], const double T[16], KeyFrame& kf) {
+  fit_frame_to_box(g, tbox, T, kf);
+}
 void set_global_error(const char* msg) { snprintf(g_create_error, sizeof(g_create_error), "%s", msg); }
 }  // namespace sbki
 
@@ -585,7 +587,7 @@ void sbki_destroy_map(sbki_map* map) {
   {
     DeviceGuard dg(m.device);
     if (m.stream || m.dc) cudaStreamSynchronize(m.stream);
-    void* ptrs[] = {m.clen, m.gpool, m.dacc, m.ctab, m.hkeys, m.hvals, m.hmark, m.hcnt, m.hcur, m.boff, m.blist, m.alpha, m.pool_keys, m.pairs, m.dc, m.s.items, m.s.sitems, m.s.keys, m.s.keys2,
+    void* ptrs[] = {m.clen, m.ftab, m.flen, m.gpool, m.dacc, m.ctab, m.hkeys, m.hvals, m.hmark, m.hcnt, m.hcur, m.boff, m.blist, m.alpha, m.pool_keys, m.pairs, m.dc, m.s.items, m.s.sitems, m.s.keys, m.s.keys2,
                     m.s.vals, m.s.vals2, m.s.flags, m.s.seg_start, m.s.train, m.s.hist, m.s.scan_tmp, m.s.touched, m.s.fresh, m.s.bbox, m.s.slow, m.s.carry,
                     m.s.desc};
     for (void* p : ptrs)

@@ -49,6 +49,7 @@ struct DevCounters {
   uint32_t n_slow;                    // downsampling cells left to the slow exact mean, this scan
   uint32_t n_points;                  // input points of the update (all scans)
   int32_t tbox[6];                    // ds-tile bounding box of the kept hits (min xyz, max xyz)
+  uint32_t acc_next;                  // work queue head of the point-major accumulation (reset before it)
 };
 
 // ---------------------------------------------------------------- geometry constants
@@ -166,6 +167,9 @@ struct MapState {
   ScanDesc* hdesc = nullptr;            // pinned host staging of s.desc
   uint32_t* ctab = nullptr;             // point-major candidate lists [kParts^3][ctab_pad]
   int32_t* clen = nullptr;              // [kParts^3] entries of each list
+  uint32_t* ftab = nullptr;             // fast accumulation form's candidate lists (2R + 1 <= 7), or null
+  int32_t* flen = nullptr;              // their entry counts
+  int ftab_pad = 0;
   float* gpool = nullptr;               // dL/dalpha [pool_blocks][K1][B3] (differentiable form, on first use)
   double* dacc = nullptr;               // [4 + 32]: held-out LL, sum s G f, sum s G u^4 D d, keys missed (as
                                         // u64), then sum G f per class
@@ -260,6 +264,8 @@ static __device__ __noinline__ bool in_support64_call(int vx, int vy, int vz, fl
 sbki_status validate_params(const sbki_params* p);
 Geom geometry_of(const sbki_params& p);
 KeyFrame frame_of_scan(const MapState& m, const double T[16]);
+// the key frame of a scan fitted to its hits' tile box (DevCounters::tbox after the transform)
+void tighten_frame(const Geom& g, const int32_t tbox[6], const double T[16], KeyFrame& kf);
 void set_global_error(const char* msg);
 
 // ---------------------------------------------------------------- launchers (one per .cu)

@@ -29,9 +29,10 @@ EXPORTED = ["sbki_default_params", "sbki_create_map", "sbki_destroy_map", "sbki_
 
 
 class SbkiError(RuntimeError):
-    def __init__(self, status: int, message: str):
+    def __init__(self, status: int, message: str, count=None):
         super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), message))
         self.status = status
+        self.count = count  # a count the failing call still reported (output-capacity errors), else None
 
 
 class Params(C.Structure):
@@ -163,22 +164,46 @@ def default_params(**kw) -> Params:
     return p
 
 
+def check_noalloc_args(params: Params, points, labels, out) -> None:
+    """Refuses arguments that would make sbki_training_set_noalloc read or
+    write past a buffer: points must be float32 [n,3], labels int32 [n], out
+    float32 [cap,4], all contiguous CUDA tensors on device params.device.
+    TypeError for a wrong kind, dtype or device; ValueError for a wrong shape."""
+    import torch
+    want = (("points", points, torch.float32), ("labels", labels, torch.int32), ("out", out, torch.float32))
+    for name, t, dt in want:
+        if not (hasattr(t, "is_cuda") and t.is_cuda):
+            raise TypeError("%s must be a CUDA tensor" % name)
+        if t.dtype != dt:
+            raise TypeError("%s must be %s, got %s" % (name, dt, t.dtype))
+        if t.device.index != params.device:
+            raise TypeError("%s is on cuda:%s, the parameters name cuda:%d" % (name, t.device.index, params.device))
+        if not t.is_contiguous():
+            raise TypeError("%s must be contiguous" % name)
+    if points.dim() != 2 or points.shape[1] != 3:
+        raise ValueError("points must have shape [n,3], got %s" % (tuple(points.shape),))
+    if labels.dim() != 1 or labels.shape[0] != points.shape[0]:
+        raise ValueError("labels must have shape [%d], got %s" % (points.shape[0], tuple(labels.shape)))
+    if out.dim() != 2 or out.shape[1] != 4:
+        raise ValueError("out must have shape [cap,4], got %s" % (tuple(out.shape),))
+
+
 def training_set_noalloc(params: Params, points, labels, pose, out):
     """Training set of a scan (steps a1-a3) through the entry point that
     allocates nothing: points [n,3] float32, labels [n] int32 and out [cap,4]
     float32 are CUDA tensors on params.device (the caller's memory); work runs
-    on params.cuda_stream.  Returns the number of points written to out."""
+    on params.cuda_stream.  Returns the number of points written to out.  When
+    out is too small, the SbkiError raised carries the full count in .count
+    (the first cap points are written)."""
+    check_noalloc_args(params, points, labels, out)
     L = load()
     T = np.ascontiguousarray(pose, dtype=np.float64).reshape(16)
-    for name, t in (("points", points), ("labels", labels), ("out", out)):
-        if not (hasattr(t, "is_cuda") and t.is_cuda and t.is_contiguous()):
-            raise TypeError("%s must be a contiguous CUDA tensor" % name)
     cnt = C.c_int64()
     st = L.sbki_training_set_noalloc(C.byref(params), C.c_void_p(points.data_ptr()), C.c_void_p(labels.data_ptr()),
                                      points.shape[0], T.ctypes.data_as(C.c_void_p), C.c_void_p(out.data_ptr()),
                                      out.shape[0], C.byref(cnt))
     if st != OK:
-        raise SbkiError(st, L.sbki_last_error(None).decode())
+        raise SbkiError(st, L.sbki_last_error(None).decode(), count=cnt.value)
     return cnt.value
 
 

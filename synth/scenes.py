@@ -155,9 +155,11 @@ def raycast(scene: Scene, origin, dirs, max_range):
         # ground plane z = 0
         with np.errstate(divide="ignore", invalid="ignore"):
             tg = np.where(d[:, 2] < -1e-12, -o[2] / d[:, 2], np.inf)
-        gx = o[0] + tg * d[:, 0]
-        gy = o[1] + tg * d[:, 1]
-        okg = np.isfinite(tg) & (gx >= x0) & (gx <= x1) & (gy >= y0) & (gy <= y1)
+        fin = np.isfinite(tg)
+        tf = np.where(fin, tg, 0.0)  # rays that miss the plane: no inf * 0
+        gx = o[0] + tf * d[:, 0]
+        gy = o[1] + tf * d[:, 1]
+        okg = fin & (gx >= x0) & (gx <= x1) & (gy >= y0) & (gy <= y1)
         tg = np.where(okg, tg, np.inf)
         gcls = np.zeros(m, np.int32)
         ay = np.abs(gy)

@@ -5,6 +5,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -105,3 +106,50 @@ def test_set_param_fills_class_arrays_and_rejects_unknown_names():
         sbki.set_param(p, "no_such_field", 1)
     with pytest.raises(ValueError):
         sbki.set_param(p, "sigma0_scale", [1.0] * 33)
+
+
+class _FakeTensor:
+    """Stands in for a CUDA tensor (dtype, shape, device, layout only) so the
+    binding's argument checks run without a GPU."""
+
+    def __init__(self, shape, dtype, device=0, cuda=True, contiguous=True):
+        import types
+        self.shape, self.dtype, self.is_cuda, self._contig = tuple(shape), dtype, cuda, contiguous
+        self.device = types.SimpleNamespace(index=device)
+
+    def dim(self):
+        return len(self.shape)
+
+    def is_contiguous(self):
+        return self._contig
+
+
+def test_noalloc_binding_refuses_malformed_arguments():
+    """Each argument the allocation-free entry point would misread (wrong
+    dtype, shape, device or layout) is refused before the library is called."""
+    import torch
+    from paper_1909_04631_gb300 import sbki
+    p = sbki.Params()
+    p.device = 0
+    F = _FakeTensor
+    good = dict(points=F((10, 3), torch.float32), labels=F((10,), torch.int32), out=F((64, 4), torch.float32))
+    sbki.check_noalloc_args(p, **good)
+    bad = [
+        (TypeError, dict(points=F((10, 3), torch.float64))),
+        (TypeError, dict(labels=F((10,), torch.int64))),
+        (TypeError, dict(out=F((64, 4), torch.float16))),
+        (TypeError, dict(out=F((64, 4), torch.float32, cuda=False))),
+        (TypeError, dict(labels=F((10,), torch.int32, device=1))),
+        (TypeError, dict(points=F((10, 3), torch.float32, contiguous=False))),
+        (ValueError, dict(points=F((10, 4), torch.float32))),
+        (ValueError, dict(points=F((30,), torch.float32), labels=F((30,), torch.int32))),
+        (ValueError, dict(labels=F((9,), torch.int32))),
+        (ValueError, dict(out=F((256,), torch.float32))),
+        (ValueError, dict(out=F((64, 3), torch.float32))),
+    ]
+    for err, change in bad:
+        args = dict(good, **change)
+        with pytest.raises(err):
+            sbki.check_noalloc_args(p, **args)
+        with pytest.raises(err):  # the public call checks before it reaches the library
+            sbki.training_set_noalloc(p, args["points"], args["labels"], np.eye(4), args["out"])
