@@ -344,8 +344,11 @@ def batched_form(sb, torch, dev, stream, scans, reps):
 
     from paper_1909_04631_gb300 import autotune
     tuned = autotune.autotune(p, batch, reps=2, stream=stream)
+    shapes, mode = autotune.split_tuning(tuned["tuning"])
+    if mode is not None:
+        p.accumulate_mode = mode
     seq = sb.Map(p, stream=stream)
-    seq.set_tuning(**tuned["tuning"])
+    seq.set_tuning(**shapes)
 
     def run_seq():
         for i in range(n):
@@ -355,7 +358,7 @@ def batched_form(sb, torch, dev, stream, scans, reps):
     ms_seq = timed(run_seq)
     seq.close()
     bat = sb.Map(p, stream=stream)
-    bat.set_tuning(**tuned["tuning"])
+    bat.set_tuning(**shapes)
     st = {}
 
     def run_batch():
@@ -370,9 +373,7 @@ def batched_form(sb, torch, dev, stream, scans, reps):
             "sequential_ms": ms_seq, "batched_ms": ms_batch, "sequential_scans_per_s": n / (ms_seq / 1e3),
             "batched_scans_per_s": n / (ms_batch / 1e3), "speedup": ms_seq / ms_batch,
             "batched_kernels_per_update": launches // (reps + 1), "tuning": tuned["tuning"],
-            "tuning_trials": len(tuned["trials"]),
-            "untuned_batched_ms": next((ms for t, ms in tuned["trials"] if t == dict(
-                accumulate_ctas_per_sm=0, accumulate_chunk=8, touch_ctas_per_sm=8, ingest_ctas_per_sm=16)), None)}
+            "tuning_trials": len(tuned["trials"]), "untuned_batched_ms": tuned.get("default_ms")}
 
 
 def differentiable_form(sb, torch, dev, stream, scans, reps):

@@ -83,6 +83,20 @@ typedef struct sbki_params {
                             * * f(d/l) (the paper's class-dependent signal variance, Sec. V);
                             * entries 0..K must be finite and > 0; sbki_default_params sets 1,
                             * which is Eq. (kernel) as printed.  Unused by the counting model */
+  int32_t association; /* which (voxel, training point) pairs Eq. (alpha_kernel) sums (Sec. IV):
+                        * 0 (default) every voxel centre within l of the point; 1 the paper's
+                        * extended block: a voxel of block b takes the points whose own voxel lies
+                        * in b or one of b's six face neighbours, so pairs reaching b from an edge
+                        * or corner neighbour are left out even when d < l.  Both accumulation
+                        * forms honour it; sbki_backward, sbki_backward_scales and sbki_grad
+                        * refuse 1.  The counting model ignores it */
+  double l_scale[32];  /* per-class length scale: class k's kernel is sigma0 sigma0_scale[k]
+                        * f(d/l_k) with support d < l_k = length_scale * l_scale[k] (Sec. V and VI
+                        * name class-dependent parameters; reading K16).  Entries 0..K finite and
+                        * > 0, l_k <= 0.75 * block_edge * res; sbki_default_params sets 1 (the
+                        * common l).  With any entry other than 1 the update takes the general
+                        * weighted accumulation; the block-major form, extended-block association
+                        * and the differentiable entry points refuse it */
 } sbki_params;
 
 /* Per-insert counters (all for the last insert). */
@@ -138,13 +152,35 @@ sbki_status sbki_sync(sbki_map* map, sbki_stats* stats);
 sbki_status sbki_training_set(sbki_map* map, const float* points, const int32_t* labels, int64_t n,
                               const double sensor_pose[16], float* xyzl_out, int64_t cap, int64_t* count);
 
+/* Soft labels (Sec. III takes the network's most probable class; the paper's
+ * discussion names the softmax output as the richer input; reading K15):
+ * every hit carries a probability vector probs [n,K] float32 over the
+ * occupied classes 1..K (row i for point i; entries finite in [0, 1], at least
+ * one > 0) instead of one label.  Free samples stay class 0 with weight 1.
+ * Downsampling groups hits and samples by (cell, most probable class, ties to
+ * the lowest), so one-hot vectors give the groups of sbki_insert_scan; a
+ * group's representative is the exact centroid with, per class 0..K, the
+ * exact mean of its members' weights rounded once to FP32; the accumulation
+ * adds sigma0 sigma0_scale[k] f(d/l_k) w^k into every class k of every voxel
+ * centre within l_k (Eq. (alpha_kernel) with the one-hot y_i replaced by w).
+ * points and probs may be host or device memory; synchronises the stream.
+ * Needs accumulate_mode 0, association 0 and the common l (all l_scale 1);
+ * stats as sbki_insert_scan (pairs: voxel-point pairs, each counted once). */
+sbki_status sbki_insert_scan_soft(sbki_map* map, const float* points, const float* probs, int64_t n,
+                                  const double sensor_pose[16], sbki_stats* stats);
+/* Steps a1-a3 of sbki_insert_scan_soft only: xyz_out [cap,3] float32 and
+ * w_out [cap,K+1] float32 (host or device, both or neither), ordered as
+ * sbki_training_set; *count as sbki_training_set. */
+sbki_status sbki_training_set_soft(sbki_map* map, const float* points, const float* probs, int64_t n,
+                                   const double sensor_pose[16], float* xyz_out, float* w_out, int64_t cap,
+                                   int64_t* count);
+
 /* The training set of one scan (steps a1-a3, same result as
  * sbki_training_set) with no device allocation and no map.  The paper has no
  * counterpart: this is a deployment variant for callers that cannot allocate
  * device memory while they run - a real-time mapping loop that reserves all of
- * its memory at start-up, a framework that owns the device heap through its
- * own pool allocator, or code recorded into a CUDA graph, where cudaMalloc and
- * cudaFree are not allowed and may synchronise the device.
+ * its memory at start-up (a cudaMalloc can stall or fail mid-run), or a
+ * framework that owns the device heap through its own pool allocator.
  *   params: as for sbki_create_map (pool_blocks, sample_capacity and
  *     track_pairs are ignored); work runs on params->device and, in stream
  *     order, on params->cuda_stream; the call synchronises that stream.
@@ -225,6 +261,13 @@ sbki_status sbki_insert_training(sbki_map* map, const float* xyzl, int64_t p, sb
  * NULL. */
 sbki_status sbki_query_probs(const sbki_map* map, const float* xyz, int64_t q, float* probs, float* var,
                              float* mode, int32_t* label, float* p_occ, int32_t* state);
+
+/* The same contents as sbki_export, computed on the device and written in
+ * pool order (blocks in allocation order; within a block x fastest, then y,
+ * z): keys [cap,3] int64 and alpha [cap,K+1] float32 with prior, each host or
+ * device memory (device buffers get no host copy; the call synchronises the
+ * stream to read the row count).  count-only when both are NULL. */
+sbki_status sbki_export_blocks(const sbki_map* map, int64_t* keys, float* alpha, int64_t cap, int64_t* count);
 
 /* Number of allocated voxels (blocks * block_edge^3). */
 sbki_status sbki_voxel_count(const sbki_map* map, int64_t* count);
@@ -316,6 +359,21 @@ sbki_status sbki_forward_alpha(const sbki_params* params, const float* xyzl, int
                                float* alpha_out, int64_t cap, int64_t* count);
 sbki_status sbki_grad(const sbki_params* params, const float* xyzl, int64_t p, const int64_t* keys,
                       const float* grad_alpha, int64_t count, double* grad_l, double* grad_sigma0, float* grad_xyz);
+
+/* Eq. (alpha_kernel) at arbitrary points of space (Sec. IV: the model can be
+ * queried at any resolution, not only at voxel centres), stateless, from a
+ * training set:  alpha_out[j, k] = alpha0 + sum over training points i with
+ * |pts_j - x_i| < l and label k of sigma0 sigma0_scale[k] f(|pts_j - x_i| / l)
+ * (every point within l: the exact association, whatever params->association
+ * says).  xyzl [p,4] float32 (x, y, z, label as float, labels 0..K); pts [q,3]
+ * float32 world; alpha_out [q,K+1] float32.  Each of the three may be host or
+ * device memory (device pointers are used in stream order on
+ * params->cuda_stream); the call allocates its own work buffers and
+ * synchronises the stream.  Membership as in the map update (exact); sums in
+ * FP32.  The counting model is refused (SBKI_ERR_INVALID_ARG); errors are
+ * reported by sbki_last_error(NULL). */
+sbki_status sbki_query_points(const sbki_params* params, const float* xyzl, int64_t p, const float* pts, int64_t q,
+                              float* alpha_out);
 
 /* Restores contents written by sbki_export into the selected map (a snapshot
  * and resume path): keys [count,3] int64 voxel indices, alpha [count,K+1]

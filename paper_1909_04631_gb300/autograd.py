@@ -27,20 +27,21 @@ def _xyzl(xyz: torch.Tensor, labels: torch.Tensor) -> torch.Tensor:
 
 class SBKIFunction(torch.autograd.Function):
     """(keys, alpha) = S-BKI(xyz, labels; l, sigma0): alpha (with prior) at every
-    voxel of the blocks the training set reaches, sorted by voxel key.  keys is
-    not differentiable; alpha is differentiable in xyz, l and sigma0."""
+    voxel of the blocks the training set reaches, in the map's pool order
+    (blocks in allocation order, x fastest inside a block).  keys is not
+    differentiable; alpha is differentiable in xyz, l and sigma0.  Both stay on
+    the device: forward and backward make no host copy of alpha or its
+    gradient."""
 
     @staticmethod
     def forward(ctx, xyz, labels, l, sigma0, params):
         m = _sb.Map(_params_with(params, l, sigma0))
         xyzl = _xyzl(xyz, labels)
         m.insert_training(xyzl[:, :3], xyzl[:, 3].to(torch.int32))
-        keys, alpha, _ = m.export()
+        kt, at = m.export_blocks(device=xyz.device)
         ctx.m, ctx.xyzl = m, xyzl
-        ctx.keys = keys
+        ctx.keys = kt
         ctx.shapes = (l.shape, sigma0.shape)
-        kt = torch.from_numpy(keys).to(xyz.device)
-        at = torch.from_numpy(alpha).to(xyz.device)
         ctx.mark_non_differentiable(kt)
         return kt, at
 
@@ -48,7 +49,7 @@ class SBKIFunction(torch.autograd.Function):
     def backward(ctx, _gkeys, galpha):
         m = ctx.m
         m.grad_clear()
-        m.grad_add_alpha(ctx.keys, galpha.detach().float().contiguous().cpu().numpy())
+        m.grad_add_alpha(ctx.keys, galpha.detach().float().contiguous())
         gl, gs, gx = m.backward(ctx.xyzl, grad_xyz=ctx.needs_input_grad[0])
         dev = ctx.xyzl.device
         lshape, sshape = ctx.shapes

@@ -16,7 +16,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsbki.so")
 SOURCES = ["scan.cu", "radix_sort.cu", "ingest.cu", "blocks.cu", "accumulate.cu", "accumulate_points.cu", "readoff.cu", "kernel_eval.cu", "backward.cu", "counts.cu", "sbki_api.cu",
-           "noalloc.cu"]
+           "noalloc.cu", "query_points.cu", "soft.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall", "-I", INCLUDE]
 

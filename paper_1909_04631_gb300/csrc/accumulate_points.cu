@@ -63,6 +63,8 @@ struct PtArgs {
   const uint32_t* ftab;  // fast form: [kFastParts^3][ftpad] (X | Y << 8 | Z << 16 row byte offsets in a slot)
   const int32_t* flen;   // [kFastParts^3] entries of each list
   int ftpad;             // entries per fast list (multiple of 32, at most 32 kFastEntries)
+  const uint32_t* ownslot;  // fast form: per training point the hash slot of its own block (touched-block pass)
+  const uint32_t* nbrslot;  // fast form: [hash_cap][32] per own block the hash slots of its touched neighbours
   DevCounters* dc;
 };
 
@@ -98,6 +100,7 @@ __device__ __forceinline__ uint32_t candidate(const PtArgs& a, const WarpTables&
       in = in_support64_call(v0[0] + (int)((ent & 0xffu) >> 3) - a.R, v0[1] + (int)((ent >> 19) & 15u) - a.R,
                              v0[2] + (int)((ent >> 23) & 15u) - a.R, p.x, p.y, p.z, g.res64, g.l2_64);
   }
+  if (g.assoc) in = in && ((kFaceDigits >> (pk & 0xff)) & 1u);  // extended block: own block and face neighbours
   float* base = t.blk[pk & 0xff];
   const float d = d2 * rsqrtf(fmaxf(d2, 1e-30f));
   const float u = fmaxf(__fmaf_rn(-d, g.inv_l, 1.0f), 0.0f);
@@ -213,7 +216,7 @@ struct __align__(256) FastWarp {
   uint32_t ptab[64];                    // pair-count element base per block digit (kTrack)
 };
 // scalars of a slot (int index into its last 64 bytes)
-constexpr int kScPart = 0, kScLabel = 1, kScS0 = 2, kScBlk = 4, kScV0 = 8;
+constexpr int kScPart = 0, kScLabel = 1, kScS0 = 2, kScPool = 3, kScV0 = 8;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ float2 lds_f2(uint32_t a) {
@@ -251,7 +254,7 @@ __device__ __forceinline__ bool band_decide(uint32_t e, const int* sc, const flo
                            l2_64);
 }
 
-template <bool kTrack>
+template <bool kTrack, bool kFace>
 __global__ void __launch_bounds__(kThreads, 4) accumulate_points_fast_kernel(PtArgs a) {
   __shared__ FastWarp s_w[kWarps];
   const Geom& g = a.g;
@@ -270,8 +273,9 @@ __global__ void __launch_bounds__(kThreads, 4) accumulate_points_fast_kernel(PtA
   const int gl = lane / 3, ax = lane - 3 * gl;
   const int axshift = ax == 0 ? 0 : (ax == 1 ? g.B_shift : 2 * g.B_shift);
   const uint32_t dmul = ax == 0 ? 4u : (ax == 1 ? 12u : 36u);
+  const uint32_t K1B3 = (uint32_t)(g.K1 * g.B3);
   const float2 neg_inv_l = make_float2(-g.inv_l, -g.inv_l), one2 = make_float2(1.0f, 1.0f);
-  int cb0 = INT_MIN, cb1 = INT_MIN, cb2 = INT_MIN, cmap = -1;  // block and map the tables belong to
+  int cpool = -1;  // own-block pool slot the tables belong to
   uint32_t npairs = 0;
   const uint32_t chunk = (uint32_t)a.chunk;
   uint32_t c = 0;
@@ -283,8 +287,9 @@ __global__ void __launch_bounds__(kThreads, 4) accumulate_points_fast_kernel(PtA
     const uint32_t c1 = min(P, c * chunk + chunk);
     for (uint32_t g0 = c * chunk; g0 < c1; g0 += kGroup) {
       const uint32_t gn = min(c1 - g0, (uint32_t)kGroup);  // warp-uniform
-      // 1. rows of every point of the group, three lanes per point
-      int pt = 0;
+      // 1. rows of every point of the group, three lanes per point; the lane
+      //    of axis x also reads the hash slot of the point's own block
+      int pt = 0, lw = 0;
       if (gl < (int)gn) {
         const float4 p = a.train[g0 + gl];
         const float xa = ax == 0 ? p.x : (ax == 1 ? p.y : p.z);
@@ -294,11 +299,11 @@ __global__ void __launch_bounds__(kThreads, 4) accumulate_points_fast_kernel(PtA
         const float phi = 0.5f - __fmul_rn(__fadd_rn(hi, lo), g.inv_res);
         pt = min(kFastParts - 1, max(0, floor_small(phi * (float)kFastParts)));
         const int b0 = v0 >> g.B_shift;
-        const int lw = label_of(p.w);
+        lw = label_of(p.w);
         const uint32_t cls = ax == 0 ? (uint32_t)((lw & ((1 << kLabelBits) - 1)) * g.B3) : 0u;
         float2* r = W.rows[gl] + kFastAxis * ax;
         // offsets in a lane-dependent order, so the lanes of one store spread over the banks
-        int j = gl % na;
+        int j = (gl + 2 * ax) % na;
 #pragma unroll
         for (int t = 0; t < kFastAxis - 1; ++t) {
           if (t < na) {
@@ -310,68 +315,57 @@ __global__ void __launch_bounds__(kThreads, 4) accumulate_points_fast_kernel(PtA
           }
         }
         if (ax == 0) r[kFastAxis - 1] = make_float2(kFar, 0.0f);
-        int* sc = reinterpret_cast<int*>(W.rows[gl] + 3 * kFastAxis);
-        sc[kScBlk + ax] = b0;
-        sc[kScV0 + ax] = v0;
-        if (ax == 0) {
-          sc[kScLabel] = lw;
-          sc[kScS0] = __float_as_int(g.sigma0_k[lw & ((1 << kLabelBits) - 1)]);
-        }
+        reinterpret_cast<int*>(W.rows[gl] + 3 * kFastAxis)[kScV0 + ax] = v0;
       }
       const int pty = __shfl_sync(0xffffffffu, pt, min(lane + 1, 31));
       const int ptz = __shfl_sync(0xffffffffu, pt, min(lane + 2, 31));
       if (ax == 0 && gl < (int)gn)
-        reinterpret_cast<int*>(W.rows[gl] + 3 * kFastAxis)[kScPart] = pt + kFastParts * (pty + kFastParts * ptz);
+        *reinterpret_cast<int4*>(reinterpret_cast<int*>(W.rows[gl] + 3 * kFastAxis) + kScPart) =
+            make_int4(pt + kFastParts * (pty + kFastParts * ptz), lw,
+                      __float_as_int(g.sigma0_k[lw & ((1 << kLabelBits) - 1)]), (int)__ldg(a.ownslot + g0 + gl));
       __syncwarp();
-      // 2. point by point: block tables (when the block changes), candidate sweeps
+      // 2. point by point: block tables (when the own block changes), candidate sweeps
       uint32_t ent[kFastEntries];
-      int len = 0;
       {
         const int part = reinterpret_cast<const int*>(W.rows[0] + 3 * kFastAxis)[kScPart];
         const uint32_t* tab = a.ftab + (size_t)part * a.ftpad;
-        len = __ldg(a.flen + part);
 #pragma unroll
-        for (int it = 0; it < kFastEntries; ++it) ent[it] = it * 32 < len ? __ldg(tab + it * 32 + lane) : kPadEntry;
+        for (int it = 0; it < kFastEntries; ++it) ent[it] = __ldg(tab + it * 32 + lane);
       }
       for (uint32_t k = 0; k < gn; ++k) {
         const int* sc = reinterpret_cast<const int*>(W.rows[k] + 3 * kFastAxis);
-        const int4 sb = *reinterpret_cast<const int4*>(sc + kScBlk);
-        const int lw = sc[kScLabel];
-        const float s0 = __int_as_float(sc[kScS0]);
-        const int map = lw >> kLabelBits;
-        // the next point's list, in flight while this one is swept
+        const int4 sv = *reinterpret_cast<const int4*>(sc + kScPart);  // part, label word, s0, own pool slot
+        // the next point's list, in flight while this one is swept (lists are
+        // padded to kFastEntries x 32 entries, so every load is in range)
         uint32_t nent[kFastEntries];
-        int nlen = 0;
-        if (k + 1 < gn) {
-          const int part = reinterpret_cast<const int*>(W.rows[k + 1] + 3 * kFastAxis)[kScPart];
+        {
+          const int part = k + 1 < gn ? sc[kScPart + kSlotBytes / 4] : sv.x;
           const uint32_t* tab = a.ftab + (size_t)part * a.ftpad;
-          nlen = __ldg(a.flen + part);
 #pragma unroll
-          for (int it = 0; it < kFastEntries; ++it)
-            nent[it] = it * 32 < nlen ? __ldg(tab + it * 32 + lane) : kPadEntry;
+          for (int it = 0; it < kFastEntries; ++it) nent[it] = __ldg(tab + it * 32 + lane);
         }
-        if (sb.x != cb0 || sb.y != cb1 || sb.z != cb2 || map != cmap) {  // warp-uniform
-          cb0 = sb.x;
-          cb1 = sb.y;
-          cb2 = sb.z;
-          cmap = map;
+        if (sv.w != cpool) {  // warp-uniform: the tables belong to another block
+          cpool = sv.w;
           __syncwarp();  // every lane is done with the old tables
           if (lane < 27) {
-            const int32_t pool = find_pool_slot(a.hkeys, a.hvals, a.hash_cap,
-                                                pack_block(sb.x - 1 + lane % 3, sb.y - 1 + (lane / 3) % 3,
-                                                           sb.z - 1 + lane / 9, map));
+            // a digit no point of this block touched holds a stale slot; no
+            // in-support pair uses it (every reduction is predicated on membership)
+            const uint32_t hs = a.nbrslot[(size_t)sv.w * 32 + lane] & (uint32_t)(a.hash_cap - 1);
+            const int32_t pool = a.hvals[hs];
             const uint32_t pb = (uint32_t)(pool >= 0 ? pool : a.sink);
-            W.btab[lane] = pb * (uint32_t)(g.K1 * g.B3) - ((4u * (uint32_t)lane) << 24);
+            W.btab[lane] = pb * K1B3 - ((4u * (uint32_t)lane) << 24);
             if (kTrack) W.ptab[lane] = pb * (uint32_t)g.B3 - ((4u * (uint32_t)lane) << 24);
           }
           __syncwarp();
         }
         const uint32_t slot = rows0 + (uint32_t)k * kSlotBytes;
+        const float s0 = __int_as_float(sv.z);
         const float2 s02 = make_float2(s0, s0);
-        const uint32_t cls = (uint32_t)((lw & ((1 << kLabelBits) - 1)) * g.B3);
+        const uint32_t cls = (uint32_t)((sv.y & ((1 << kLabelBits) - 1)) * g.B3);
+        const int len = __ldg(a.flen + sv.x);
 #pragma unroll
         for (int jp = 0; jp < (kFastEntries + 1) / 2; ++jp) {
-          if (jp * 64 < len) {  // warp-uniform
+          if (jp < 2 || jp * 64 < len) {  // warp-uniform; lists hold more than 64 entries
             const uint32_t ea = ent[2 * jp], eb = 2 * jp + 1 < kFastEntries ? ent[2 * jp + 1] : kPadEntry;
             float d2a, d2b;
             uint32_t pka, pkb;
@@ -383,6 +377,10 @@ __global__ void __launch_bounds__(kThreads, 4) accumulate_points_fast_kernel(PtA
               if (bnda) ina = band_decide(ea, sc, a.train, g0 + k, R, g.res64, g.l2_64);
               if (bndb) inb = band_decide(eb, sc, a.train, g0 + k, R, g.res64, g.l2_64);
             }
+            if (kFace) {  // extended block: own block and face neighbours (digit in the top byte, times 4)
+              ina = ina && ((kFaceDigits >> (pka >> 26)) & 1u);
+              inb = inb && ((kFaceDigits >> (pkb >> 26)) & 1u);
+            }
             // kernel of both candidates: f = u^5 Q(u^2), u = 1 - d / l, times sigma0 s_k
             const float2 d = make_float2(sqrt_approx(d2a), sqrt_approx(d2b));
             const float2 u = __ffma2_rn(d, neg_inv_l, one2);
@@ -391,8 +389,8 @@ __global__ void __launch_bounds__(kThreads, 4) accumulate_points_fast_kernel(PtA
             const float2 v = __fmul2_rn(__fmul2_rn(__fmul2_rn(__fmul2_rn(w, w), u), q), s02);
             const uint32_t elema = lds_u32(__byte_perm(pka, btab, 0x7653)) + pka;
             const uint32_t elemb = lds_u32(__byte_perm(pkb, btab, 0x7653)) + pkb;
-            red_add_if(ina, a.alpha + elema, v.x);
-            red_add_if(inb, a.alpha + elemb, v.y);
+            if (ina) atomicAdd(a.alpha + elema, v.x);  // result unused: a reduction
+            if (inb) atomicAdd(a.alpha + elemb, v.y);
             if (kTrack) {
               red_add_if(ina, a.pairs + (lds_u32(__byte_perm(pka, ptab, 0x7653)) + pka - cls), 1);
               red_add_if(inb, a.pairs + (lds_u32(__byte_perm(pkb, ptab, 0x7653)) + pkb - cls), 1);
@@ -402,7 +400,6 @@ __global__ void __launch_bounds__(kThreads, 4) accumulate_points_fast_kernel(PtA
         }
 #pragma unroll
         for (int it = 0; it < kFastEntries; ++it) ent[it] = nent[it];
-        len = nlen;
       }
       __syncwarp();  // the slots are rewritten by the next group
     }
@@ -509,15 +506,19 @@ cudaError_t build_candidate_tables(MapState& m) {
   if (e != cudaSuccess) return e;
   m.ctab_pad = tpad;
   m.ctab_R = Rt;
-  if (na > kFastAxis - 1) return cudaSuccess;  // the fast form needs 2R + 1 <= 7
+  // the fast form needs 2R + 1 <= 7 and l above half the voxel diagonal (a
+  // point's own voxel, hence its own block, is then always touched)
+  if (na > kFastAxis - 1 || lr <= 0.8661) return cudaSuccess;
   // fast form: entry = X row byte offset 8 jx | (64 + 8 jy) << 8 | (128 + 8 jz) << 16
   // inside a point's slot; padding entries name the X padding row
   const int Rf = candidate_lists(lr, kFastParts, lists);
   const int nf = (int)lists.size();
   longest = 0;
   for (auto& L : lists) longest = std::max(longest, L.size());
-  const int fpad = (int)((longest + 31) / 32 * 32);
-  if (fpad > 32 * kFastEntries) return cudaSuccess;
+  // every list holds exactly 32 kFastEntries entries (padding after the
+  // candidates): the sweep loads all of them unconditionally
+  const int fpad = 32 * kFastEntries;
+  if ((int)longest > fpad) return cudaSuccess;
   std::vector<uint32_t> ff((size_t)nf * fpad, kPadEntry);
   std::vector<int32_t> fl(nf);
   for (int t = 0; t < nf; ++t) {
@@ -547,6 +548,12 @@ cudaError_t launch_persistent(Kernel kern, const PtArgs& a, int sm_count, int ct
   if (ctas_per_sm > 0) per_sm = std::min(per_sm, ctas_per_sm);
   kern<<<std::max(1, per_sm) * sm_count, kThreads, 0, st>>>(a);
   return cudaGetLastError();
+}
+
+template <bool kTrack>
+cudaError_t launch_fast(const PtArgs& a, int sm_count, int ctas_per_sm, cudaStream_t st) {
+  return a.g.assoc ? launch_persistent(accumulate_points_fast_kernel<kTrack, true>, a, sm_count, ctas_per_sm, st)
+                   : launch_persistent(accumulate_points_fast_kernel<kTrack, false>, a, sm_count, ctas_per_sm, st);
 }
 
 template <bool kTrack>
@@ -591,14 +598,15 @@ cudaError_t launch_accumulate_points(MapState& m) {
   a.ftab = m.ftab;
   a.flen = m.flen;
   a.ftpad = m.ftab_pad;
+  a.ownslot = m.s.ownslot;
+  a.nbrslot = m.nbrslot;
   a.dc = m.dc;
   m.launches += 2;
   const int cps = m.tune.accumulate_ctas_per_sm;
   // the fast form addresses alpha and the pair counts with 32-bit element indices
-  const bool fast = m.ftab != nullptr && (uint64_t)(m.pool_blocks + 1) * (uint64_t)(m.g.K1 * m.g.B3) <= (1ull << 32);
+  const bool fast = m.ftab != nullptr && m.nbrslot != nullptr && (uint64_t)(m.pool_blocks + 1) * (uint64_t)(m.g.K1 * m.g.B3) <= (1ull << 32);
   if (fast)
-    return m.pairs ? launch_persistent(accumulate_points_fast_kernel<true>, a, m.sm_count, cps, m.stream)
-                   : launch_persistent(accumulate_points_fast_kernel<false>, a, m.sm_count, cps, m.stream);
+    return m.pairs ? launch_fast<true>(a, m.sm_count, cps, m.stream) : launch_fast<false>(a, m.sm_count, cps, m.stream);
   return m.pairs ? launch_general<true>(a, m.sm_count, cps, m.stream)
                  : launch_general<false>(a, m.sm_count, cps, m.stream);
 }

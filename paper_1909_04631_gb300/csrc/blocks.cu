@@ -33,6 +33,8 @@ struct TouchArgs {
   uint32_t* touched;
   uint32_t* fresh;
   uint32_t* blist;
+  uint32_t* ownslot;  // fast accumulation form (or null): per training point, the hash slot of its own block
+  uint32_t* nbrslot;  // [hash_cap][32]: per own block, the hash slots of the neighbour blocks its points touch
   DevCounters* dc;
 };
 
@@ -103,9 +105,29 @@ __device__ int64_t find_block(const TouchArgs& a, unsigned long long key) {
   return -1;
 }
 
+// The support of a point's kernel: the common l, or its class's l_k when
+// classes have their own length scales (reading K16).
+struct Support {
+  float l2_lo, l2_hi;
+  double l2_64;
+};
+__device__ __forceinline__ Support support_of(const Geom& g, int label) {
+  Support s;
+  if (g.lscaled) {
+    s.l2_lo = g.l2k_lo[label];
+    s.l2_hi = g.l2k_hi[label];
+    s.l2_64 = g.l2k_64[label];
+  } else {
+    s.l2_lo = g.l2_lo;
+    s.l2_hi = g.l2_hi;
+    s.l2_64 = g.l2_64;
+  }
+  return s;
+}
+
 // candidate block range of a point: at most 3 blocks per axis (l <= 0.75 B res)
-__device__ void candidate_blocks(const float xs[3], const Geom& g, int blo[3], int bhi[3]) {
-  const float lw = __fmul_rn(sqrtf(g.l2_hi), 1.001f);
+__device__ void candidate_blocks(const float xs[3], const Geom& g, const Support& sup, int blo[3], int bhi[3]) {
+  const float lw = __fmul_rn(sqrtf(sup.l2_hi), 1.001f);
 #pragma unroll
   for (int ax = 0; ax < 3; ++ax) {
     const int vlo = floor_i(__fmul_rn(__fsub_rn(xs[ax], lw), g.inv_res)) - 1;
@@ -125,14 +147,16 @@ struct PointBlocks {
   float xs[3];
   int v0[3], blo[3], nb[3], vn[3][3];
   float m2[3][3];
+  Support sup;
 };
 
 __device__ __forceinline__ void point_blocks(const float4& p, const Geom& g, PointBlocks& pb) {
   pb.xs[0] = p.x;
   pb.xs[1] = p.y;
   pb.xs[2] = p.z;
+  pb.sup = support_of(g, (int)p.w & ((1 << kLabelBits) - 1));
   int bhi[3];
-  candidate_blocks(pb.xs, g, pb.blo, bhi);
+  candidate_blocks(pb.xs, g, pb.sup, pb.blo, bhi);
 #pragma unroll
   for (int ax = 0; ax < 3; ++ax) {
     pb.nb[ax] = bhi[ax] - pb.blo[ax] + 1;
@@ -164,8 +188,8 @@ __device__ __forceinline__ double axis_min64_near(int vn, int first, const Geom&
 // Does candidate block (kx, ky, kz) (indices into the point's ranges) hold a voxel centre within l?
 __device__ bool touches(const PointBlocks& pb, int kx, int ky, int kz, const Geom& g) {
   const float d2 = __fadd_rn(__fadd_rn(pb.m2[0][kx], pb.m2[1][ky]), pb.m2[2][kz]);
-  if (d2 < g.l2_lo) return true;
-  if (!(d2 < g.l2_hi)) return false;
+  if (d2 < pb.sup.l2_lo) return true;
+  if (!(d2 < pb.sup.l2_hi)) return false;
   const int k[3] = {kx, ky, kz};
   double s = 0.0;
 #pragma unroll
@@ -173,7 +197,13 @@ __device__ bool touches(const PointBlocks& pb, int kx, int ky, int kz, const Geo
     const double e = axis_min64_near(pb.vn[ax][k[ax]], (pb.blo[ax] + k[ax]) << g.B_shift, g, pb.xs[ax]);
     s = __dadd_rn(s, __dmul_rn(e, e));
   }
-  return s < g.l2_64;
+  return s < pb.sup.l2_64;
+}
+
+// Extended-block association: only the point's own block and its face neighbours.
+__device__ __forceinline__ bool allowed(const PointBlocks& pb, int kx, int ky, int kz, const Geom& g) {
+  return !g.assoc || face_or_own(pb.blo[0] + kx - (pb.v0[0] >> g.B_shift), pb.blo[1] + ky - (pb.v0[1] >> g.B_shift),
+                                 pb.blo[2] + kz - (pb.v0[2] >> g.B_shift));
 }
 
 // The number of blocks a CTA's threads marked touched first, added with one
@@ -215,6 +245,19 @@ __global__ void __launch_bounds__(256) touch_kernel(TouchArgs a) {
       pb.nb[0] = pb.nb[1] = pb.nb[2] = 0;
       pb.blo[0] = pb.blo[1] = pb.blo[2] = 0;
     }
+    // for the fast accumulation form: the point's own block first (it is always
+    // touched: the fast form needs l above half the voxel diagonal), then per
+    // touched candidate block its hash slot under the own block's digit
+    int64_t own = -1;
+    if (a.ownslot) {
+      const unsigned long long okey =
+          active ? pack_block(pb.v0[0] >> g.B_shift, pb.v0[1] >> g.B_shift, pb.v0[2] >> g.B_shift, map) : kEmpty;
+      const unsigned opeers = __match_any_sync(0xffffffffu, okey);
+      const int oleader = __ffs(opeers) - 1;
+      if (active && oleader == (int)(threadIdx.x & 31u)) own = insert_block<kCount>(a, okey, &nfirst);
+      own = __shfl_sync(0xffffffffu, own, oleader);
+      if (active) a.ownslot[i] = (uint32_t)own;
+    }
     // the warp walks the smallest cube of candidate offsets that covers every lane
     const int mx = __reduce_max_sync(0xffffffffu, (unsigned)pb.nb[0]);
     const int my = __reduce_max_sync(0xffffffffu, (unsigned)pb.nb[1]);
@@ -229,13 +272,28 @@ __global__ void __launch_bounds__(256) touch_kernel(TouchArgs a) {
           ++kz;
         }
       }
-      const bool hit = kx < pb.nb[0] && ky < pb.nb[1] && kz < pb.nb[2] && touches(pb, kx, ky, kz, g);
+      const bool hit = kx < pb.nb[0] && ky < pb.nb[1] && kz < pb.nb[2] && allowed(pb, kx, ky, kz, g) &&
+                       touches(pb, kx, ky, kz, g);
       const unsigned long long key =
           hit ? pack_block(pb.blo[0] + kx, pb.blo[1] + ky, pb.blo[2] + kz, map) : kEmpty;
       const unsigned peers = __match_any_sync(0xffffffffu, key);
-      if (hit && (unsigned)(__ffs(peers) - 1) == (threadIdx.x & 31u)) {
-        const int64_t slot = insert_block<kCount>(a, key, &nfirst);
+      const int leader = __ffs(peers) - 1;
+      int64_t slot = -1;
+      if (hit && leader == (int)(threadIdx.x & 31u)) {
+        slot = insert_block<kCount>(a, key, &nfirst);
         if (kCount && slot >= 0) atomicAdd(&a.hcnt[slot], (uint32_t)__popc(peers));
+      }
+      if (a.ownslot) {  // warp-uniform
+        slot = __shfl_sync(0xffffffffu, slot, leader);
+        // one write per (own block, neighbour): the leader for its own block, other
+        // lanes only when their own block differs from the leader's
+        const int64_t lown = __shfl_sync(0xffffffffu, own, leader);
+        if (hit && own >= 0 && slot >= 0 && (leader == (int)(threadIdx.x & 31u) || own != lown)) {
+          const int digit = (pb.blo[0] + kx - (pb.v0[0] >> g.B_shift) + 1) +
+                            3 * (pb.blo[1] + ky - (pb.v0[1] >> g.B_shift) + 1) +
+                            9 * (pb.blo[2] + kz - (pb.v0[2] >> g.B_shift) + 1);
+          a.nbrslot[(size_t)own * 32 + digit] = (uint32_t)slot;
+        }
       }
     }
   }
@@ -299,7 +357,8 @@ __global__ void __launch_bounds__(256) bin_fill_kernel(TouchArgs a) {
           ++kz;
         }
       }
-      const bool hit = kx < pb.nb[0] && ky < pb.nb[1] && kz < pb.nb[2] && touches(pb, kx, ky, kz, g);
+      const bool hit = kx < pb.nb[0] && ky < pb.nb[1] && kz < pb.nb[2] && allowed(pb, kx, ky, kz, g) &&
+                       touches(pb, kx, ky, kz, g);
       const unsigned long long key =
           hit ? pack_block(pb.blo[0] + kx, pb.blo[1] + ky, pb.blo[2] + kz, map) : kEmpty;
       const unsigned peers = __match_any_sync(0xffffffffu, key);
@@ -432,6 +491,8 @@ TouchArgs touch_args(MapState& m) {
   a.hcnt = m.hcnt;
   a.hcur = m.hcur;
   a.blist = m.blist;
+  a.ownslot = nullptr;
+  a.nbrslot = nullptr;
   a.dc = m.dc;
   return a;
 }
@@ -448,7 +509,11 @@ cudaError_t launch_touch_cells(MapState& m, int64_t bound) {
 }
 
 cudaError_t launch_touch_blocks(MapState& m, const KeyFrame& /*kf*/, int64_t bound) {
-  const TouchArgs a = touch_args(m);
+  TouchArgs a = touch_args(m);
+  if (m.acc_mode == 0 && m.nbrslot && !m.g.lscaled && !m.soft) {  // tables of the fast point-major accumulation
+    a.ownslot = m.s.ownslot;
+    a.nbrslot = m.nbrslot;
+  }
   // bound: the training points never exceed the items of the update
   const int64_t blocks =
       std::max<int64_t>(1, std::min<int64_t>((bound + 255) / 256, (int64_t)m.sm_count * m.tune.touch_ctas_per_sm));

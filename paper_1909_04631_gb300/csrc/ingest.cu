@@ -83,8 +83,27 @@ __device__ __forceinline__ void transform_count_one(const ScanDesc& d, int64_t i
                                                     DevCounters* dc, int tlo[3], int thi[3]) {
   const int64_t li = i - d.off;
   const float px = d.pts[3 * li], py = d.pts[3 * li + 1], pz = d.pts[3 * li + 2];
-  const int lab = d.labels[li];
-  if (lab < 1 || lab > g.K1 - 1) set_error(dc, SBKI_ERR_LABEL_RANGE);
+  int lab;
+  if (d.probs) {
+    // soft labels: the most probable class (ties to the lowest; class 0 has
+    // weight 0 for a hit); every entry finite in [0, 1], at least one above 0
+    const float* pr = d.probs + li * (g.K1 - 1);
+    lab = 0;
+    float best = 0.0f;
+    bool bad = false;
+    for (int k = 1; k < g.K1; ++k) {
+      const float v = pr[k - 1];
+      bad = bad || !(v >= 0.0f && v <= 1.0f);
+      if (v > best) {
+        best = v;
+        lab = k;
+      }
+    }
+    if (bad || lab == 0) set_error(dc, SBKI_ERR_LABEL_RANGE);
+  } else {
+    lab = d.labels[li];
+    if (lab < 1 || lab > g.K1 - 1) set_error(dc, SBKI_ERR_LABEL_RANGE);
+  }
   bool ok = isfinite(px) && isfinite(py) && isfinite(pz);
   unsigned long long c = 0;
   float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -173,7 +192,8 @@ __global__ void __launch_bounds__(256) emit_kernel(const float4* __restrict__ wo
                                                    const unsigned long long* __restrict__ cnt,
                                                    const ScanDesc* __restrict__ desc, int ns, Geom g, KeyFrame kf,
                                                    float4* __restrict__ items, unsigned long long* __restrict__ keys,
-                                                   uint32_t* __restrict__ vals, DevCounters* dc) {
+                                                   uint32_t* __restrict__ vals, uint32_t* __restrict__ hit_src,
+                                                   DevCounters* dc) {
   __shared__ int64_t s_off[kMaxScans + 1];
   for (int t = threadIdx.x; t <= ns; t += blockDim.x) s_off[t] = desc[t].off;
   __syncthreads();
@@ -205,6 +225,7 @@ __global__ void __launch_bounds__(256) emit_kernel(const float4* __restrict__ wo
         items[hpos] = w;
         keys[hpos] = make_key(w.x, w.y, w.z, (int)w.w, g, kf, og, sc, dc);
         vals[hpos] = (uint32_t)hpos;
+        if (hit_src) hit_src[hpos] = (uint32_t)i;  // soft labels: the point whose probabilities the hit carries
         nfree = (uint32_t)((c1 & kFreeMask) - (c0 & kFreeMask));
         fpos = nvalid + (c0 & kFreeMask);
         ex = __fsub_rn(w.x, ox);
@@ -1103,12 +1124,12 @@ cudaError_t launch_transform_count(MapState& m, int ns, int64_t total_n) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_emit(MapState& m, int ns, int64_t total_n, const KeyFrame& kf) {
+cudaError_t launch_emit(MapState& m, int ns, int64_t total_n, const KeyFrame& kf, uint32_t* hit_src) {
   const int64_t warps = (total_n + 31) / 32;
   unsigned blocks = (unsigned)std::min<int64_t>((warps + 7) / 8, (int64_t)m.sm_count * m.tune.ingest_ctas_per_sm);
   if (blocks == 0) blocks = 1;
   emit_kernel<<<blocks, 256, 0, m.stream>>>(m.s.world, m.s.cnt, m.s.desc, ns, m.g, kf, m.s.items, m.s.keys, m.s.vals,
-                                            m.dc);
+                                            hit_src, m.dc);
   m.launches += 1;
   return cudaGetLastError();
 }

@@ -5,6 +5,8 @@
 // free / unknown / occupied state with the thresholds of Sec. V-A.  A voxel
 // with no kernel mass (never reached, or outside every allocated block) reads
 // as the prior alpha_0 and is unknown.
+#include <algorithm>
+
 #include "sbki_internal.cuh"
 
 namespace sbki {
@@ -124,6 +126,57 @@ cudaError_t launch_query(const MapState& m, const float* xyz, int64_t q, float* 
 cudaError_t launch_gather_alpha(const MapState& m, float* out, int64_t nblocks) {
   return cudaMemcpyAsync(out, m.alpha, sizeof(float) * (size_t)nblocks * m.g.K1 * m.g.B3, cudaMemcpyDeviceToDevice,
                          m.stream);
+}
+
+}  // namespace sbki
+
+namespace sbki {
+namespace {
+
+// 1 for every pool block of the selected map (scanned into output rows next)
+__global__ void export_flags_kernel(const unsigned long long* __restrict__ pool_keys, uint32_t nb, int map,
+                                    uint32_t* __restrict__ flags) {
+  for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x)
+    flags[b] = map_of_block(pool_keys[b]) == map ? 1u : 0u;
+}
+
+// One row per voxel of every selected block: key (x, y, z) and alpha with prior.
+__global__ void export_rows_kernel(const unsigned long long* __restrict__ pool_keys, const uint32_t* __restrict__ rowb,
+                                   uint32_t nb, int map, Geom g, const float* __restrict__ alpha, float alpha0,
+                                   int64_t* __restrict__ keys, float* __restrict__ out) {
+  const int64_t total = (int64_t)nb * g.B3;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t b = (uint32_t)(e / g.B3);
+    const int li = (int)(e - (int64_t)b * g.B3);
+    const unsigned long long k = pool_keys[b];
+    if (map_of_block(k) != map) continue;
+    const int64_t row = (int64_t)rowb[b] * g.B3 + li;
+    int32_t bx, by, bz;
+    unpack_block(k, bx, by, bz);
+    if (keys) {
+      keys[3 * row] = (int64_t)bx * g.B + li % g.B;
+      keys[3 * row + 1] = (int64_t)by * g.B + (li / g.B) % g.B;
+      keys[3 * row + 2] = (int64_t)bz * g.B + li / (g.B * g.B);
+    }
+    if (out)
+      for (int c = 0; c < g.K1; ++c)
+        out[row * g.K1 + c] = __fadd_rn(alpha0, alpha[((size_t)b * g.K1 + c) * g.B3 + li]);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_export_rows(const MapState& m, uint32_t nb, uint32_t* rowb, void* scan_tmp, int64_t* keys,
+                               float* out) {
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(((int64_t)nb + 255) / 256, 4096));
+  export_flags_kernel<<<grid, 256, 0, m.stream>>>(m.pool_keys, nb, m.active_map, rowb);
+  cudaError_t e = exclusive_scan_u32(rowb, nb, scan_tmp, m.stream);
+  if (e != cudaSuccess) return e;
+  const int64_t total = (int64_t)nb * m.g.B3;
+  const unsigned g2 = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)m.sm_count * 16));
+  export_rows_kernel<<<g2, 256, 0, m.stream>>>(m.pool_keys, rowb, nb, m.active_map, m.g, m.alpha,
+                                               (float)m.prm.alpha0, keys, out);
+  return cudaGetLastError();
 }
 
 }  // namespace sbki

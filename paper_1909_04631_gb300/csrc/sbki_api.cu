@@ -11,6 +11,8 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "sbki_internal.cuh"
 
 using namespace sbki;
@@ -77,6 +79,29 @@ int64_t floor_div64(int64_t a, int64_t b) {
   return q;
 }
 
+// A named range on the profiler's timeline (NVTX; header-only, a no-op unless a
+// tool is attached): the stages of an update appear beside the kernels.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+// device temporaries of one call, freed (after the stream drains) when it returns
+struct TmpFree {
+  void* p[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaStream_t st = nullptr;
+  ~TmpFree() {
+    bool any = false;
+    for (void* q : p) any = any || q;
+    if (!any) return;
+    cudaStreamSynchronize(st);
+    for (void* q : p)
+      if (q) cudaFree(q);
+  }
+};
+
 template <typename T>
 cudaError_t dalloc(T** p, size_t count) {
   *p = nullptr;
@@ -98,6 +123,7 @@ __global__ void begin_kernel(DevCounters* dc, uint32_t epoch, uint32_t n_points)
   dc->n_new = 0;
   dc->n_slow = 0;
   dc->work_next = 0;
+  dc->n_soft = 0;
   dc->epoch = epoch;
   dc->n_blocks_before = dc->n_blocks;
   for (int a = 0; a < 3; ++a) {
@@ -121,6 +147,7 @@ __global__ void batch_begin_kernel(DevCounters* dc, const ScanDesc* desc, int ns
   dc->n_new = 0;
   dc->n_slow = 0;
   dc->work_next = 0;
+  dc->n_soft = 0;
   dc->epoch = dc->epoch + 1;
   dc->n_blocks_before = dc->n_blocks;
   dc->n_points = (uint32_t)desc[ns].off;
@@ -164,6 +191,18 @@ sbki_status check_params(const sbki_params* p) {
     return fail(nullptr, SBKI_ERR_INVALID_ARG, "sensor_model must be 0 (kernel inference) or 1 (counting)");
   if (p->sensor_model == 1 && p->accumulate_mode != 0)
     return fail(nullptr, SBKI_ERR_INVALID_ARG, "the counting sensor model needs accumulate_mode 0");
+  if (p->association != 0 && p->association != 1)
+    return fail(nullptr, SBKI_ERR_INVALID_ARG, "association must be 0 (every voxel within l) or 1 (extended block)");
+  bool lscaled = false;
+  for (int k = 0; k <= p->num_classes; ++k) {
+    if (!(p->l_scale[k] > 0) || !std::isfinite(p->l_scale[k]))
+      return fail(nullptr, SBKI_ERR_INVALID_ARG, "l_scale[%d] must be finite and > 0", k);
+    if (p->length_scale * p->l_scale[k] > 0.75 * p->block_edge * p->res)
+      return fail(nullptr, SBKI_ERR_INVALID_ARG, "length_scale * l_scale[%d] must be <= 0.75 * block_edge * res", k);
+    lscaled = lscaled || p->l_scale[k] != 1.0;
+  }
+  if (lscaled && p->sensor_model == 0 && (p->accumulate_mode != 0 || p->association != 0))
+    return fail(nullptr, SBKI_ERR_INVALID_ARG, "per-class length scales need accumulate_mode 0 and association 0");
   for (int k = 0; k <= p->num_classes; ++k)
     if (!(p->sigma0_scale[k] > 0) || !std::isfinite(p->sigma0_scale[k]))
       return fail(nullptr, SBKI_ERR_INVALID_ARG, "sigma0_scale[%d] must be finite and > 0", k);
@@ -214,6 +253,19 @@ Geom make_geom(const sbki_params& p) {
   g.B_shift = p.block_edge == 8 ? 3 : 2;
   g.B3 = p.block_edge * p.block_edge * p.block_edge;
   g.label_bits = std::max(1, ceil_log2(g.K1));
+  g.assoc = p.sensor_model == 0 ? p.association : 0;
+  g.lscaled = 0;
+  g.lmax64 = p.length_scale;
+  for (int k = 0; k < 32; ++k) {
+    const bool used = k <= p.num_classes;
+    const double lk = p.length_scale * (used ? p.l_scale[k] : 1.0);
+    if (used && p.l_scale[k] != 1.0) g.lscaled = 1;
+    if (used) g.lmax64 = std::max(g.lmax64, lk);
+    g.inv_lk[k] = (float)(1.0 / lk);
+    g.l2k_lo[k] = (float)(lk * lk * (1.0 - band));
+    g.l2k_hi[k] = (float)(lk * lk * (1.0 + band));
+    g.l2k_64[k] = lk * lk;
+  }
   return g;
 }
 
@@ -261,6 +313,7 @@ void fill_desc(ScanDesc& d, const float* pts, const int32_t* labels, int64_t n, 
     d.org[r] = kf.org[r];
   }
   d.map_id = map;
+  d.probs = nullptr;
 }
 
 cudaError_t free_scratch_points(Scratch& s) {
@@ -288,6 +341,27 @@ sbki_status ensure_point_capacity(MapState& m, int64_t n) {
   CK(&m, dalloc(&s.cnt, cap + 1));
   s.n_cap = cap;  // scan partials are sized at creation for 2^27 entries
   m.scratch_gen += 1;  // recorded graphs name the old buffers
+  return SBKI_OK;
+}
+
+// Buffers of the soft-label path, sized for n input points (allocated on first use).
+sbki_status ensure_soft_capacity(MapState& m, int64_t n) {
+  Scratch& s = m.s;
+  if (!s.softidx) CK(&m, dalloc(&s.softidx, s.s_cap));
+  if (n <= s.soft_cap) return SBKI_OK;
+  CK(&m, cudaStreamSynchronize(m.stream));
+  cudaFree(s.probs);
+  cudaFree(s.hit_src);
+  cudaFree(s.wsoft);
+  s.probs = nullptr;
+  s.hit_src = nullptr;
+  s.wsoft = nullptr;
+  s.soft_cap = 0;
+  const int64_t cap = std::max<int64_t>(n, 1 << 16);
+  CK(&m, dalloc(&s.probs, (size_t)cap * (m.g.K1 - 1)));
+  CK(&m, dalloc(&s.hit_src, cap));
+  CK(&m, dalloc(&s.wsoft, (size_t)cap * m.g.K1));
+  s.soft_cap = cap;
   return SBKI_OK;
 }
 
@@ -332,7 +406,8 @@ void fill_stats(const MapState& m, int64_t n, sbki_stats* st) {
 // Steps a1-a3 on device; leaves the training set in s.train.  On return
 // *nitems holds the number of hits + free samples (0 on a pending error).
 sbki_status run_ingest(MapState& m, const float* points, const int32_t* labels, int64_t n, const double T[16],
-                       KeyFrame& kf, int64_t* nitems, int map) {
+                       KeyFrame& kf, int64_t* nitems, int map, const float* probs = nullptr) {
+  NvtxRange range("sbki: ingest (a1-a3)");
   *nitems = 0;
   for (int i = 0; i < 16; ++i)
     if (!std::isfinite(T[i])) return fail(&m, SBKI_ERR_INVALID_ARG, "sensor_pose has a non-finite entry");
@@ -349,7 +424,16 @@ sbki_status run_ingest(MapState& m, const float* points, const int32_t* labels, 
     CK(&m, cudaMemcpyAsync(m.s.pts, points, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, m.stream));
     dpts = m.s.pts;
   }
-  if (!is_device_ptr(labels)) {
+  const float* dprobs = probs;
+  if (probs) {  // soft labels: probability vectors instead of labels
+    st = ensure_soft_capacity(m, n);
+    if (st != SBKI_OK) return st;
+    if (!is_device_ptr(probs)) {
+      CK(&m, cudaMemcpyAsync(m.s.probs, probs, sizeof(float) * (m.g.K1 - 1) * n, cudaMemcpyHostToDevice, m.stream));
+      dprobs = m.s.probs;
+    }
+    dlab = nullptr;
+  } else if (!is_device_ptr(labels)) {
     CK(&m, cudaMemcpyAsync(m.s.labels, labels, sizeof(int32_t) * n, cudaMemcpyHostToDevice, m.stream));
     dlab = m.s.labels;
   }
@@ -359,6 +443,7 @@ sbki_status run_ingest(MapState& m, const float* points, const int32_t* labels, 
   m.launches += 1;
   kf = scan_frame(m, T);
   fill_desc(m.hdesc[0], dpts, dlab, n, 0, T, kf, map);
+  m.hdesc[0].probs = dprobs;
   m.hdesc[1] = ScanDesc{};
   m.hdesc[1].off = n;
   CK(&m, cudaMemcpyAsync(m.s.desc, m.hdesc, 2 * sizeof(ScanDesc), cudaMemcpyHostToDevice, m.stream));
@@ -373,14 +458,16 @@ sbki_status run_ingest(MapState& m, const float* points, const int32_t* labels, 
   m.hdesc[0].org[1] = kf.org[1];
   m.hdesc[0].org[2] = kf.org[2];
   CK(&m, cudaMemcpyAsync(m.s.desc, m.hdesc, sizeof(ScanDesc), cudaMemcpyHostToDevice, m.stream));
-  CK(&m, launch_emit(m, 1, n, kf));
+  CK(&m, launch_emit(m, 1, n, kf, probs ? m.s.hit_src : nullptr));
   CK(&m, launch_downsample_n(m, kf, *nitems));
+  if (probs) CK(&m, launch_soft_weights(m));
   return SBKI_OK;
 }
 
 sbki_status run_update(MapState& m, const KeyFrame& kf, int64_t bound) {
   if (m.profiling) CK(&m, cudaEventRecord(m.ev[1], m.stream));
   if (m.prm.sensor_model == 1) {  // counting model, Eq. (alpha): the block of each point's voxel
+    NvtxRange range("sbki: counting model (a4, a5)");
     CK(&m, launch_touch_cells(m, bound));
     CK(&m, launch_commit_blocks(m));
     if (m.profiling) CK(&m, cudaEventRecord(m.ev[2], m.stream));
@@ -388,12 +475,19 @@ sbki_status run_update(MapState& m, const KeyFrame& kf, int64_t bound) {
     if (m.profiling) CK(&m, cudaEventRecord(m.ev[3], m.stream));
     return SBKI_OK;
   }
-  CK(&m, launch_touch_blocks(m, kf, bound));
-  CK(&m, launch_commit_blocks(m));
-  if (m.acc_mode == 1) CK(&m, launch_bin_points(m, bound));
+  {
+    NvtxRange range("sbki: touched blocks (a4)");
+    CK(&m, launch_touch_blocks(m, kf, bound));
+    CK(&m, launch_commit_blocks(m));
+    if (m.acc_mode == 1) CK(&m, launch_bin_points(m, bound));
+  }
   if (m.profiling) CK(&m, cudaEventRecord(m.ev[2], m.stream));
-  if (m.acc_mode == 1) CK(&m, launch_accumulate(m, kf));
-  else CK(&m, launch_accumulate_points(m));
+  {
+    NvtxRange range("sbki: accumulation (a5)");
+    if (m.soft || m.g.lscaled) CK(&m, launch_accumulate_weighted(m, m.soft));  // soft labels, per-class l
+    else if (m.acc_mode == 1) CK(&m, launch_accumulate(m, kf));
+    else CK(&m, launch_accumulate_points(m));
+  }
   if (m.profiling) CK(&m, cudaEventRecord(m.ev[3], m.stream));
   return SBKI_OK;
 }
@@ -415,10 +509,10 @@ void profile_collect(MapState& m) {
 }
 
 sbki_status insert_scan_impl(sbki_map* map, const float* points, const int32_t* labels, int64_t n,
-                             const double pose[16], bool sync_end, sbki_stats* stats) {
+                             const double pose[16], bool sync_end, sbki_stats* stats, const float* probs = nullptr) {
   if (!map) return fail(nullptr, SBKI_ERR_INVALID_ARG, "map is NULL");
   MapState& m = map->st;
-  if (n < 0 || (n > 0 && (!points || !labels)) || !pose)
+  if (n < 0 || (n > 0 && (!points || (!labels && !probs))) || !pose)
     return fail(&m, SBKI_ERR_INVALID_ARG, "need n >= 0, points/labels non-NULL for n > 0, pose non-NULL");
   if (n > (1ll << 26)) return fail(&m, SBKI_ERR_INVALID_ARG, "n too large");
   DeviceGuard dg(m.device);
@@ -431,14 +525,16 @@ sbki_status insert_scan_impl(sbki_map* map, const float* points, const int32_t* 
   }
   KeyFrame kf;
   int64_t nitems = 0;
-  sbki_status st = run_ingest(m, points, labels, n, pose, kf, &nitems, m.active_map);
+  sbki_status st = run_ingest(m, points, labels, n, pose, kf, &nitems, m.active_map, probs);
   if (st != SBKI_OK) {
     fill_stats(m, n, &m.last_stats);
     if (stats) *stats = m.last_stats;
     return st;
   }
   if (nitems > 0) {
+    m.soft = probs != nullptr;
     st = run_update(m, kf, nitems);
+    m.soft = false;
     if (st != SBKI_OK) return st;
   }
   if (!sync_end) return SBKI_OK;
@@ -490,6 +586,8 @@ sbki_status sbki_default_params(sbki_params* p) {
   p->cuda_stream = nullptr;
   p->sensor_model = 0;
   for (int k = 0; k < 32; ++k) p->sigma0_scale[k] = 1.0;
+  p->association = 0;
+  for (int k = 0; k < 32; ++k) p->l_scale[k] = 1.0;
   return SBKI_OK;
 }
 
@@ -575,6 +673,12 @@ sbki_status sbki_create_map(const sbki_params* params, sbki_map** out) {
   for (int i = 0; i < 4; ++i)
     if ((ce = cudaEventCreate(&m.ev[i])) != cudaSuccess) return bail("events", ce);
   if ((ce = build_candidate_tables(m)) != cudaSuccess) return bail("candidate tables", ce);
+  if (m.ftab) {
+    if ((ce = dalloc(&m.nbrslot, (size_t)m.hash_cap * 32)) != cudaSuccess) return bail("neighbour slot table", ce);
+    if ((ce = dalloc(&m.s.ownslot, S)) != cudaSuccess) return bail("own block slots", ce);
+    if ((ce = cudaMemsetAsync(m.nbrslot, 0, sizeof(uint32_t) * (size_t)m.hash_cap * 32, m.stream)) != cudaSuccess)
+      return bail("neighbour slot init", ce);
+  }
   if ((ce = cudaStreamSynchronize(m.stream)) != cudaSuccess) return bail("create sync", ce);
   std::memset(m.hc, 0, sizeof(DevCounters));
   *out = map;
@@ -587,7 +691,7 @@ void sbki_destroy_map(sbki_map* map) {
   {
     DeviceGuard dg(m.device);
     if (m.stream || m.dc) cudaStreamSynchronize(m.stream);
-    void* ptrs[] = {m.clen, m.ftab, m.flen, m.gpool, m.dacc, m.ctab, m.hkeys, m.hvals, m.hmark, m.hcnt, m.hcur, m.boff, m.blist, m.alpha, m.pool_keys, m.pairs, m.dc, m.s.items, m.s.sitems, m.s.keys, m.s.keys2,
+    void* ptrs[] = {m.clen, m.ftab, m.flen, m.nbrslot, m.s.ownslot, m.s.probs, m.s.hit_src, m.s.softidx, m.s.wsoft, m.gpool, m.dacc, m.ctab, m.hkeys, m.hvals, m.hmark, m.hcnt, m.hcur, m.boff, m.blist, m.alpha, m.pool_keys, m.pairs, m.dc, m.s.items, m.s.sitems, m.s.keys, m.s.keys2,
                     m.s.vals, m.s.vals2, m.s.flags, m.s.seg_start, m.s.train, m.s.hist, m.s.scan_tmp, m.s.touched, m.s.fresh, m.s.bbox, m.s.slow, m.s.carry,
                     m.s.desc};
     for (void* p : ptrs)
@@ -607,6 +711,61 @@ void sbki_destroy_map(sbki_map* map) {
 sbki_status sbki_insert_scan(sbki_map* map, const float* points, const int32_t* labels, int64_t n,
                              const double sensor_pose[16], sbki_stats* stats) {
   return insert_scan_impl(map, points, labels, n, sensor_pose, true, stats);
+}
+
+sbki_status sbki_insert_scan_soft(sbki_map* map, const float* points, const float* probs, int64_t n,
+                                  const double sensor_pose[16], sbki_stats* stats) {
+  if (!map) return fail(nullptr, SBKI_ERR_INVALID_ARG, "map is NULL");
+  MapState& m = map->st;
+  if (m.prm.sensor_model != 0 || m.acc_mode != 0 || m.prm.association != 0 || m.g.lscaled)
+    return fail(&m, SBKI_ERR_INVALID_ARG,
+                "soft labels need the kernel model, accumulate_mode 0, association 0 and the common l");
+  if (n > 0 && !probs) return fail(&m, SBKI_ERR_INVALID_ARG, "probs is NULL");
+  return insert_scan_impl(map, points, nullptr, n, sensor_pose, true, stats, probs);
+}
+
+sbki_status sbki_training_set_soft(sbki_map* map, const float* points, const float* probs, int64_t n,
+                                   const double sensor_pose[16], float* xyz_out, float* w_out, int64_t cap,
+                                   int64_t* count) {
+  if (!map) return fail(nullptr, SBKI_ERR_INVALID_ARG, "map is NULL");
+  MapState& m = map->st;
+  if (n < 0 || (n > 0 && (!points || !probs)) || !sensor_pose || !count || cap < 0 ||
+      (cap > 0 && (!xyz_out || !w_out)))
+    return fail(&m, SBKI_ERR_INVALID_ARG, "bad arguments");
+  DeviceGuard dg(m.device);
+  *count = 0;
+  if (n == 0) return SBKI_OK;
+  KeyFrame kf;
+  int64_t nitems = 0;
+  sbki_status st = run_ingest(m, points, nullptr, n, sensor_pose, kf, &nitems, 0, probs);
+  if (st != SBKI_OK) return st;
+  st = read_counters(m);
+  if (st != SBKI_OK) return st;
+  if (m.hc->err != 0) return status_from_device(m);
+  const int64_t P = nitems > 0 ? m.hc->n_train : 0;
+  *count = P;
+  const int64_t c = std::min(P, cap);
+  if (c > 0) {
+    const bool dev = is_device_ptr(xyz_out) && is_device_ptr(w_out);
+    float *dx = xyz_out, *dw = w_out;
+    TmpFree tf;
+    tf.st = m.stream;
+    if (!dev) {
+      CK(&m, cudaMalloc(&tf.p[0], sizeof(float) * 3 * c));
+      CK(&m, cudaMalloc(&tf.p[1], sizeof(float) * m.g.K1 * c));
+      dx = static_cast<float*>(tf.p[0]);
+      dw = static_cast<float*>(tf.p[1]);
+    }
+    CK(&m, launch_soft_export(m, dx, dw, c));
+    if (!dev) {
+      CK(&m, cudaMemcpyAsync(xyz_out, dx, sizeof(float) * 3 * c, cudaMemcpyDeviceToHost, m.stream));
+      CK(&m, cudaMemcpyAsync(w_out, dw, sizeof(float) * m.g.K1 * c, cudaMemcpyDeviceToHost, m.stream));
+    }
+    CK(&m, cudaStreamSynchronize(m.stream));
+  }
+  if (P > cap) return fail(&m, SBKI_ERR_CAPACITY, "training set has %lld points, cap %lld", (long long)P,
+                           (long long)cap);
+  return SBKI_OK;
 }
 
 sbki_status sbki_get_tuning(const sbki_map* map, sbki_tuning* out) {
@@ -643,6 +802,7 @@ sbki_status sbki_select_map(sbki_map* map, int32_t map_id) {
 }
 
 sbki_status sbki_insert_batch(sbki_map* map, const sbki_scan* scans, int32_t count, sbki_stats* stats) {
+  NvtxRange range("sbki: batched update (a9)");
   if (!map) return fail(nullptr, SBKI_ERR_INVALID_ARG, "map is NULL");
   MapState& m = map->st;
   if (!scans || count < 1 || count > kMaxScans)
@@ -879,6 +1039,7 @@ sbki_status sbki_insert_training(sbki_map* map, const float* xyzl, int64_t p, sb
 
 sbki_status sbki_query_probs(const sbki_map* cmap, const float* xyz, int64_t q, float* probs, float* var,
                              float* mode, int32_t* label, float* p_occ, int32_t* state) {
+  NvtxRange range("sbki: read-off (a6)");
   if (!cmap) return fail(nullptr, SBKI_ERR_INVALID_ARG, "map is NULL");
   sbki_map* map = const_cast<sbki_map*>(cmap);
   MapState& m = map->st;
@@ -953,6 +1114,44 @@ sbki_status sbki_voxel_count(const sbki_map* cmap, int64_t* count) {
   int64_t mine = 0;
   for (unsigned long long k : bkeys) mine += map_of_block(k) == m.active_map ? 1 : 0;
   *count = mine * m.g.B3;
+  return SBKI_OK;
+}
+
+sbki_status sbki_export_blocks(const sbki_map* cmap, int64_t* keys, float* alpha, int64_t cap, int64_t* count) {
+  if (!cmap || !count || cap < 0) return fail(nullptr, SBKI_ERR_INVALID_ARG, "bad arguments");
+  MapState& m = const_cast<sbki_map*>(cmap)->st;
+  DeviceGuard dg(m.device);
+  sbki_status st = read_counters(m);
+  if (st != SBKI_OK) return st;
+  const uint32_t nb = m.hc->n_blocks;
+  *count = 0;
+  if (nb == 0) return SBKI_OK;
+  uint32_t* rowb = m.boff;  // [hash_cap + 1] >= nb + 1 (free between updates)
+  CK(&m, launch_export_rows(m, nb, rowb, m.s.scan_tmp, nullptr, nullptr));
+  uint32_t nsel = 0;
+  CK(&m, cudaMemcpyAsync(&nsel, rowb + nb, sizeof(nsel), cudaMemcpyDeviceToHost, m.stream));
+  CK(&m, cudaStreamSynchronize(m.stream));
+  *count = (int64_t)nsel * m.g.B3;
+  if (!keys && !alpha) return SBKI_OK;
+  if (cap < *count)
+    return fail(&m, SBKI_ERR_CAPACITY, "export needs %lld rows, cap %lld", (long long)*count, (long long)cap);
+  const bool dk = !keys || is_device_ptr(keys), da = !alpha || is_device_ptr(alpha);
+  TmpFree tf;
+  tf.st = m.stream;
+  int64_t* ko = keys;
+  float* ao = alpha;
+  if (!dk) {
+    CK(&m, cudaMalloc(&tf.p[0], sizeof(int64_t) * 3 * *count));
+    ko = static_cast<int64_t*>(tf.p[0]);
+  }
+  if (!da) {
+    CK(&m, cudaMalloc(&tf.p[1], sizeof(float) * m.g.K1 * *count));
+    ao = static_cast<float*>(tf.p[1]);
+  }
+  CK(&m, launch_export_rows(m, nb, rowb, m.s.scan_tmp, ko, ao));
+  if (!dk) CK(&m, cudaMemcpyAsync(keys, ko, sizeof(int64_t) * 3 * *count, cudaMemcpyDeviceToHost, m.stream));
+  if (!da) CK(&m, cudaMemcpyAsync(alpha, ao, sizeof(float) * m.g.K1 * *count, cudaMemcpyDeviceToHost, m.stream));
+  CK(&m, cudaStreamSynchronize(m.stream));
   return SBKI_OK;
 }
 
@@ -1071,18 +1270,6 @@ sbki_status device_input(MapState& m, const T* src, size_t count, const T** dst,
   return SBKI_OK;
 }
 
-struct TmpFree {
-  void* p[4] = {nullptr, nullptr, nullptr, nullptr};
-  cudaStream_t st = nullptr;
-  ~TmpFree() {
-    bool any = false;
-    for (void* q : p) any = any || q;
-    if (!any) return;
-    cudaStreamSynchronize(st);
-    for (void* q : p)
-      if (q) cudaFree(q);
-  }
-};
 
 }  // namespace
 
@@ -1102,6 +1289,7 @@ sbki_status sbki_grad_clear(sbki_map* map) {
 
 sbki_status sbki_heldout_loglik(sbki_map* map, const float* xyz, const int32_t* labels, int64_t h,
                                 int32_t accumulate_grad, double* loglik) {
+  NvtxRange range("sbki: held-out log-likelihood (a7)");
   if (!map) return fail(nullptr, SBKI_ERR_INVALID_ARG, "map is NULL");
   MapState& m = map->st;
   if (h < 0 || (h > 0 && (!xyz || !labels)) || !loglik) return fail(&m, SBKI_ERR_INVALID_ARG, "bad arguments");
@@ -1164,6 +1352,10 @@ static sbki_status backward_impl(sbki_map* map, const float* xyzl, int64_t p, do
   if (p < 0 || (p > 0 && !xyzl)) return fail(&m, SBKI_ERR_INVALID_ARG, "bad arguments");
   if (m.prm.sensor_model != 0)
     return fail(&m, SBKI_ERR_INVALID_ARG, "the counting sensor model has no kernel to differentiate");
+  if (m.prm.association != 0)
+    return fail(&m, SBKI_ERR_INVALID_ARG, "the backward pass takes the exact association (association 0)");
+  if (m.g.lscaled)
+    return fail(&m, SBKI_ERR_INVALID_ARG, "the backward pass takes the common length scale (all l_scale 1)");
   DeviceGuard dg(m.device);
   sbki_status st = ensure_grad(m);
   if (st != SBKI_OK) return st;
@@ -1203,6 +1395,7 @@ static sbki_status backward_impl(sbki_map* map, const float* xyzl, int64_t p, do
 
 sbki_status sbki_backward(sbki_map* map, const float* xyzl, int64_t p, double* grad_l, double* grad_sigma0,
                           float* grad_xyz) {
+  NvtxRange range("sbki: backward (a8)");
   return backward_impl(map, xyzl, p, grad_l, grad_sigma0, grad_xyz, nullptr);
 }
 

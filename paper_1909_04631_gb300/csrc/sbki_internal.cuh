@@ -50,6 +50,7 @@ struct DevCounters {
   uint32_t n_points;                  // input points of the update (all scans)
   int32_t tbox[6];                    // ds-tile bounding box of the kept hits (min xyz, max xyz)
   uint32_t acc_next;                  // work queue head of the point-major accumulation (reset before it)
+  uint32_t n_soft;                    // soft labels: training points with a weight row, this scan
 };
 
 // ---------------------------------------------------------------- geometry constants
@@ -71,7 +72,22 @@ struct Geom {
   int K1;                  // classes incl. free
   int B, B_shift, B3;      // block edge (power of two), log2, B^3
   int label_bits;          // bits for a label in a sort key
+  int assoc;               // 1: extended-block association (a voxel takes points of its block and face neighbours)
+  int lscaled;             // 1: some class has its own length scale (l_scale[k] != 1)
+  float inv_lk[32];        // per class: fp32(1 / l_k), l_k = l * l_scale[k]
+  float l2k_lo[32], l2k_hi[32];  // per class: l_k^2 (1 -/+ band)
+  double l2k_64[32];       // per class: l_k^2
+  double lmax64;           // largest l_k of the classes 0..K
 };
+
+// Extended-block association (Sec. IV): a pair counts only when the voxel's
+// block is the point's own block or one of its six face neighbours.  Block
+// digits d = dx + 3 dy + 9 dz (each of dx, dy, dz in 0..2, 1 = the own block's
+// coordinate): the own block is 13, the faces 4, 10, 12, 14, 16, 22.
+constexpr uint32_t kFaceDigits = (1u << 13) | (1u << 4) | (1u << 10) | (1u << 12) | (1u << 14) | (1u << 16) | (1u << 22);
+__host__ __device__ inline bool face_or_own(int dx, int dy, int dz) {  // block offsets in -1..1
+  return (dx < 0 ? -dx : dx) + (dy < 0 ? -dy : dy) + (dz < 0 ? -dz : dz) <= 1;
+}
 
 // Per-scan key frame: training-point tiles are packed relative to an origin tile.
 struct KeyFrame {
@@ -93,6 +109,7 @@ struct ScanDesc {
   float o[3];             // fp32 sensor origin
   int32_t org[3];         // key-frame origin tile
   int32_t map_id;         // target map of the handle
+  const float* probs;     // soft labels: [n,K] probability vectors over classes 1..K (device), else null
 };
 
 // ---------------------------------------------------------------- scratch of one map
@@ -125,6 +142,13 @@ struct Scratch {
   uint32_t* slow = nullptr;       // [s_cap + 2] downsampling cells left to the slow exact mean
   void* carry = nullptr;          // [2 seg_tiles(s_cap)] partial sums of cells crossing a segment tile
   ScanDesc* desc = nullptr;       // [kMaxScans + 1] scans of the current update
+  uint32_t* ownslot = nullptr;    // [s_cap] fast accumulation form: hash slot of each training point's own block
+  // soft labels (allocated on first use)
+  float* probs = nullptr;         // [n_cap, K] staged host probability vectors
+  uint32_t* hit_src = nullptr;    // [n_cap] global point index of each kept hit (by hit rank)
+  int32_t* softidx = nullptr;     // [s_cap] weight row of each training point, -1 for none (one-hot label)
+  float* wsoft = nullptr;         // [soft_cap, K+1] weight rows
+  int64_t soft_cap = 0;           // point capacity the soft buffers were sized for
 };
 
 // ---------------------------------------------------------------- the map
@@ -157,6 +181,7 @@ struct MapState {
   sbki_status sticky = SBKI_OK;
   int64_t launches = 0;                 // kernels launched on this map
   int acc_mode = 0;                     // 0: point-major (global reductions), 1: block-major (shared tile)
+  bool soft = false;                    // the update in progress carries soft labels
   int active_map = 0;                   // map index the single-map calls act on
   sbki_tuning tune{0, 20, 8, 16};       // launch shapes (sbki_set_tuning)
   cudaStream_t rec_stream = nullptr;    // private stream the batched update is recorded on
@@ -170,6 +195,8 @@ struct MapState {
   uint32_t* ftab = nullptr;             // fast accumulation form's candidate lists (2R + 1 <= 7), or null
   int32_t* flen = nullptr;              // their entry counts
   int ftab_pad = 0;
+  uint32_t* nbrslot = nullptr;          // fast form: [hash_cap][32] per own block (hash slot), the hash slots of the
+                                        // neighbour blocks its points touched in the last update, by block digit
   float* gpool = nullptr;               // dL/dalpha [pool_blocks][K1][B3] (differentiable form, on first use)
   double* dacc = nullptr;               // [4 + 32]: held-out LL, sum s G f, sum s G u^4 D d, keys missed (as
                                         // u64), then sum G f per class
@@ -303,7 +330,7 @@ cudaError_t radix_wait_selftest(unsigned long long* keys, uint32_t* vals, unsign
 // ingest.cu
 // ingest of the ns scans described in m.s.desc (ns + 1 entries, the last holding the total)
 cudaError_t launch_transform_count(MapState& m, int ns, int64_t total_n);
-cudaError_t launch_emit(MapState& m, int ns, int64_t total_n, const KeyFrame& kf);
+cudaError_t launch_emit(MapState& m, int ns, int64_t total_n, const KeyFrame& kf, uint32_t* hit_src = nullptr);
 cudaError_t launch_downsample_n(MapState& m, const KeyFrame& kf, int64_t nitems);
 cudaError_t launch_train_bbox(MapState& m, const float4* in, int64_t p, int* bbox_dev);
 cudaError_t launch_train_prepare(MapState& m, const float4* in, int64_t p, const KeyFrame& kf);
@@ -332,9 +359,18 @@ cudaError_t launch_backward(const MapState& m, const float4* xyzl, int64_t p, co
                             float* grad_xyz, double* acc_class);
 size_t accumulate_smem_bytes(const Geom& g);
 
+// soft.cu: weight rows of the groups holding hits (soft labels), their export,
+// and the weighted accumulation (soft labels and/or per-class length scales)
+cudaError_t launch_soft_weights(MapState& m);
+cudaError_t launch_soft_export(MapState& m, float* xyz, float* w, int64_t cap);
+cudaError_t launch_accumulate_weighted(MapState& m, bool soft);
+
 // readoff.cu
 cudaError_t launch_query(const MapState& m, const float* xyz, int64_t q, float* probs, float* var, float* mode,
                          int32_t* label, float* p_occ, int32_t* state);
 cudaError_t launch_gather_alpha(const MapState& m, float* out, int64_t nblocks);
+// rows of the selected map's blocks in pool order: rowb [nb + 1] work (scanned block row offsets)
+cudaError_t launch_export_rows(const MapState& m, uint32_t nb, uint32_t* rowb, void* scan_tmp, int64_t* keys,
+                               float* out);
 
 }  // namespace sbki

@@ -25,7 +25,8 @@ EXPORTED = ["sbki_default_params", "sbki_create_map", "sbki_destroy_map", "sbki_
             "sbki_voxel_count", "sbki_export", "sbki_profile", "sbki_profile_read", "sbki_kernel_values", "sbki_last_error", "sbki_status_string",
             "sbki_training_set_noalloc", "sbki_grad_clear", "sbki_heldout_loglik", "sbki_grad_add_alpha",
             "sbki_backward", "sbki_forward_alpha", "sbki_grad", "sbki_insert_batch", "sbki_select_map",
-            "sbki_get_tuning", "sbki_set_tuning", "sbki_import", "sbki_selftest_bounded_wait", "sbki_backward_scales"]
+            "sbki_get_tuning", "sbki_set_tuning", "sbki_import", "sbki_selftest_bounded_wait", "sbki_backward_scales",
+            "sbki_query_points", "sbki_insert_scan_soft", "sbki_training_set_soft", "sbki_export_blocks"]
 
 
 class SbkiError(RuntimeError):
@@ -41,7 +42,8 @@ class Params(C.Structure):
                [("num_classes", C.c_int32), ("block_edge", C.c_int32), ("pool_blocks", C.c_int64),
                 ("sample_capacity", C.c_int64), ("track_pairs", C.c_int32), ("device", C.c_int32),
                 ("accumulate_mode", C.c_int32), ("num_maps", C.c_int32),
-                ("cuda_stream", C.c_void_p), ("sensor_model", C.c_int32), ("sigma0_scale", C.c_double * 32)]
+                ("cuda_stream", C.c_void_p), ("sensor_model", C.c_int32), ("sigma0_scale", C.c_double * 32),
+                ("association", C.c_int32), ("l_scale", C.c_double * 32)]
 
 
 class Scan(C.Structure):
@@ -118,6 +120,10 @@ def load(build_if_missing: bool = True):
         L.sbki_backward_scales.argtypes = [vp, vp, i64, vp]
         L.sbki_forward_alpha.argtypes = [P(Params), vp, i64, vp, vp, i64, P(i64)]
         L.sbki_grad.argtypes = [P(Params), vp, i64, vp, vp, i64, P(C.c_double), P(C.c_double), vp]
+        L.sbki_query_points.argtypes = [P(Params), vp, i64, vp, i64, vp]
+        L.sbki_insert_scan_soft.argtypes = [vp, vp, vp, i64, vp, P(Stats)]
+        L.sbki_export_blocks.argtypes = [vp, vp, vp, i64, P(i64)]
+        L.sbki_training_set_soft.argtypes = [vp, vp, vp, i64, vp, vp, vp, i64, P(i64)]
         L.sbki_voxel_count.argtypes = [vp, P(i64)]
         L.sbki_export.argtypes = [vp, vp, vp, vp, i64, P(i64)]
         L.sbki_last_error.argtypes = [vp]
@@ -135,7 +141,8 @@ def load(build_if_missing: bool = True):
                   "sbki_export", "sbki_training_set_noalloc", "sbki_grad_clear", "sbki_heldout_loglik",
                   "sbki_grad_add_alpha", "sbki_backward", "sbki_forward_alpha", "sbki_grad", "sbki_insert_batch",
                   "sbki_select_map", "sbki_get_tuning", "sbki_set_tuning", "sbki_import",
-                  "sbki_selftest_bounded_wait", "sbki_backward_scales"):
+                  "sbki_selftest_bounded_wait", "sbki_backward_scales", "sbki_query_points", "sbki_insert_scan_soft",
+                  "sbki_training_set_soft", "sbki_export_blocks"):
             getattr(L, f).restype = C.c_int
         _lib = L
         return L
@@ -146,12 +153,13 @@ def set_param(p: Params, k: str, v) -> None:
     0..len-1; the remaining entries keep their values)."""
     if not hasattr(p, k):
         raise TypeError("unknown parameter %r" % k)
-    if k == "sigma0_scale":
+    if k in ("sigma0_scale", "l_scale"):
         vals = [float(x) for x in v]
         if len(vals) > 32:
             raise ValueError("at most 32 classes")
+        arr = getattr(p, k)
         for i, x in enumerate(vals):
-            p.sigma0_scale[i] = x
+            arr[i] = x
         return
     setattr(p, k, v)
 
@@ -233,6 +241,30 @@ def forward_alpha(params: Params, xyzl):
     if st != OK:
         raise SbkiError(st, L.sbki_last_error(None).decode())
     return keys[:cnt.value], alpha[:cnt.value]
+
+
+def query_points(params: Params, xyzl, pts, out=None):
+    """Eq. (alpha_kernel) at arbitrary points pts [q,3] from a training set xyzl
+    [p,4] (stateless): alpha [q,K+1] float32.  numpy arrays or CUDA tensors;
+    out (optional) receives the result in place."""
+    L = load()
+    x = _as(xyzl, np.float32, 4)
+    q = _as(pts, np.float32, 3)
+    K1 = params.num_classes + 1
+    nq = q.shape[0]
+    if out is None:
+        if hasattr(q, "data_ptr"):
+            import torch
+            out = torch.empty((nq, K1), dtype=torch.float32, device=q.device)
+        else:
+            out = np.empty((nq, K1), np.float32)
+    xp, k1 = _ptr(x)
+    qp, k2 = _ptr(q)
+    op, k3 = _ptr(out)
+    st = L.sbki_query_points(C.byref(params), xp, x.shape[0], qp, nq, op)
+    if st != OK:
+        raise SbkiError(st, L.sbki_last_error(None).decode())
+    return out
 
 
 def grad(params: Params, xyzl, keys, grad_alpha):
@@ -378,6 +410,38 @@ class Map:
                                               out.ctypes.data_as(C.c_void_p), cap, C.byref(cnt)))
         P = cnt.value
         return out[:P, :3].copy(), out[:P, 3].astype(np.int32)
+
+    def insert_scan_soft(self, points, probs, pose):
+        """One scan update with soft labels: probs [n,K] float32 over classes 1..K."""
+        pts = _as(points, np.float32, 3)
+        n = pts.shape[0]
+        pr = _as(probs, np.float32, int(self.params.num_classes))
+        T = np.ascontiguousarray(pose, dtype=np.float64).reshape(16)
+        pp, k1 = _ptr(pts)
+        qp, k2 = _ptr(pr)
+        s = Stats()
+        self._check(self._L.sbki_insert_scan_soft(self._h, pp, qp, n, T.ctypes.data_as(C.c_void_p), C.byref(s)))
+        return s.as_dict()
+
+    def training_set_soft(self, points, probs, pose, cap=None):
+        """(xyz float32 [P,3], weights float32 [P,K+1]) of a scan with soft labels, host arrays."""
+        pts = _as(points, np.float32, 3)
+        n = pts.shape[0]
+        pr = _as(probs, np.float32, int(self.params.num_classes))
+        T = np.ascontiguousarray(pose, dtype=np.float64).reshape(16)
+        pp, k1 = _ptr(pts)
+        qp, k2 = _ptr(pr)
+        if cap is None:
+            cap = int(self.params.sample_capacity)
+        K1 = int(self.params.num_classes) + 1
+        xyz = np.empty((max(cap, 1), 3), np.float32)
+        w = np.empty((max(cap, 1), K1), np.float32)
+        cnt = C.c_int64()
+        self._check(self._L.sbki_training_set_soft(self._h, pp, qp, n, T.ctypes.data_as(C.c_void_p),
+                                                   xyz.ctypes.data_as(C.c_void_p), w.ctypes.data_as(C.c_void_p),
+                                                   cap, C.byref(cnt)))
+        P = cnt.value
+        return xyz[:P].copy(), w[:P].copy()
 
     def insert_training(self, xyz, labels):
         """Eq. (alpha_kernel) for a given training set (world xyz, labels 0..K)."""
@@ -539,6 +603,26 @@ class Map:
         kp, k1 = _ptr(k)
         ap, k2 = _ptr(a)
         self._check(self._L.sbki_import(self._h, kp, ap, k.shape[0]))
+
+    def export_blocks(self, device=None):
+        """(keys int64 [n,3], alpha float32 [n,K+1]) of the selected map in pool
+        order, computed on the device; CUDA tensors on `device` (a torch device)
+        when given, else numpy arrays."""
+        cnt = C.c_int64()
+        self._check(self._L.sbki_export_blocks(self._h, None, None, 0, C.byref(cnt)))
+        n = cnt.value
+        if device is not None:
+            import torch
+            keys = torch.empty((n, 3), dtype=torch.int64, device=device)
+            alpha = torch.empty((n, self.K1), dtype=torch.float32, device=device)
+        else:
+            keys = np.empty((n, 3), np.int64)
+            alpha = np.empty((n, self.K1), np.float32)
+        if n > 0:
+            kp, k1 = _ptr(keys)
+            ap, k2 = _ptr(alpha)
+            self._check(self._L.sbki_export_blocks(self._h, kp, ap, n, C.byref(cnt)))
+        return keys, alpha
 
     def export(self, pairs=False):
         """(keys int64 [n,3], alpha float32 [n,K+1], pairs int32 [n] or None), sorted by key."""

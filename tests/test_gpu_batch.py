@@ -157,6 +157,10 @@ def test_tuning_changes_speed_not_results(sb, scans):
     res = autotune.autotune(_params(sb, 3), _as_batch(scans[:3], [0, 1, 2]),
                             candidates=dict(accumulate_ctas_per_sm=(0, 2), accumulate_chunk=(4,), touch_ctas_per_sm=(8,),
                                             ingest_ctas_per_sm=(16,)), reps=1)
-    assert len(res["trials"]) == 2 and res["tuning"] in [t for t, _ in res["trials"]] and res["ms"] > 0
+    # two shapes in each accumulation form, and the library's default shape timed beside them
+    assert len(res["trials"]) == 4 and res["tuning"] in [t for t, _ in res["trials"]] and res["ms"] > 0
+    assert {t["accumulate_mode"] for t, _ in res["trials"]} == {0, 1} and res["default_ms"] > 0
+    shapes, mode = autotune.split_tuning(res["tuning"])
+    assert mode in (0, 1) and "accumulate_mode" not in shapes
     with pytest.raises(sb.SbkiError):
         sb.Map(_params(sb, 1)).set_tuning(accumulate_chunk=0)

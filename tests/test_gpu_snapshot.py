@@ -63,3 +63,27 @@ def test_export_import_roundtrip_and_resume(sb):
     b.import_(keys[:10], np.full((10, alpha.shape[1]), 0.5, np.float32))
     qk = ((keys[:10] + 0.5) * scenes.SMALL_SCENE_PARAMS["res"]).astype(np.float32)
     np.testing.assert_allclose(b.query(qk)["probs"], 1.0 / alpha.shape[1], rtol=1e-6)
+
+
+def test_device_export_in_pool_order_equals_the_sorted_export(sb):
+    """sbki_export_blocks (device rows in pool order) holds exactly the rows of
+    sbki_export (host, sorted by key), for the selected map of a multi-map
+    handle, into device and into host buffers."""
+    import torch
+    scans = [scenes.small_region_scan(s, n_az=50, n_el=30) for s in range(2)]
+    m = sb.Map(_params(sb, num_maps=2))
+    for i, sc in enumerate(scans):
+        m.select(i)
+        m.insert_scan(sc["points"], sc["labels"], sc["pose"])
+    for i in range(2):
+        m.select(i)
+        keys, alpha, _ = m.export()
+        dk, da = m.export_blocks(device=torch.device("cuda", 0))
+        hk, ha = m.export_blocks()
+        assert dk.is_cuda and da.is_cuda
+        np.testing.assert_array_equal(dk.cpu().numpy(), hk)
+        np.testing.assert_array_equal(da.cpu().numpy(), ha)
+        order = np.lexsort((hk[:, 2], hk[:, 1], hk[:, 0]))
+        np.testing.assert_array_equal(hk[order], keys)
+        np.testing.assert_array_equal(ha[order], alpha)
+    m.close()

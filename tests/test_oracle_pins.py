@@ -732,3 +732,22 @@ def test_exact_mean_against_rational_arithmetic(orc):
     for v in cases:
         exact = sum(Fraction(float(x)) for x in v) / len(v)
         assert orc.exact_mean_f32(v) == _f32_round_fraction(exact), v[:4]
+
+
+def test_slab_split_of_the_oracle_gradient_is_exact(orc):
+    """The full-size GPU test runs the oracle's held-out gradient per slab of
+    held-out points in parallel and adds the slabs' terms; on a small case
+    that sum equals one call over everything (FP64 summation order only)."""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    from test_gpu_fullsize import _oracle_grad_parallel, _world
+    prm = dict(scenes.DIFF_PARAMS)
+    sc = next(iter(scenes.small_region_lidar_sequence(1, n_beams=16, n_az=256)))
+    x, lab, _ = orc.training_set(orc.params(**prm), sc["points"], sc["labels"], sc["pose"])
+    held = _world(sc["held_points"], sc["pose"])
+    hl = sc["held_labels"].astype(np.int32)
+    ll, gl, gs, gx = orc.heldout_grad(orc.params(**prm), x.astype(np.float64), lab, held, hl)
+    pll, pgl, pgs, pgx = _oracle_grad_parallel(prm, x, lab.astype(np.int32), held, hl, slabs=5)
+    assert pll == pytest.approx(ll, rel=1e-12)
+    assert pgl == pytest.approx(gl, rel=1e-10) and pgs == pytest.approx(gs, rel=1e-10)
+    assert np.abs(pgx - gx).max() <= 1e-10 * np.abs(gx).max()
