@@ -37,7 +37,7 @@ METRIC = "LiDAR scans/sec (64x2048 street sequence, S-BKI per-scan update)"
 PAIR_CLK_PER_SM = max(14.0 / 128.0, 3.0 / 16.0)
 # sources of the accumulation kernel (a committed DRAM-traffic figure is valid only for these bytes)
 KERNEL_SOURCES = ["paper_1909_04631_gb300/csrc/accumulate_points.cu", "paper_1909_04631_gb300/csrc/kernel_value.cuh",
-                  "paper_1909_04631_gb300/csrc/kernel_poly.cuh", "paper_1909_04631_gb300/csrc/sbki_internal.cuh"]
+                  "paper_1909_04631_gb300/csrc/kernel_poly.cuh", "paper_1909_04631_gb300/csrc/point_common.cuh"]
 
 
 def _gen(args):
@@ -641,7 +641,7 @@ def run_ours(args, rank, world, local_rank):
     t_hbm = bytes_alg / (bw * 1e9)
     t_alu = pairs_per * PAIR_CLK_PER_SM / (n_sm * sm_mhz_max * 1e6)
     traffic = profiled_traffic()
-    common = {"kernel": "accumulate_points_kernel (+ fresh_fill_kernel)", "seconds_per_launch": acc_s,
+    common = {"kernel": "accumulate_points_fast_kernel (+ fresh_fill_kernel)", "seconds_per_launch": acc_s,
               "bytes_alg_per_launch": bytes_alg, "pairs_per_launch": pairs_per, "touched_voxels_per_launch": vt / args.steps,
               "t_hbm_s": t_hbm, "t_alu_s": t_alu, "traffic": traffic}
     if t_alu > t_hbm:
