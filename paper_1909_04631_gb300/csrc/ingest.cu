@@ -621,6 +621,44 @@ constexpr size_t kSegStageKeys = (size_t)seg_pad(kSegTile) * 16;
 constexpr size_t kSegSmemBytes = kSegCellBytes + (size_t)kSegTile * sizeof(uint32_t);
 static_assert(kSegStageKeys + (size_t)seg_pad(kSegTile + 2) * 8 <= kSegCellBytes, "load stage fits the cell stage");
 
+// The tile's cells in shared memory, one array per field (consecutive cells in
+// consecutive words, so a warp reading the cells q, q + 1, ... meets no bank conflict).
+struct SegCells {
+  unsigned long long* T[3];
+  uint32_t* n;
+  uint32_t* flags;
+  __device__ __forceinline__ explicit SegCells(unsigned char* base) {
+    T[0] = reinterpret_cast<unsigned long long*>(base);
+    T[1] = T[0] + kSegTile;
+    T[2] = T[1] + kSegTile;
+    n = reinterpret_cast<uint32_t*>(T[2] + kSegTile);
+    flags = n + kSegTile;
+  }
+  __device__ __forceinline__ void store(uint32_t j, const SegState& s) const {
+    T[0][j] = s.T[0];
+    T[1][j] = s.T[1];
+    T[2][j] = s.T[2];
+    n[j] = s.n;
+    flags[j] = s.flags;
+  }
+  __device__ __forceinline__ SegState load(uint32_t j) const {
+    SegState s;
+    s.T[0] = T[0][j];
+    s.T[1] = T[1][j];
+    s.T[2] = T[2][j];
+    s.n = n[j];
+    s.flags = flags[j];
+    return s;
+  }
+  __device__ __forceinline__ void add(uint32_t j, const SegState& s) const {  // shared-memory atomics
+    atomicAdd(&T[0][j], s.T[0]);
+    atomicAdd(&T[1][j], s.T[1]);
+    atomicAdd(&T[2][j], s.T[2]);
+    atomicAdd(&n[j], s.n);
+    atomicOr(&flags[j], s.flags);
+  }
+};
+
 struct SegCarry {   // partial sums of a cell that crosses a tile boundary
   SegState st;
   uint32_t s;       // part in the head's tile: the cell's index
@@ -813,7 +851,7 @@ __global__ void __launch_bounds__(kSegThreads, 3) seg_reduce_kernel(
     Geom g, float4* __restrict__ train, const ScanDesc* __restrict__ desc, KeyFrame kf, uint32_t* __restrict__ slow,
     DevCounters* dc) {
   extern __shared__ __align__(16) unsigned char seg_smem[];
-  SegState* s_cell = reinterpret_cast<SegState*>(seg_smem);                   // by tile-local cell index
+  const SegCells s_cell(seg_smem);                                             // by tile-local cell index
   uint32_t* s_head = reinterpret_cast<uint32_t*>(seg_smem + kSegCellBytes);  // the cell's label word
   float4* s_items = reinterpret_cast<float4*>(seg_smem + kSegStageItems);     // load stage (aliases s_cell)
   unsigned long long* s_keys = reinterpret_cast<unsigned long long*>(seg_smem + kSegStageKeys);
@@ -944,29 +982,32 @@ __global__ void __launch_bounds__(kSegThreads, 3) seg_reduce_kernel(
           ++j;
         }
         seg_add(R, unit, px[k], py[k], pz[k]);
-        if (hashead && ((ends & (1u << k)) || k == last_k)) s_cell[j] = R;
+        if (hashead && ((ends & (1u << k)) || k == last_k)) s_cell.store(j, R);
       }
     }
     if (!hashead) P = R;
     __syncthreads();
     if (has_items && !(heads & 1u)) {  // the end of a cell begun before this thread
-      SegState* dst = hthread > 0u ? s_cell + (hthread - 1u) : &s_open;
-      atomicAdd(&dst->T[0], P.T[0]);
-      atomicAdd(&dst->T[1], P.T[1]);
-      atomicAdd(&dst->T[2], P.T[2]);
-      atomicAdd(&dst->n, P.n);
-      atomicOr(&dst->flags, P.flags);
+      if (hthread > 0u) {
+        s_cell.add(hthread - 1u, P);
+      } else {
+        atomicAdd(&s_open.T[0], P.T[0]);
+        atomicAdd(&s_open.T[1], P.T[1]);
+        atomicAdd(&s_open.T[2], P.T[2]);
+        atomicAdd(&s_open.n, P.n);
+        atomicOr(&s_open.flags, P.flags);
+      }
     }
     __syncthreads();
     // round every cell whose head lies in the tile, but a last one that goes on
     const bool cross_out = s_cross && total > 0u;
     const uint32_t nround = total - (cross_out ? 1u : 0u);
     for (uint32_t q = threadIdx.x; q < nround; q += kSegThreads)
-      if (!try_round_cell(s_cell[q], excl + q, s_head[q], train))
+      if (!try_round_cell(s_cell.load(q), excl + q, s_head[q], train))
         slow[atomicAdd(&dc->n_slow, 1u)] = excl + q;
     if (threadIdx.x == 0) {
       if (cross_out) {
-        st_carry(closing_run + t, s_cell[total - 1u], excl + total - 1u, 0u);
+        st_carry(closing_run + t, s_cell.load(total - 1u), excl + total - 1u, 0u);
         closing[t] = 1u;
       }
       if (s_open.n) st_carry(opening_run + t, s_open, 0u, (total > 0u || !s_cross) ? 1u : 0u);
