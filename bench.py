@@ -625,20 +625,23 @@ def run_ours(args, rank, world, local_rank):
         m.insert_scan(dpts[j], dlab[j], poses[j])
     m.profile(True, reset=True)
     launches0 = m.profile_read()["launches"]
-    stats = []
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    # scans streamed through the asynchronous entry point: each update still reads its
+    # counters back once (to size the sort), but the host issues the next scan without
+    # waiting for the end of the previous one; errors surface at the sync below
     with ClockSampler(local_rank, args.clock_log) as clk:
         ev0.record(stream)
         for i in range(args.steps):
             j = (args.warmup + i) % nscan
-            stats.append(m.insert_scan(dpts[j], dlab[j], poses[j]))
+            m.insert_scan(dpts[j], dlab[j], poses[j], sync=False)
         ev1.record(stream)
         torch.cuda.synchronize()
+    m.sync()
     ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
     prof = m.profile_read()
     launches = prof["launches"] - launches0
@@ -661,14 +664,25 @@ def run_ours(args, rank, world, local_rank):
     h2d = 0
     for i in range(args.steps):
         j = (args.warmup + i) % nscan
-        m.insert_scan(hp[j].numpy(), hl[j].numpy(), poses[j])
+        m.insert_scan(hp[j].numpy(), hl[j].numpy(), poses[j], sync=False)
         h2d += hp[j].numel() * 4 + hl[j].numel() * 4
+    last = m.sync()  # the stats of the last update (device to host)
     torch.cuda.synchronize()
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
+    d2h = prof["readback_bytes"] + 80 // args.steps  # the counters once per update; the final stats once
     m.close()
 
     if rank != 0:
         return 0
+    # per-scan counts (untimed): the same scans in the same order into a fresh map, one synchronous update each
+    stats = []
+    with sb.Map(p, stream=stream) as sm:
+        for i in range(args.warmup + args.steps):
+            j = i % nscan
+            s = sm.insert_scan(dpts[j], dlab[j], poses[j])
+            if i >= args.warmup:
+                stats.append(s)
+    assert stats[-1]["pairs"] == last["pairs"] and stats[-1]["train_points"] == last["train_points"]
     # voxels touched per scan (untimed): the block-major form counts them; the
     # same scans in the same order into a fresh map give the same touched sets
     acc = sb.Map(p, stream=stream, accumulate_mode=1)
@@ -736,7 +750,8 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk.summary(),
         "gpu_launches": launches,
         "e2e": {"value": args.steps * world / e2e_s, "unit": "scans/s",
-                "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": 80},
+                "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h,
+                "api": "Map.insert_scan(host arrays, sync=False) per scan (sbki_insert_scan_async), Map.sync() at the end"},
         "cpu_baseline": cpu,
     }
     if forms_input is not None:

@@ -280,16 +280,21 @@ sbki_status sbki_export(const sbki_map* map, int64_t* keys, float* alpha, int32_
                         int64_t* count);
 
 /* Per-stage device timing and launch counting (tracing aid).  With profiling
- * on, each synchronous insert records CUDA events on the map's stream around
- * step a1-a3 (sampling + downsampling), a4 (block hash) and a5 (accumulation)
- * and adds the elapsed times; launches counts every kernel the library
- * launched on the map since creation (profiling on or off). */
+ * on, each insert records CUDA events on the map's stream around step a1-a3
+ * (sampling + downsampling), a4 (block hash) and a5 (accumulation) and adds
+ * the elapsed times: a synchronous insert at its end, an asynchronous one
+ * (sbki_insert_scan_async) at the next synchronising call on the map (two
+ * sets of events, so back-to-back asynchronous inserts are all timed);
+ * launches counts every kernel the library launched on the map since
+ * creation (profiling on or off).  A reset drops an asynchronous insert not
+ * yet read. */
 typedef struct sbki_profile_data {
-  int64_t inserts;     /* synchronous inserts timed since the last reset */
+  int64_t inserts;     /* inserts timed since the last reset */
   int64_t launches;    /* kernels launched by this map since creation */
   double ingest_ms;    /* a1-a3 */
   double blocks_ms;    /* a4 */
   double accumulate_ms;/* a5 */
+  int64_t readback_bytes; /* device-to-host bytes of one scan update: the counter block, read once */
 } sbki_profile_data;
 sbki_status sbki_profile(sbki_map* map, int32_t enable, int32_t reset);
 sbki_status sbki_profile_read(const sbki_map* map, sbki_profile_data* out);

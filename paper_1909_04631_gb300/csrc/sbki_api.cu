@@ -365,9 +365,17 @@ sbki_status ensure_soft_capacity(MapState& m, int64_t n) {
   return SBKI_OK;
 }
 
+void profile_collect(MapState& m, const cudaEvent_t* ev);
+
+// Copies the device counters to the host and waits for the stream; the stage
+// times of an asynchronous update issued before are complete then, and are added.
 sbki_status read_counters(MapState& m) {
   CK(&m, cudaMemcpyAsync(m.hc, m.dc, sizeof(DevCounters), cudaMemcpyDeviceToHost, m.stream));
   CK(&m, cudaStreamSynchronize(m.stream));
+  if (m.prof_pending) {
+    m.prof_pending = false;
+    profile_collect(m, m.ev_alt);
+  }
   return SBKI_OK;
 }
 
@@ -492,13 +500,13 @@ sbki_status run_update(MapState& m, const KeyFrame& kf, int64_t bound) {
   return SBKI_OK;
 }
 
-// after a synchronising read: add the stage times of the update just finished
-void profile_collect(MapState& m) {
+// after a synchronising read: add the stage times of a finished update (its events ev[0..3])
+void profile_collect(MapState& m, const cudaEvent_t* ev) {
   if (!m.profiling) return;
   float t01 = 0.f, t12 = 0.f, t23 = 0.f;
-  if (cudaEventElapsedTime(&t01, m.ev[0], m.ev[1]) != cudaSuccess ||
-      cudaEventElapsedTime(&t12, m.ev[1], m.ev[2]) != cudaSuccess ||
-      cudaEventElapsedTime(&t23, m.ev[2], m.ev[3]) != cudaSuccess) {
+  if (cudaEventElapsedTime(&t01, ev[0], ev[1]) != cudaSuccess ||
+      cudaEventElapsedTime(&t12, ev[1], ev[2]) != cudaSuccess ||
+      cudaEventElapsedTime(&t23, ev[2], ev[3]) != cudaSuccess) {
     cudaGetLastError();
     return;
   }
@@ -537,10 +545,17 @@ sbki_status insert_scan_impl(sbki_map* map, const float* points, const int32_t* 
     m.soft = false;
     if (st != SBKI_OK) return st;
   }
-  if (!sync_end) return SBKI_OK;
+  if (!sync_end) {
+    // the stage times are read at the next synchronising call, from the other set of events
+    if (nitems > 0 && m.profiling) {
+      std::swap(m.ev, m.ev_alt);
+      m.prof_pending = true;
+    }
+    return SBKI_OK;
+  }
   st = read_counters(m);
   if (st != SBKI_OK) return st;
-  if (nitems > 0 && m.hc->err == 0) profile_collect(m);
+  if (nitems > 0 && m.hc->err == 0) profile_collect(m, m.ev);
   m.host_blocks = m.hc->n_blocks;
   fill_stats(m, n, &m.last_stats);
   if (stats) *stats = m.last_stats;
@@ -671,7 +686,8 @@ sbki_status sbki_create_map(const sbki_params* params, sbki_map** out) {
     return bail("count init", ce);
   if ((ce = cudaMemsetAsync(m.dc, 0, sizeof(DevCounters), m.stream)) != cudaSuccess) return bail("counters init", ce);
   for (int i = 0; i < 4; ++i)
-    if ((ce = cudaEventCreate(&m.ev[i])) != cudaSuccess) return bail("events", ce);
+    if ((ce = cudaEventCreate(&m.ev[i])) != cudaSuccess || (ce = cudaEventCreate(&m.ev_alt[i])) != cudaSuccess)
+      return bail("events", ce);
   if ((ce = build_candidate_tables(m)) != cudaSuccess) return bail("candidate tables", ce);
   if (m.ftab) {
     if ((ce = dalloc(&m.nbrslot, (size_t)m.hash_cap * 32)) != cudaSuccess) return bail("neighbour slot table", ce);
@@ -702,8 +718,10 @@ void sbki_destroy_map(sbki_map* map) {
     for (int i = 0; i <= kMaxScans; ++i)
       if (m.batch_exec[i]) cudaGraphExecDestroy(m.batch_exec[i]);
     if (m.rec_stream) cudaStreamDestroy(m.rec_stream);
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 4; ++i) {
       if (m.ev[i]) cudaEventDestroy(m.ev[i]);
+      if (m.ev_alt[i]) cudaEventDestroy(m.ev_alt[i]);
+    }
   }
   delete map;
 }
@@ -916,7 +934,7 @@ sbki_status sbki_insert_batch(sbki_map* map, const sbki_scan* scans, int32_t cou
   }
   st = read_counters(m);
   if (st != SBKI_OK) return st;
-  if (m.hc->err == 0) profile_collect(m);
+  if (m.hc->err == 0) profile_collect(m, m.ev);
   m.host_blocks = m.hc->n_blocks;
   fill_stats(m, total, &m.last_stats);
   if (stats) *stats = m.last_stats;
@@ -1027,7 +1045,7 @@ sbki_status sbki_insert_training(sbki_map* map, const float* xyzl, int64_t p, sb
   if (st != SBKI_OK) return st;
   st = read_counters(m);
   if (st != SBKI_OK) return st;
-  if (m.hc->err == 0) profile_collect(m);
+  if (m.hc->err == 0) profile_collect(m, m.ev);
   m.host_blocks = m.hc->n_blocks;
   fill_stats(m, 0, &m.last_stats);
   m.last_stats.hits = 0;
@@ -1230,6 +1248,7 @@ sbki_status sbki_profile(sbki_map* map, int32_t enable, int32_t reset) {
     const int64_t l = map->st.prof.launches;
     map->st.prof = sbki_profile_data{};
     map->st.prof.launches = l;
+    map->st.prof_pending = false;  // an asynchronous update issued before the reset is not counted
   }
   return SBKI_OK;
 }
@@ -1238,6 +1257,7 @@ sbki_status sbki_profile_read(const sbki_map* map, sbki_profile_data* out) {
   if (!map || !out) return fail(nullptr, SBKI_ERR_INVALID_ARG, "bad arguments");
   *out = map->st.prof;
   out->launches = map->st.launches;
+  out->readback_bytes = (int64_t)sizeof(DevCounters);
   return SBKI_OK;
 }
 

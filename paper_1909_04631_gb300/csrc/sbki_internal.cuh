@@ -202,7 +202,9 @@ struct MapState {
                                         // u64), then sum G f per class
   int ctab_pad = 0, ctab_R = 0;
   bool profiling = false;
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};      // stage events of the update being issued
+  cudaEvent_t ev_alt[4] = {nullptr, nullptr, nullptr, nullptr};  // those of an asynchronous update not yet read
+  bool prof_pending = false;                                     // ev_alt holds such an update
   sbki_profile_data prof{};
   char last_error[512] = {0};
   sbki_stats last_stats{};

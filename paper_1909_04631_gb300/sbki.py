@@ -61,7 +61,7 @@ class Tuning(C.Structure):
 
 class ProfileData(C.Structure):
     _fields_ = [("inserts", C.c_int64), ("launches", C.c_int64), ("ingest_ms", C.c_double),
-                ("blocks_ms", C.c_double), ("accumulate_ms", C.c_double)]
+                ("blocks_ms", C.c_double), ("accumulate_ms", C.c_double), ("readback_bytes", C.c_int64)]
 
     def as_dict(self):
         return {n: (float(getattr(self, n)) if n.endswith("_ms") else int(getattr(self, n))) for n, _ in self._fields_}
