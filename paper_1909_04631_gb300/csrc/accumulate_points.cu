@@ -28,6 +28,7 @@
 // flight at any moment update a compact region of the map (L2 locality).
 // Blocks allocated by this update are zero-filled before (fresh_fill_kernel).
 #include <algorithm>
+#include <type_traits>
 #include <climits>
 #include <cmath>
 #include <vector>
@@ -65,6 +66,9 @@ struct PtArgs {
   int ftpad;             // entries per fast list (multiple of 32, at most 32 kFastEntries)
   const uint32_t* ownslot;  // fast form: per training point the hash slot of its own block (touched-block pass)
   const uint32_t* nbrslot;  // fast form: [hash_cap][32] per own block the hash slots of its touched neighbours
+  const int32_t* softidx;   // soft labels (fast form), or null: per training point its weight row, or -1
+  const float* wsoft;       // weight rows [.][K+1]
+  int tab_of[kMaxClasses];  // per-class supports (fast form): each class's list table, or -1 (not this form)
   DevCounters* dc;
 };
 
@@ -215,8 +219,11 @@ struct __align__(256) FastWarp {
   uint32_t btab[64];                    // alpha element base per block digit (27 used)
   uint32_t ptab[64];                    // pair-count element base per block digit (kTrack)
 };
+struct __align__(256) FastWarpSoft : FastWarp {
+  float cw[kGroup][kMaxClasses];        // soft labels: per point sigma0 s_k w^k by class
+};
 // scalars of a slot (int index into its last 64 bytes)
-constexpr int kScPart = 0, kScLabel = 1, kScS0 = 2, kScPool = 3, kScV0 = 8;
+constexpr int kScPart = 0, kScLabel = 1, kScS0 = 2, kScPool = 3, kScMask = 4, kScSoft = 5, kScV0 = 8;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ float2 lds_f2(uint32_t a) {
@@ -254,12 +261,20 @@ __device__ __forceinline__ bool band_decide(uint32_t e, const int* sc, const flo
                            l2_64);
 }
 
-template <bool kTrack, bool kFace>
+// Soft labels (kSoft, reading K15): a point with a weight row forms its rows
+// for class 0 (no class row in the X parts) with s0 = 1, and each of its
+// in-support pairs adds f(d/l) sigma0 s_k w^k into every class k with a
+// nonzero weight; a point without one (free samples) is a hard class-0 point.
+// Per-class supports (kLk, reading K16): a point's list comes from the table
+// of its class's support l_k, its membership test and kernel use l_k; points
+// of a class without a table are left to the weighted form.
+template <bool kTrack, bool kFace, bool kSoft = false, bool kLk = false>
 __global__ void __launch_bounds__(kThreads, 4) accumulate_points_fast_kernel(PtArgs a) {
-  __shared__ FastWarp s_w[kWarps];
+  using Warp = typename std::conditional<kSoft, FastWarpSoft, FastWarp>::type;
+  __shared__ Warp s_w[kWarps];
   const Geom& g = a.g;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  FastWarp& W = s_w[wid];
+  Warp& W = s_w[wid];
   const int R = a.R, na = 2 * R + 1, m = g.B - 1;
   if (a.dc->err != 0) return;
   if ((smem_addr(&W) & 255u) != 0u) {  // the byte permutes need 256-byte aligned slots
@@ -289,9 +304,10 @@ __global__ void __launch_bounds__(kThreads, 4) accumulate_points_fast_kernel(PtA
       const uint32_t gn = min(c1 - g0, (uint32_t)kGroup);  // warp-uniform
       // 1. rows of every point of the group, three lanes per point; the lane
       //    of axis x also reads the hash slot of the point's own block
-      int pt = 0, lw = 0;
+      int pt = 0, lw = 0, srow = -1;
       if (gl < (int)gn) {
         const float4 p = a.train[g0 + gl];
+        if (kSoft) srow = __ldg(a.softidx + g0 + gl);
         const float xa = ax == 0 ? p.x : (ax == 1 ? p.y : p.z);
         const int v0 = floor_small(__fmul_rn(xa, g.inv_res));
         float hi, lo;
@@ -300,6 +316,7 @@ __global__ void __launch_bounds__(kThreads, 4) accumulate_points_fast_kernel(PtA
         pt = min(kFastParts - 1, max(0, floor_small(phi * (float)kFastParts)));
         const int b0 = v0 >> g.B_shift;
         lw = label_of(p.w);
+        if (kSoft && srow >= 0) lw &= ~((1 << kLabelBits) - 1);  // class rows come per class in the sweep
         const uint32_t cls = ax == 0 ? (uint32_t)((lw & ((1 << kLabelBits) - 1)) * g.B3) : 0u;
         float2* r = W.rows[gl] + kFastAxis * ax;
         // offsets in a lane-dependent order, so the lanes of one store spread over the banks
@@ -319,15 +336,36 @@ __global__ void __launch_bounds__(kThreads, 4) accumulate_points_fast_kernel(PtA
       }
       const int pty = __shfl_sync(0xffffffffu, pt, min(lane + 1, 31));
       const int ptz = __shfl_sync(0xffffffffu, pt, min(lane + 2, 31));
+      int list = pt + kFastParts * (pty + kFastParts * ptz);
+      if constexpr (kLk) {  // the table of the point's class support, or -1
+        const int tb = a.tab_of[lw & ((1 << kLabelBits) - 1)];
+        list = tb >= 0 ? list + tb * kFastParts * kFastParts * kFastParts : -1;
+      }
       if (ax == 0 && gl < (int)gn)
         *reinterpret_cast<int4*>(reinterpret_cast<int*>(W.rows[gl] + 3 * kFastAxis) + kScPart) =
-            make_int4(pt + kFastParts * (pty + kFastParts * ptz), lw,
-                      __float_as_int(g.sigma0_k[lw & ((1 << kLabelBits) - 1)]), (int)__ldg(a.ownslot + g0 + gl));
+            make_int4(list, lw,
+                      __float_as_int((kSoft && srow >= 0) ? 1.0f : g.sigma0_k[lw & ((1 << kLabelBits) - 1)]),
+                      (int)__ldg(a.ownslot + g0 + gl));
+      if constexpr (kSoft) {  // class factors sigma0 s_k w^k of the group's soft points
+        for (uint32_t k = 0; k < gn; ++k) {
+          const int row = __shfl_sync(0xffffffffu, srow, 3 * k);
+          float ck = 0.0f;
+          if (row >= 0 && lane < g.K1) ck = g.sigma0_k[lane] * __ldg(a.wsoft + (size_t)row * g.K1 + lane);
+          const unsigned cm = __ballot_sync(0xffffffffu, ck != 0.0f);
+          if (lane < g.K1) W.cw[k][lane] = ck;
+          if (lane == 0) {
+            int* sc = reinterpret_cast<int*>(W.rows[k] + 3 * kFastAxis);
+            sc[kScMask] = (int)cm;
+            sc[kScSoft] = row >= 0 ? 1 : 0;
+          }
+        }
+      }
       __syncwarp();
       // 2. point by point: block tables (when the own block changes), candidate sweeps
       uint32_t ent[kFastEntries];
       {
-        const int part = reinterpret_cast<const int*>(W.rows[0] + 3 * kFastAxis)[kScPart];
+        int part = reinterpret_cast<const int*>(W.rows[0] + 3 * kFastAxis)[kScPart];
+        if constexpr (kLk) part = max(0, part);  // a skipped point (-1) loads list 0, unused
         const uint32_t* tab = a.ftab + (size_t)part * a.ftpad;
 #pragma unroll
         for (int it = 0; it < kFastEntries; ++it) ent[it] = __ldg(tab + it * 32 + lane);
@@ -335,67 +373,92 @@ __global__ void __launch_bounds__(kThreads, 4) accumulate_points_fast_kernel(PtA
       for (uint32_t k = 0; k < gn; ++k) {
         const int* sc = reinterpret_cast<const int*>(W.rows[k] + 3 * kFastAxis);
         const int4 sv = *reinterpret_cast<const int4*>(sc + kScPart);  // part, label word, s0, own pool slot
+        const bool soft_pt = kSoft && sc[kScSoft] != 0;
+        const unsigned cmask = kSoft ? (unsigned)sc[kScMask] : 0u;
         // the next point's list, in flight while this one is swept (lists are
         // padded to kFastEntries x 32 entries, so every load is in range)
         uint32_t nent[kFastEntries];
         {
-          const int part = k + 1 < gn ? sc[kScPart + kSlotBytes / 4] : sv.x;
+          int part = k + 1 < gn ? sc[kScPart + kSlotBytes / 4] : sv.x;
+          if constexpr (kLk) part = max(0, part);
           const uint32_t* tab = a.ftab + (size_t)part * a.ftpad;
 #pragma unroll
           for (int it = 0; it < kFastEntries; ++it) nent[it] = __ldg(tab + it * 32 + lane);
         }
-        if (sv.w != cpool) {  // warp-uniform: the tables belong to another block
-          cpool = sv.w;
-          __syncwarp();  // every lane is done with the old tables
-          if (lane < 27) {
-            // a digit no point of this block touched holds a stale slot; no
-            // in-support pair uses it (every reduction is predicated on membership)
-            const uint32_t hs = a.nbrslot[(size_t)sv.w * 32 + lane] & (uint32_t)(a.hash_cap - 1);
-            const int32_t pool = a.hvals[hs];
-            const uint32_t pb = (uint32_t)(pool >= 0 ? pool : a.sink);
-            W.btab[lane] = pb * K1B3 - ((4u * (uint32_t)lane) << 24);
-            if (kTrack) W.ptab[lane] = pb * (uint32_t)g.B3 - ((4u * (uint32_t)lane) << 24);
+        if (!(kLk && sv.x < 0)) {  // warp-uniform: a point of a class without a table is the weighted form's
+          if (sv.w != cpool) {  // warp-uniform: the tables belong to another block
+            cpool = sv.w;
+            __syncwarp();  // every lane is done with the old tables
+            if (lane < 27) {
+              // a digit no point of this block touched holds a stale slot; no
+              // in-support pair uses it (every reduction is predicated on membership)
+              const uint32_t hs = a.nbrslot[(size_t)sv.w * 32 + lane] & (uint32_t)(a.hash_cap - 1);
+              const int32_t pool = a.hvals[hs];
+              const uint32_t pb = (uint32_t)(pool >= 0 ? pool : a.sink);
+              W.btab[lane] = pb * K1B3 - ((4u * (uint32_t)lane) << 24);
+              if (kTrack) W.ptab[lane] = pb * (uint32_t)g.B3 - ((4u * (uint32_t)lane) << 24);
+            }
+            __syncwarp();
           }
-          __syncwarp();
-        }
-        const uint32_t slot = rows0 + (uint32_t)k * kSlotBytes;
-        const float s0 = __int_as_float(sv.z);
-        const float2 s02 = make_float2(s0, s0);
-        const uint32_t cls = (uint32_t)((sv.y & ((1 << kLabelBits) - 1)) * g.B3);
-        const int len = __ldg(a.flen + sv.x);
+          const uint32_t slot = rows0 + (uint32_t)k * kSlotBytes;
+          const float s0 = __int_as_float(sv.z);
+          const float2 s02 = make_float2(s0, s0);
+          const uint32_t cls = (uint32_t)((sv.y & ((1 << kLabelBits) - 1)) * g.B3);
+          const int len = __ldg(a.flen + sv.x);
+          // the support of the point's class (common l: the kernel's constants)
+          const int cl = sv.y & ((1 << kLabelBits) - 1);
+          const float l2lo = kLk ? g.l2k_lo[cl] : g.l2_lo, l2hi = kLk ? g.l2k_hi[cl] : g.l2_hi;
+          const double l264 = kLk ? g.l2k_64[cl] : g.l2_64;
+          const float2 ninv = kLk ? make_float2(-g.inv_lk[cl], -g.inv_lk[cl]) : neg_inv_l;
 #pragma unroll
-        for (int jp = 0; jp < (kFastEntries + 1) / 2; ++jp) {
-          if (jp < 2 || jp * 64 < len) {  // warp-uniform; lists hold more than 64 entries
-            const uint32_t ea = ent[2 * jp], eb = 2 * jp + 1 < kFastEntries ? ent[2 * jp + 1] : kPadEntry;
-            float d2a, d2b;
-            uint32_t pka, pkb;
-            candidate_rows2(ea, slot, d2a, pka);
-            candidate_rows2(eb, slot, d2b, pkb);
-            bool ina = d2a < g.l2_lo, inb = d2b < g.l2_lo;
-            const bool bnda = !ina && d2a < g.l2_hi, bndb = !inb && d2b < g.l2_hi;
-            if (__any_sync(0xffffffffu, bnda || bndb)) {
-              if (bnda) ina = band_decide(ea, sc, a.train, g0 + k, R, g.res64, g.l2_64);
-              if (bndb) inb = band_decide(eb, sc, a.train, g0 + k, R, g.res64, g.l2_64);
+          for (int jp = 0; jp < (kFastEntries + 1) / 2; ++jp) {
+            if (jp < 2 || jp * 64 < len) {  // warp-uniform; lists hold more than 64 entries
+              const uint32_t ea = ent[2 * jp], eb = 2 * jp + 1 < kFastEntries ? ent[2 * jp + 1] : kPadEntry;
+              float d2a, d2b;
+              uint32_t pka, pkb;
+              candidate_rows2(ea, slot, d2a, pka);
+              candidate_rows2(eb, slot, d2b, pkb);
+              bool ina = d2a < l2lo, inb = d2b < l2lo;
+              const bool bnda = !ina && d2a < l2hi, bndb = !inb && d2b < l2hi;
+              if (__any_sync(0xffffffffu, bnda || bndb)) {
+                if (bnda) ina = band_decide(ea, sc, a.train, g0 + k, R, g.res64, l264);
+                if (bndb) inb = band_decide(eb, sc, a.train, g0 + k, R, g.res64, l264);
+              }
+              if (kFace) {  // extended block: own block and face neighbours (digit in the top byte, times 4)
+                ina = ina && ((kFaceDigits >> (pka >> 26)) & 1u);
+                inb = inb && ((kFaceDigits >> (pkb >> 26)) & 1u);
+              }
+              // kernel of both candidates: f = u^5 Q(u^2), u = 1 - d / l, times sigma0 s_k
+              const float2 d = make_float2(sqrt_approx(d2a), sqrt_approx(d2b));
+              const float2 u = __ffma2_rn(d, ninv, one2);
+              const float2 w = __fmul2_rn(u, u);
+              const float2 q = kernel_q2(w);
+              const float2 v = __fmul2_rn(__fmul2_rn(__fmul2_rn(__fmul2_rn(w, w), u), q), s02);
+              const uint32_t elema = lds_u32(__byte_perm(pka, btab, 0x7653)) + pka;
+              const uint32_t elemb = lds_u32(__byte_perm(pkb, btab, 0x7653)) + pkb;
+              bool spread = false;
+              if constexpr (kSoft) {
+                if (soft_pt) {  // warp-uniform: every class with a weight
+                  for (unsigned cl = cmask; cl; cl &= cl - 1u) {
+                    const int kc = __ffs((int)cl) - 1;
+                    const float ck = W.cw[k][kc];
+                    const uint32_t off = (uint32_t)kc * (uint32_t)g.B3;
+                    if (ina) atomicAdd(a.alpha + elema + off, v.x * ck);
+                    if (inb) atomicAdd(a.alpha + elemb + off, v.y * ck);
+                  }
+                  spread = true;
+                }
+              }
+              if (!spread) {
+                if (ina) atomicAdd(a.alpha + elema, v.x);  // result unused: a reduction
+                if (inb) atomicAdd(a.alpha + elemb, v.y);
+              }
+              if (kTrack) {
+                red_add_if(ina, a.pairs + (lds_u32(__byte_perm(pka, ptab, 0x7653)) + pka - cls), 1);
+                red_add_if(inb, a.pairs + (lds_u32(__byte_perm(pkb, ptab, 0x7653)) + pkb - cls), 1);
+              }
+              npairs += (ina ? 1u : 0u) + (inb ? 1u : 0u);
             }
-            if (kFace) {  // extended block: own block and face neighbours (digit in the top byte, times 4)
-              ina = ina && ((kFaceDigits >> (pka >> 26)) & 1u);
-              inb = inb && ((kFaceDigits >> (pkb >> 26)) & 1u);
-            }
-            // kernel of both candidates: f = u^5 Q(u^2), u = 1 - d / l, times sigma0 s_k
-            const float2 d = make_float2(sqrt_approx(d2a), sqrt_approx(d2b));
-            const float2 u = __ffma2_rn(d, neg_inv_l, one2);
-            const float2 w = __fmul2_rn(u, u);
-            const float2 q = kernel_q2(w);
-            const float2 v = __fmul2_rn(__fmul2_rn(__fmul2_rn(__fmul2_rn(w, w), u), q), s02);
-            const uint32_t elema = lds_u32(__byte_perm(pka, btab, 0x7653)) + pka;
-            const uint32_t elemb = lds_u32(__byte_perm(pkb, btab, 0x7653)) + pkb;
-            if (ina) atomicAdd(a.alpha + elema, v.x);  // result unused: a reduction
-            if (inb) atomicAdd(a.alpha + elemb, v.y);
-            if (kTrack) {
-              red_add_if(ina, a.pairs + (lds_u32(__byte_perm(pka, ptab, 0x7653)) + pka - cls), 1);
-              red_add_if(inb, a.pairs + (lds_u32(__byte_perm(pkb, ptab, 0x7653)) + pkb - cls), 1);
-            }
-            npairs += (ina ? 1u : 0u) + (inb ? 1u : 0u);
           }
         }
 #pragma unroll
@@ -506,34 +569,86 @@ cudaError_t build_candidate_tables(MapState& m) {
   if (e != cudaSuccess) return e;
   m.ctab_pad = tpad;
   m.ctab_R = Rt;
-  // the fast form needs 2R + 1 <= 7 and l above half the voxel diagonal (a
-  // point's own voxel, hence its own block, is then always touched)
-  if (na > kFastAxis - 1 || lr <= 0.8661) return cudaSuccess;
-  // fast form: entry = X row byte offset 8 jx | (64 + 8 jy) << 8 | (128 + 8 jz) << 16
-  // inside a point's slot; padding entries name the X padding row
-  const int Rf = candidate_lists(lr, kFastParts, lists);
-  const int nf = (int)lists.size();
-  longest = 0;
-  for (auto& L : lists) longest = std::max(longest, L.size());
-  // every list holds exactly 32 kFastEntries entries (padding after the
-  // candidates): the sweep loads all of them unconditionally
+  // The fast form: one table of kFastParts^3 lists per distinct class support
+  // l_k = l l_scale[k] (one table for the common l).  A support qualifies with
+  // 2R + 1 <= 7 offsets per axis and l_k above half the voxel diagonal (a
+  // point's own voxel, hence its own block, is then always touched); every
+  // list is padded to 32 kFastEntries entries (the sweep loads all of them
+  // unconditionally).  Entry = X row byte offset 8 jx | (64 + 8 jy) << 8 |
+  // (128 + 8 jz) << 16 inside a point's slot; padding entries name the X
+  // padding row.
+  const int K1 = m.prm.num_classes + 1;
   const int fpad = 32 * kFastEntries;
-  if ((int)longest > fpad) return cudaSuccess;
-  std::vector<uint32_t> ff((size_t)nf * fpad, kPadEntry);
-  std::vector<int32_t> fl(nf);
-  for (int t = 0; t < nf; ++t) {
-    fl[t] = (int32_t)lists[t].size();
-    for (size_t k = 0; k < lists[t].size(); ++k) {
-      const int32_t e = lists[t][k];
-      const uint32_t jx = (uint32_t)((e & 15) - Rf + Rt), jy = (uint32_t)(((e >> 4) & 15) - Rf + Rt),
-                     jz = (uint32_t)(((e >> 8) & 15) - Rf + Rt);
-      if (jx >= (uint32_t)na || jy >= (uint32_t)na || jz >= (uint32_t)na) return cudaErrorInvalidValue;
-      ff[(size_t)t * fpad + k] = (8u * jx) | ((64u + 8u * jy) << 8) | ((128u + 8u * jz) << 16);
+  std::vector<double> lrs;                              // distinct supports (voxel units)
+  std::vector<std::vector<std::vector<int32_t>>> tabs;  // their lists
+  std::vector<int> rfs;                                 // candidate_lists' R of each
+  int rmax = 0;
+  bool own_touched = true;
+  m.ftab_classes = 0;
+  for (int k = 0; k < 32; ++k) m.ftab_of[k] = -1;
+  for (int k = 0; k < K1; ++k) {
+    const double lrk = m.prm.length_scale * m.prm.l_scale[k] / m.prm.res;
+    own_touched = own_touched && lrk > 0.8661;
+    size_t t = 0;
+    while (t < lrs.size() && lrs[t] != lrk) ++t;
+    if (t == lrs.size()) {  // a new support: its lists, if it qualifies
+      std::vector<std::vector<int32_t>> fl;
+      const int Rf = candidate_lists(lrk, kFastParts, fl);
+      size_t lng = 0;
+      int md = 0;
+      for (auto& L : fl) {
+        lng = std::max(lng, L.size());
+        for (int32_t e : L)
+          for (int a2 = 0; a2 < 3; ++a2) md = std::max(md, std::abs(((e >> (4 * a2)) & 15) - Rf));
+      }
+      if (2 * md + 1 > kFastAxis - 1 || lrk <= 0.8661 || (int)lng > fpad) {
+        lrs.push_back(lrk);
+        tabs.emplace_back();  // does not qualify
+        rfs.push_back(-1);
+      } else {
+        lrs.push_back(lrk);
+        tabs.push_back(std::move(fl));
+        rfs.push_back(Rf);
+        rmax = std::max(rmax, md);
+      }
     }
+    if (rfs[t] >= 0) m.ftab_classes |= 1u << k;
+  }
+  if (m.ftab_classes == 0) return cudaSuccess;
+  // tables in order of first use; rows -rmax..rmax for all of them
+  const int nf = kFastParts * kFastParts * kFastParts, naf = 2 * rmax + 1;
+  std::vector<int> index(lrs.size(), -1);
+  int ntab = 0;
+  for (size_t t = 0; t < lrs.size(); ++t)
+    if (rfs[t] >= 0) index[t] = ntab++;
+  std::vector<uint32_t> ff((size_t)ntab * nf * fpad, kPadEntry);
+  std::vector<int32_t> fl((size_t)ntab * nf);
+  for (size_t t = 0; t < lrs.size(); ++t) {
+    if (index[t] < 0) continue;
+    const size_t b = (size_t)index[t] * nf;
+    for (int q = 0; q < nf; ++q) {
+      const auto& L = tabs[t][q];
+      fl[b + q] = (int32_t)L.size();
+      for (size_t k = 0; k < L.size(); ++k) {
+        const int32_t e = L[k];
+        const uint32_t jx = (uint32_t)((e & 15) - rfs[t] + rmax), jy = (uint32_t)(((e >> 4) & 15) - rfs[t] + rmax),
+                       jz = (uint32_t)(((e >> 8) & 15) - rfs[t] + rmax);
+        if (jx >= (uint32_t)naf || jy >= (uint32_t)naf || jz >= (uint32_t)naf) return cudaErrorInvalidValue;
+        ff[(b + q) * fpad + k] = (8u * jx) | ((64u + 8u * jy) << 8) | ((128u + 8u * jz) << 16);
+      }
+    }
+  }
+  for (int k = 0; k < K1; ++k) {
+    size_t t = 0;
+    const double lrk = m.prm.length_scale * m.prm.l_scale[k] / m.prm.res;
+    while (lrs[t] != lrk) ++t;
+    m.ftab_of[k] = index[t];
   }
   e = upload_lists(ff, fl, &m.ftab, &m.flen);
   if (e != cudaSuccess) return e;
   m.ftab_pad = fpad;
+  m.ftab_R = rmax;
+  m.ftab_own_touched = own_touched;
   return cudaSuccess;
 }
 
@@ -552,6 +667,11 @@ cudaError_t launch_persistent(Kernel kern, const PtArgs& a, int sm_count, int ct
 
 template <bool kTrack>
 cudaError_t launch_fast(const PtArgs& a, int sm_count, int ctas_per_sm, cudaStream_t st) {
+  if (a.g.lscaled)  // per-class supports: the exact association and hard labels only
+    return launch_persistent(accumulate_points_fast_kernel<kTrack, false, false, true>, a, sm_count, ctas_per_sm,
+                             st);
+  if (a.softidx)  // soft labels take the exact association only
+    return launch_persistent(accumulate_points_fast_kernel<kTrack, false, true>, a, sm_count, ctas_per_sm, st);
   return a.g.assoc ? launch_persistent(accumulate_points_fast_kernel<kTrack, true>, a, sm_count, ctas_per_sm, st)
                    : launch_persistent(accumulate_points_fast_kernel<kTrack, false>, a, sm_count, ctas_per_sm, st);
 }
@@ -577,6 +697,15 @@ cudaError_t launch_fresh_fill(MapState& m) {
   return cudaGetLastError();
 }
 
+// the fast form needs its tables (with per-class supports, every class's l_k
+// above half the voxel diagonal, so that the touched-block pass may record
+// every point's own block) and addresses alpha and the pair counts with
+// 32-bit element indices
+bool fast_form_ready(const MapState& m) {
+  return m.ftab != nullptr && m.nbrslot != nullptr && (!m.g.lscaled || m.ftab_own_touched) &&
+         (uint64_t)(m.pool_blocks + 1) * (uint64_t)(m.g.K1 * m.g.B3) <= (1ull << 32);
+}
+
 cudaError_t launch_accumulate_points(MapState& m) {
   fresh_fill_kernel<<<m.sm_count * 4, 256, 0, m.stream>>>(m.s.fresh, m.hvals, m.alpha, m.pairs, m.g.K1 * m.g.B3,
                                                           m.g.B3, m.dc);
@@ -600,11 +729,16 @@ cudaError_t launch_accumulate_points(MapState& m) {
   a.ftpad = m.ftab_pad;
   a.ownslot = m.s.ownslot;
   a.nbrslot = m.nbrslot;
+  a.softidx = m.soft ? m.s.softidx : nullptr;
+  a.wsoft = m.soft ? m.s.wsoft : nullptr;
+  for (int k = 0; k < kMaxClasses; ++k) a.tab_of[k] = m.ftab_of[k];
   a.dc = m.dc;
   m.launches += 2;
   const int cps = m.tune.accumulate_ctas_per_sm;
-  // the fast form addresses alpha and the pair counts with 32-bit element indices
-  const bool fast = m.ftab != nullptr && m.nbrslot != nullptr && (uint64_t)(m.pool_blocks + 1) * (uint64_t)(m.g.K1 * m.g.B3) <= (1ull << 32);
+  const bool fast = fast_form_ready(m);
+  // soft labels and per-class supports without the fast form: the caller takes the weighted form instead
+  if ((m.soft || m.g.lscaled) && !fast) return cudaErrorInvalidValue;
+  if (fast) a.R = m.ftab_R;
   if (fast)
     return m.pairs ? launch_fast<true>(a, m.sm_count, cps, m.stream) : launch_fast<false>(a, m.sm_count, cps, m.stream);
   return m.pairs ? launch_general<true>(a, m.sm_count, cps, m.stream)

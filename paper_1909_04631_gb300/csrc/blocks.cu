@@ -510,7 +510,7 @@ cudaError_t launch_touch_cells(MapState& m, int64_t bound) {
 
 cudaError_t launch_touch_blocks(MapState& m, const KeyFrame& /*kf*/, int64_t bound) {
   TouchArgs a = touch_args(m);
-  if (m.acc_mode == 0 && m.nbrslot && !m.g.lscaled && !m.soft) {  // tables of the fast point-major accumulation
+  if (m.acc_mode == 0 && fast_form_ready(m)) {  // tables of the fast point-major accumulation
     a.ownslot = m.s.ownslot;
     a.nbrslot = m.nbrslot;
   }

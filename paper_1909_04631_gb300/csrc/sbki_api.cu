@@ -492,9 +492,17 @@ sbki_status run_update(MapState& m, const KeyFrame& kf, int64_t bound) {
   if (m.profiling) CK(&m, cudaEventRecord(m.ev[2], m.stream));
   {
     NvtxRange range("sbki: accumulation (a5)");
-    if (m.soft || m.g.lscaled) CK(&m, launch_accumulate_weighted(m, m.soft));  // soft labels, per-class l
-    else if (m.acc_mode == 1) CK(&m, launch_accumulate(m, kf));
-    else CK(&m, launch_accumulate_points(m));
+    if (m.g.lscaled && fast_form_ready(m)) {  // per-class l: the fast form for the classes it has tables of
+      CK(&m, launch_accumulate_points(m));
+      const uint32_t all = m.g.K1 >= 32 ? 0xffffffffu : (1u << m.g.K1) - 1u;
+      if ((m.ftab_classes & all) != all) CK(&m, launch_accumulate_weighted(m, false, false, m.ftab_classes));
+    } else if (m.g.lscaled || (m.soft && !fast_form_ready(m))) {  // the weighted form alone
+      CK(&m, launch_accumulate_weighted(m, m.soft));
+    } else if (m.acc_mode == 1) {
+      CK(&m, launch_accumulate(m, kf));
+    } else {
+      CK(&m, launch_accumulate_points(m));
+    }
   }
   if (m.profiling) CK(&m, cudaEventRecord(m.ev[3], m.stream));
   return SBKI_OK;

@@ -192,9 +192,14 @@ struct MapState {
   ScanDesc* hdesc = nullptr;            // pinned host staging of s.desc
   uint32_t* ctab = nullptr;             // point-major candidate lists [kParts^3][ctab_pad]
   int32_t* clen = nullptr;              // [kParts^3] entries of each list
-  uint32_t* ftab = nullptr;             // fast accumulation form's candidate lists (2R + 1 <= 7), or null
+  uint32_t* ftab = nullptr;             // fast accumulation form's candidate lists (2R + 1 <= 7), or null:
+                                        // one table of kFastParts^3 lists per distinct class support
   int32_t* flen = nullptr;              // their entry counts
   int ftab_pad = 0;
+  int ftab_R = 0;                       // offsets -R..R per axis of the fast form's rows
+  int32_t ftab_of[32] = {};             // per class: its table, or -1 (the weighted form takes the class)
+  uint32_t ftab_classes = 0;            // classes with a table
+  bool ftab_own_touched = false;        // every class's l above half the voxel diagonal (own block always touched)
   uint32_t* nbrslot = nullptr;          // fast form: [hash_cap][32] per own block (hash slot), the hash slots of the
                                         // neighbour blocks its points touched in the last update, by block digit
   float* gpool = nullptr;               // dL/dalpha [pool_blocks][K1][B3] (differentiable form, on first use)
@@ -348,6 +353,7 @@ cudaError_t launch_bin_points(MapState& m, int64_t bound);
 // accumulate.cu
 cudaError_t launch_accumulate(MapState& m, const KeyFrame& kf);
 cudaError_t launch_accumulate_points(MapState& m);
+bool fast_form_ready(const MapState& m);  // the fast point-major form can run on this map
 cudaError_t launch_accumulate_counts(MapState& m, int64_t bound);  // counting model, Eq. (alpha)
 cudaError_t launch_fresh_fill(MapState& m);  // zero the blocks created by this update
 cudaError_t build_candidate_tables(MapState& m);
@@ -365,7 +371,7 @@ size_t accumulate_smem_bytes(const Geom& g);
 // and the weighted accumulation (soft labels and/or per-class length scales)
 cudaError_t launch_soft_weights(MapState& m);
 cudaError_t launch_soft_export(MapState& m, float* xyz, float* w, int64_t cap);
-cudaError_t launch_accumulate_weighted(MapState& m, bool soft);
+cudaError_t launch_accumulate_weighted(MapState& m, bool soft, bool fill = true, uint32_t skip = 0u);
 
 // readoff.cu
 cudaError_t launch_query(const MapState& m, const float* xyz, int64_t q, float* probs, float* var, float* mode,

@@ -10,7 +10,9 @@
 // Weighted accumulation (Eq. (alpha_kernel) with the one-hot y_i replaced by a
 // weight vector, and class k's kernel sigma0 s_k f(d/l_k) with support l_k):
 // one warp per training point sweeps the cube of voxel offsets within
-// +-(ceil(l_max/res) + 1) of the point's voxel, decides membership per class
+// +-R of the point's voxel, R the largest of its weighted classes' R_k
+// (offsets j with |j| - 1/2 >= l_k / res hold no voxel centre within l_k of a
+// point in the voxel), decides membership per class
 // exactly as the map update does (compensated FP32 offsets, FP64 inside the
 // relative band around l_k^2) and adds sigma0 s_k f(d/l_k) w^k into every
 // class k with w^k != 0 whose support holds the voxel; a (voxel, point) pair
@@ -79,31 +81,43 @@ __device__ float unit_mean(Get get, uint32_t n) {
   return ldexpf((float)mant, drop - 245);
 }
 
-// One thread per training point (group): its weight row, if it holds a hit.
+// Weight rows of the groups that hold hits: a warp takes 32 consecutive
+// training points (groups); a group's class is its members' most probable
+// class, which is 1..K for a hit and 0 for a free sample, so a group of class
+// k >= 1 holds hits only (class-0 weight 0) and a group of class 0 free
+// samples only (no row).  Each group with hits is then taken by the whole
+// warp, lane k computing the exact mean of class k (one member: its vector).
 __global__ void soft_weights_kernel(const uint32_t* __restrict__ seg_start, const uint32_t* __restrict__ svals,
-                                    const uint32_t* __restrict__ hit_src, const ScanDesc* __restrict__ desc,
-                                    int32_t* __restrict__ softidx, float* __restrict__ wsoft, int K1, DevCounters* dc) {
+                                    const uint32_t* __restrict__ hit_src, const float4* __restrict__ train,
+                                    const ScanDesc* __restrict__ desc, int32_t* __restrict__ softidx,
+                                    float* __restrict__ wsoft, int K1, DevCounters* dc) {
   if (dc->err != 0) return;
-  const uint32_t P = dc->n_train, nvalid = dc->n_valid;
+  const uint32_t P = dc->n_train;
   const float* probs = desc[0].probs;
-  const int K = K1 - 1;
-  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < P; t += gridDim.x * blockDim.x) {
-    const uint32_t a = seg_start[t], b = seg_start[t + 1];
-    bool hit = false;
-    for (uint32_t j = a; j < b && !hit; ++j) hit = svals[j] < nvalid;
-    if (!hit) {
-      softidx[t] = -1;
-      continue;
-    }
-    const uint32_t row = atomicAdd(&dc->n_soft, 1u);
-    softidx[t] = (int32_t)row;
-    for (int k = 0; k < K1; ++k) {
-      auto get = [&](uint32_t i) -> float {
-        const uint32_t v = svals[a + i];
-        if (v >= nvalid) return k == 0 ? 1.0f : 0.0f;  // a free sample
-        return k == 0 ? 0.0f : probs[(size_t)hit_src[v] * K + (k - 1)];
-      };
-      wsoft[(size_t)row * K1 + k] = unit_mean(get, b - a);
+  const int K = K1 - 1, lane = threadIdx.x & 31;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t base = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 32; base < P; base += nw * 32) {
+    const uint32_t t = base + lane;
+    const bool hits = t < P && (label_of(train[t].w) & ((1 << kLabelBits) - 1)) != 0;
+    unsigned todo = __ballot_sync(0xffffffffu, hits);
+    uint32_t row0 = 0;
+    if (lane == 0 && todo) row0 = atomicAdd(&dc->n_soft, (uint32_t)__popc(todo));
+    row0 = __shfl_sync(0xffffffffu, row0, 0);
+    if (t < P) softidx[t] = hits ? (int32_t)(row0 + __popc(todo & ((1u << lane) - 1u))) : -1;
+    for (uint32_t r = row0; todo; todo &= todo - 1u, ++r) {  // warp-uniform
+      const uint32_t tg = base + (uint32_t)(__ffs((int)todo) - 1);
+      const uint32_t a = seg_start[tg], n = seg_start[tg + 1] - a;
+      if (lane < K1) {
+        float w = 0.0f;
+        if (lane > 0) {
+          if (n == 1)
+            w = probs[(size_t)hit_src[svals[a]] * K + (lane - 1)];
+          else
+            w = unit_mean([&](uint32_t i) -> float { return probs[(size_t)hit_src[svals[a + i]] * K + (lane - 1)]; },
+                          n);
+        }
+        wsoft[(size_t)r * K1 + lane] = w;
+      }
     }
   }
 }
@@ -139,7 +153,8 @@ struct WArgs {
   float* alpha;
   int32_t* pairs;
   int32_t sink;
-  int R;                   // sweep half-width in voxels
+  int Rk[kMaxClasses];     // sweep half-width of class k's support, in voxels
+  uint32_t skip;           // hard labels of these classes are the fast form's (per-class supports)
   DevCounters* dc;
 };
 
@@ -159,18 +174,21 @@ __global__ void __launch_bounds__(kWThreads) accumulate_weighted_kernel(WArgs a)
   WTables& t = s_t[wid];
   if (a.dc->err != 0) return;
   const uint32_t P = a.dc->n_train;
-  const int R = a.R, na = 2 * R + 1, ncube = na * na * na, m = g.B - 1;
+  const int m = g.B - 1;
   uint32_t npairs = 0;
   for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < P; i += (gridDim.x * blockDim.x) >> 5) {
     const float4 p = a.train[i];
     const int lw = label_of(p.w);
     const int label = lw & ((1 << kLabelBits) - 1), map = lw >> kLabelBits;
     const int row = a.softidx ? a.softidx[i] : -1;
+    if (row < 0 && ((a.skip >> label) & 1u)) continue;  // warp-uniform
     // weights and the classes that carry one
     float wk = 0.0f;
     if (lane < g.K1) wk = row >= 0 ? a.wsoft[(size_t)row * g.K1 + lane] : (lane == label ? 1.0f : 0.0f);
     const unsigned classes = __ballot_sync(0xffffffffu, lane < g.K1 && wk != 0.0f);
     if (lane < g.K1) t.w[lane] = wk;
+    const int R = __reduce_max_sync(0xffffffffu, (lane < g.K1 && wk != 0.0f) ? a.Rk[lane] : 0);
+    const int na = 2 * R + 1, ncube = na * na * na;
     // per-axis offsets, digits and in-block indices
     int v0[3];
 #pragma unroll
@@ -234,9 +252,9 @@ __global__ void __launch_bounds__(kWThreads) accumulate_weighted_kernel(WArgs a)
 }  // namespace
 
 cudaError_t launch_soft_weights(MapState& m) {
-  const unsigned grid = (unsigned)(m.sm_count * 8);
-  soft_weights_kernel<<<grid, 128, 0, m.stream>>>(m.s.seg_start, m.s.vals, m.s.hit_src, m.s.desc, m.s.softidx,
-                                                  m.s.wsoft, m.g.K1, m.dc);
+  const unsigned grid = (unsigned)(m.sm_count * 8);  // persistent: warps stride over the training points
+  soft_weights_kernel<<<grid, 128, 0, m.stream>>>(m.s.seg_start, m.s.vals, m.s.hit_src, m.s.train, m.s.desc,
+                                                  m.s.softidx, m.s.wsoft, m.g.K1, m.dc);
   m.launches += 1;
   return cudaGetLastError();
 }
@@ -248,10 +266,14 @@ cudaError_t launch_soft_export(MapState& m, float* xyz, float* w, int64_t cap) {
   return cudaGetLastError();
 }
 
-// Zero-fills the blocks created by this update, then the weighted accumulation.
-cudaError_t launch_accumulate_weighted(MapState& m, bool soft) {
-  cudaError_t e = launch_fresh_fill(m);
-  if (e != cudaSuccess) return e;
+// Zero-fills the blocks created by this update (unless the fast form ran
+// first and did), then the weighted accumulation of the points of every class
+// outside `skip`.
+cudaError_t launch_accumulate_weighted(MapState& m, bool soft, bool fill, uint32_t skip) {
+  if (fill) {
+    cudaError_t e = launch_fresh_fill(m);
+    if (e != cudaSuccess) return e;
+  }
   WArgs a;
   a.g = m.g;
   a.train = m.s.train;
@@ -263,10 +285,14 @@ cudaError_t launch_accumulate_weighted(MapState& m, bool soft) {
   a.alpha = m.alpha;
   a.pairs = m.pairs;
   a.sink = (int32_t)m.pool_blocks;
-  // offsets j with |j| - 1/2 >= l_max / res hold no voxel centre within l_max of a point in the voxel
-  a.R = (int)std::ceil(m.g.lmax64 / m.prm.res + 0.5 + 1e-6) - 1;
+  // offsets j with |j| - 1/2 >= l_k / res hold no voxel centre within l_k of a point in the voxel
+  for (int k = 0; k < kMaxClasses; ++k) {
+    const double lk = k < m.g.K1 ? m.prm.length_scale * m.prm.l_scale[k] : 0.0;
+    a.Rk[k] = k < m.g.K1 ? (int)std::ceil(lk / m.prm.res + 0.5 + 1e-6) - 1 : 0;
+    if (2 * a.Rk[k] + 1 > kWAxis - 1) return cudaErrorInvalidValue;
+  }
+  a.skip = soft ? 0u : skip;
   a.dc = m.dc;
-  if (2 * a.R + 1 > kWAxis - 1) return cudaErrorInvalidValue;
   const unsigned grid = (unsigned)(m.sm_count * 16);
   if (m.pairs) accumulate_weighted_kernel<true><<<grid, kWThreads, 0, m.stream>>>(a);
   else accumulate_weighted_kernel<false><<<grid, kWThreads, 0, m.stream>>>(a);

@@ -95,6 +95,22 @@ def test_soft_map_matches_oracle(sb, orc, seed):
     assert _rel(alpha, oalpha).max() <= RTOL
 
 
+def test_soft_map_in_the_weighted_form(sb, orc):
+    """l = 4.5 voxels: beyond the fast point-major form (offsets -3..3), so soft
+    labels take the weighted form (one warp per point over the cube)."""
+    sc, probs = _small_soft_scan(2)
+    prm = dict(scenes.SMALL_SCENE_PARAMS, length_scale=0.45)
+    om = orc.OracleMap(orc.params(**prm))
+    om.insert_scan_soft(sc["points"], probs, sc["pose"])
+    with sb.Map(_params(sb, prm)) as m:
+        m.insert_scan_soft(sc["points"], probs, sc["pose"])
+        keys, alpha, pairs = m.export(pairs=True)
+    okeys, oalpha, opairs = om.export()
+    np.testing.assert_array_equal(keys, okeys)
+    np.testing.assert_array_equal(pairs, opairs)
+    assert _rel(alpha, oalpha).max() <= RTOL
+
+
 def test_one_hot_probabilities_reproduce_the_hard_update(sb):
     sc = scenes.small_region_scan(3)
     prm = dict(scenes.SMALL_SCENE_PARAMS)
@@ -157,7 +173,10 @@ def test_soft_labels_refusals_leave_the_map_unchanged(sb):
 
 # ------------------------------------------------------------ per-class length scales
 
-@pytest.mark.parametrize("seed,ls", [(0, [1.0, 0.6, 1.4, 0.9]), (1, [1.2, 1.0, 0.5, 1.45])])
+# supports in voxels: (2.5, 1.5, 3.5, 2.25) and (3, 2.5, 1.25, 3.625): the fast point-major form takes the
+# classes whose support needs at most 7 offsets per axis, the weighted form the others; (2.5, 0.75, 3, 2.5):
+# a support below half the voxel diagonal sends every class to the weighted form
+@pytest.mark.parametrize("seed,ls", [(0, [1.0, 0.6, 1.4, 0.9]), (1, [1.2, 1.0, 0.5, 1.45]), (2, [1.0, 0.3, 1.2, 1.0])])
 def test_per_class_length_scale_matches_oracle(sb, orc, seed, ls):
     rng = np.random.default_rng(seed)
     n = 1200
