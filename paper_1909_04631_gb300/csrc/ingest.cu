@@ -1158,8 +1158,9 @@ inline unsigned grid_for(int64_t n, int threads) { return (unsigned)((n + thread
 cudaError_t launch_transform_count(MapState& m, int ns, int64_t total_n) {
   const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(total_n, 256), (int64_t)m.sm_count * m.tune.ingest_ctas_per_sm));
   transform_count_kernel<<<blocks, 256, 0, m.stream>>>(m.s.desc, ns, m.g, m.s.world, m.s.cnt, m.dc);
-  m.launches += 1 + 3 + 1;  // transform, scan, check
-  cudaError_t e = exclusive_scan_u64(m.s.cnt, total_n, m.s.scan_tmp, m.stream, &m.dc->n_points);
+  m.launches += 1 + 1 + 1;  // transform, scan, check
+  cudaError_t e = exclusive_scan_u64_onepass(m.s.cnt, total_n, m.s.scan_tmp, m.stream, &m.dc->n_points, m.sm_count,
+                                             m.dc);
   if (e != cudaSuccess) return e;
   check_counts_kernel<<<1, 1, 0, m.stream>>>(m.s.cnt, m.s.s_cap, m.dc);
   return cudaGetLastError();

@@ -58,6 +58,7 @@ constexpr size_t kHistEntries = (size_t)sbki::radix_work_entries(kMaxItems);
 constexpr size_t kOffHist = align256(kOffCarry + (size_t)sbki::kSegCarryBytes * 2 * sbki::seg_tiles(kMaxItems));
 constexpr size_t kOffScanTmp = align256(kOffHist + 4 * kHistEntries);
 constexpr size_t kScanTmpBytes = 8 * ((kMaxItems + 2) / 2048 + 64);  // partial sums of the largest scan
+static_assert(kScanTmpBytes >= (size_t)sbki::scan_tmp_bytes_ce(kMaxPoints + 1), "prefix-sum scratch");
 constexpr size_t kOffDesc = align256(kOffScanTmp + kScanTmpBytes);
 constexpr size_t kScratchBytes = align256(kOffDesc + 2 * sizeof(sbki::ScanDesc));
 

@@ -309,6 +309,11 @@ cudaError_t exclusive_scan_u32(uint32_t* data, int64_t n, void* tmp, cudaStream_
 cudaError_t exclusive_scan_u64(unsigned long long* data, int64_t n, void* tmp, cudaStream_t st,
                                const uint32_t* n_dev = nullptr);
 int64_t scan_tmp_bytes(int64_t n);
+// scratch of either form for n entries: the partial sums, or a counter, flags and two values per tile of 2048
+constexpr int64_t scan_tmp_bytes_ce(int64_t n) { return 24 * ((n + 2047) / 2048 + 2); }
+// one launch (chained tiles, bounded look-back: SBKI_ERR_TIMEOUT in dc when a wait runs out); sm_count sizes the grid
+cudaError_t exclusive_scan_u64_onepass(unsigned long long* data, int64_t n, void* tmp, cudaStream_t st,
+                                       const uint32_t* n_dev, int sm_count, DevCounters* dc);
 
 // radix_sort.cu: stable LSD sort of (keys, vals) over bits [0, bits) (at most
 // 8 passes of 8 bits); count read from *n_dev, cap >= count bounds the work

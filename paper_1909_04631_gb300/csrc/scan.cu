@@ -1,5 +1,8 @@
-// Device-wide exclusive prefix sums (reduce, scan of tile totals, downsweep).
-// Three launches, no inter-CTA waiting, deterministic.
+// Device-wide exclusive prefix sums: reduce, scan of tile totals, downsweep
+// (three launches, no inter-CTA waiting), and a one-pass form (below) for the
+// prefix sum of every update.  Both deterministic (integer sums).
+#include <algorithm>
+
 #include "sbki_internal.cuh"
 
 namespace sbki {
@@ -8,6 +11,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kIpt = 8;
 constexpr int kTile = kThreads * kIpt;
+static_assert(scan_tmp_bytes_ce(kTile) == 24 * 3, "scratch sizing assumes tiles of 2048");
 
 template <typename T>
 __device__ T block_exclusive_scan(T v, T* warp_tot, T* total) {
@@ -123,9 +127,148 @@ cudaError_t scan_impl(T* data, int64_t n, void* tmp, cudaStream_t st, const uint
   return cudaGetLastError();
 }
 
+// One-pass form: tiles are claimed in order from a counter; each publishes its
+// sum ("aggregate", flag 1), then warp 0 looks back over the preceding tiles
+// 32 at a time, adding aggregates until it meets an inclusive prefix (flag 2),
+// and publishes its own inclusive prefix (a chained scan with decoupled
+// look-back: a tile waits only on earlier tiles, all claimed by running CTAs).
+// A value is written before its flag with a fence between, and read after it.
+// A wait that outlasts kMaxSpin polls sets SBKI_ERR_TIMEOUT and publishes
+// anyway, so no later tile waits on it.  tmp: [counter, pad] u32, flags
+// u32[ntiles_cap], then aggregates and inclusive prefixes T[ntiles_cap] each
+// (flags and counter zero on entry).
+constexpr int kMaxSpin = 1 << 20;
+
+template <typename T>
+__device__ __forceinline__ T vload(const T* p) { return *reinterpret_cast<const volatile T*>(p); }
+template <typename T>
+__device__ __forceinline__ void vstore(T* p, T v) { *reinterpret_cast<volatile T*>(p) = v; }
+
+struct OnePass {
+  uint32_t* ctr;
+  uint32_t* flags;
+  void* agg;
+  void* incl;
+};
+__host__ __device__ inline OnePass onepass_of(void* tmp, int64_t ntiles_cap) {
+  OnePass o;
+  o.ctr = static_cast<uint32_t*>(tmp);
+  o.flags = o.ctr + 2;
+  unsigned char* v = reinterpret_cast<unsigned char*>(o.flags + ntiles_cap + (ntiles_cap & 1));  // 8-byte aligned
+  o.agg = v;
+  o.incl = v + 8 * ntiles_cap;
+  return o;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) scan_onepass(T* data, int64_t cap, const uint32_t* n_dev, OnePass o,
+                                                         DevCounters* dc) {
+  __shared__ T tile[kTile];
+  __shared__ T warp_tot[kThreads / 32];
+  __shared__ T total;
+  __shared__ T s_excl;
+  __shared__ uint32_t s_t;
+  T* agg = static_cast<T*>(o.agg);
+  T* incl = static_cast<T*>(o.incl);
+  const int64_t n = count_of(cap, n_dev);
+  const int64_t nt = (n + kTile - 1) / kTile;
+  if (nt == 0 && blockIdx.x == 0 && threadIdx.x == 0) data[0] = T(0);
+  const int lane = threadIdx.x & 31;
+  for (;;) {
+    if (threadIdx.x == 0) s_t = atomicAdd(o.ctr, 1u);
+    __syncthreads();
+    const int64_t t = s_t;
+    if (t >= nt) break;
+    const int64_t base = t * kTile;
+    for (int i = threadIdx.x; i < kTile; i += kThreads) tile[i] = base + i < n ? data[base + i] : T(0);
+    __syncthreads();
+    T loc[kIpt];
+    T sum = 0;
+#pragma unroll
+    for (int k = 0; k < kIpt; ++k) {
+      loc[k] = tile[threadIdx.x * kIpt + k];
+      sum += loc[k];
+    }
+    T ex = block_exclusive_scan<T>(sum, warp_tot, &total);
+    if (threadIdx.x < 32) {  // warp 0: publish, look back, publish the inclusive prefix
+      const T tsum = total;
+      T prefix = 0;
+      if (t == 0) {
+        if (lane == 0) {
+          vstore(incl, tsum);
+          __threadfence();
+          vstore(o.flags, 2u);
+        }
+      } else {
+        if (lane == 0) {
+          vstore(agg + t, tsum);
+          __threadfence();
+          vstore(o.flags + t, 1u);
+        }
+        int64_t j = t - 1;  // nearest predecessor not yet added
+        int spins = 0;
+        for (;;) {
+          const int64_t q = j - lane;
+          const uint32_t f = q >= 0 ? vload(o.flags + q) : 2u;
+          const unsigned pre = __ballot_sync(0xffffffffu, f == 2u);
+          const unsigned none = __ballot_sync(0xffffffffu, f == 0u);
+          const int stop = pre ? __ffs((int)pre) - 1 : 31;  // lanes 0..stop are needed
+          const unsigned need = stop == 31 ? 0xffffffffu : ((2u << stop) - 1u);
+          if (none & need) {  // a needed predecessor has not published yet
+            if (++spins > kMaxSpin) {
+              if (lane == 0) set_error(dc, SBKI_ERR_TIMEOUT);
+              break;
+            }
+            __nanosleep(20);
+            continue;
+          }
+          __threadfence();
+          T v = 0;
+          if (lane <= stop && q >= 0) v = f == 2u ? vload(incl + q) : vload(agg + q);
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+          prefix += v;
+          if (pre) break;
+          j -= 32;
+        }
+        if (lane == 0) {
+          vstore(incl + t, prefix + tsum);
+          __threadfence();
+          vstore(o.flags + t, 2u);
+        }
+      }
+      if (lane == 0) s_excl = prefix;
+    }
+    __syncthreads();
+    ex += s_excl;
+#pragma unroll
+    for (int k = 0; k < kIpt; ++k) {
+      tile[threadIdx.x * kIpt + k] = ex;
+      ex += loc[k];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kTile; i += kThreads)
+      if (base + i < n) data[base + i] = tile[i];
+    if (t == nt - 1 && threadIdx.x == 0) data[n] = s_excl + total;
+    __syncthreads();
+  }
+}
+
 }  // namespace
 
-int64_t scan_tmp_bytes(int64_t n) { return ((n + kTile - 1) / kTile + 1) * (int64_t)sizeof(unsigned long long); }
+int64_t scan_tmp_bytes(int64_t n) { return scan_tmp_bytes_ce(n); }
+
+cudaError_t exclusive_scan_u64_onepass(unsigned long long* data, int64_t n, void* tmp, cudaStream_t st,
+                                       const uint32_t* n_dev, int sm_count, DevCounters* dc) {
+  if (n <= 0) return cudaMemsetAsync(data, 0, sizeof(unsigned long long), st);
+  const int64_t nt = (n + kTile - 1) / kTile;
+  const OnePass o = onepass_of(tmp, nt);
+  cudaError_t e = cudaMemsetAsync(tmp, 0, sizeof(uint32_t) * (2 + nt), st);
+  if (e != cudaSuccess) return e;
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nt, (int64_t)sm_count * 4));
+  scan_onepass<unsigned long long><<<grid, kThreads, 0, st>>>(data, n, n_dev, o, dc);
+  return cudaGetLastError();
+}
 
 cudaError_t exclusive_scan_u32(uint32_t* data, int64_t n, void* tmp, cudaStream_t st, const uint32_t* n_dev) {
   return scan_impl<uint32_t>(data, n, tmp, st, n_dev);
