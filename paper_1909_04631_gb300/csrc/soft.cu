@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <climits>
 
+#include "exact_round.cuh"
 #include "kernel_value.cuh"
 #include "point_common.cuh"
 
@@ -36,13 +37,48 @@ __device__ __forceinline__ bool split_float(float v, unsigned& m, int& e) {
   return true;
 }
 
+// Exact mean of n values in [0, 1] rounded once to FP32, 64-bit form: with
+// every nonzero value m 2^e (m < 2^24) and E the smallest e, the sum is the
+// integer T = sum m 2^(e - E) times 2^E, which fits 64 bits when the values
+// span few enough binades; round_mean64 rounds T 2^E / n.  False (nothing
+// decided) when they span more, for n >= 2^16, or for a mean below the FP32
+// normal range.
+template <typename Get>
+__device__ bool unit_mean_int(Get get, uint32_t n, float& out) {
+  if (n >= (1u << 16)) return false;
+  int emin = INT_MAX, emax = INT_MIN;
+  for (uint32_t i = 0; i < n; ++i) {
+    unsigned m;
+    int e;
+    if (split_float(get(i), m, e)) {
+      emin = min(emin, e);
+      emax = max(emax, e);
+    }
+  }
+  if (emin == INT_MAX) {  // all zero
+    out = 0.0f;
+    return true;
+  }
+  if (emax - emin + 24 + (32 - __clz((int)n)) > 63) return false;
+  unsigned long long T = 0ull;
+  for (uint32_t i = 0; i < n; ++i) {
+    unsigned m;
+    int e;
+    if (split_float(get(i), m, e)) T += (unsigned long long)m << (e - emin);
+  }
+  return round_mean64(T, n, emin, out);
+}
+
 // Exact mean of n values in [0, 1] rounded once to FP32 (nearest, ties to
-// even).  The sum is held in units of 2^-149 in 6 32-bit limbs (a value below
-// 2^1 needs 150 bits, n < 2^32 adds at most 32), divided by n limb by limb
-// from the top with 3 fractional limbs, and rounded to 24 significant bits
-// (fewer for a result below the FP32 normal range).
+// even): the 64-bit form when it can decide, else the sum is held in units of
+// 2^-149 in 6 32-bit limbs (a value below 2^1 needs 150 bits, n < 2^32 adds at
+// most 32), divided by n limb by limb from the top with 3 fractional limbs,
+// and rounded to 24 significant bits (fewer for a result below the FP32
+// normal range).
 template <typename Get>
 __device__ float unit_mean(Get get, uint32_t n) {
+  float f;
+  if (unit_mean_int(get, n, f)) return f;
   uint32_t w[6] = {0u, 0u, 0u, 0u, 0u, 0u};
   for (uint32_t i = 0; i < n; ++i) {
     unsigned m;
