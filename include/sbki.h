@@ -393,10 +393,12 @@ sbki_status sbki_query_points(const sbki_params* params, const float* xyzl, int6
 sbki_status sbki_import(sbki_map* map, const int64_t* keys, const float* alpha, int64_t count);
 
 /* Failure-detection self-test on `device` (diagnostic): runs one digit pass
- * of the downsampling step's radix sort over three tiles whose first tile is
- * never processed, so every bounded wait of the others on it runs out (about a
- * second); the kernel reports SBKI_ERR_TIMEOUT in *device_status instead of
- * spinning, and the context stays usable.  Returns SBKI_OK when the test itself
+ * of the downsampling step's radix sort, then the one-pass prefix sum of the
+ * sample offsets, each over three tiles whose first tile is never processed,
+ * so every bounded wait of the others on it runs out (about a second each);
+ * the kernels report SBKI_ERR_TIMEOUT instead of spinning, and the context
+ * stays usable.  *device_status: SBKI_ERR_TIMEOUT when the waits of both ran
+ * out, else the first other status.  Returns SBKI_OK when the test itself
  * ran. */
 sbki_status sbki_selftest_bounded_wait(int32_t device, int32_t* device_status);
 

@@ -397,6 +397,9 @@ __global__ void bin_cursor_kernel(const uint32_t* touched, uint32_t* hcnt, uint3
   }
 }
 
+// Pool slots for the blocks this update created, or (an error pending, or the
+// pool would overflow) their hash slots cleared again.  The last CTA to finish
+// (a counter after a fence) then commits the block count.
 __global__ void commit_kernel(unsigned long long* hkeys, int32_t* hvals, const uint32_t* fresh,
                               unsigned long long* pool_keys, int64_t pool_blocks, DevCounters* dc) {
   const uint32_t n_new = dc->n_new;
@@ -413,17 +416,20 @@ __global__ void commit_kernel(unsigned long long* hkeys, int32_t* hvals, const u
       pool_keys[pool] = hkeys[slot];
     }
   }
-}
-
-__global__ void commit_counts_kernel(int64_t pool_blocks, DevCounters* dc) {
-  const uint32_t nb = dc->n_blocks;
-  dc->n_blocks_before = nb;
-  if (dc->err != 0) return;
-  if ((unsigned long long)nb + dc->n_new > (unsigned long long)pool_blocks) {
-    set_error(dc, SBKI_ERR_CAPACITY);
-    return;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(&dc->commit_done, 1u) == gridDim.x - 1) {  // every CTA has read n_blocks
+      dc->commit_done = 0u;
+      dc->n_blocks_before = nb;
+      if (pending) return;
+      if (overflow) {
+        set_error(dc, SBKI_ERR_CAPACITY);
+        return;
+      }
+      dc->n_blocks = nb + n_new;
+    }
   }
-  dc->n_blocks = nb + dc->n_new;
 }
 
 // Restoring exported contents: the blocks of the given voxel keys (warp-deduplicated
@@ -557,8 +563,7 @@ cudaError_t launch_import(MapState& m, const int64_t* keys, const float* alpha, 
 
 cudaError_t launch_commit_blocks(MapState& m) {
   commit_kernel<<<m.sm_count * 2, 256, 0, m.stream>>>(m.hkeys, m.hvals, m.s.fresh, m.pool_keys, m.pool_blocks, m.dc);
-  commit_counts_kernel<<<1, 1, 0, m.stream>>>(m.pool_blocks, m.dc);
-  m.launches += 2;
+  m.launches += 1;
   return cudaGetLastError();
 }
 

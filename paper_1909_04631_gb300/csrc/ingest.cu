@@ -20,8 +20,6 @@
 namespace sbki {
 namespace {
 
-constexpr unsigned long long kValidOne = 1ull << 40;
-constexpr unsigned long long kFreeMask = kValidOne - 1;
 
 
 __device__ __forceinline__ int floor_i(float v) { return (int)floorf(v); }
@@ -168,21 +166,6 @@ __global__ void __launch_bounds__(256) transform_count_kernel(const ScanDesc* __
   if (threadIdx.x < 3 && s_box[threadIdx.x] <= s_box[3 + threadIdx.x]) {
     atomicMin(&dc->tbox[threadIdx.x], s_box[threadIdx.x]);
     atomicMax(&dc->tbox[3 + threadIdx.x], s_box[3 + threadIdx.x]);
-  }
-}
-
-__global__ void check_counts_kernel(const unsigned long long* cnt, int64_t cap, DevCounters* dc) {
-  const unsigned long long tot = cnt[dc->n_points];
-  const uint32_t nv = (uint32_t)(tot >> 40);
-  const unsigned long long nf = tot & kFreeMask;
-  dc->n_valid = nv;
-  dc->n_free = nf;
-  const unsigned long long items = (unsigned long long)nv + nf;
-  if (items > (unsigned long long)cap) {
-    set_error(dc, SBKI_ERR_CAPACITY);
-    dc->n_items = 0;
-  } else {
-    dc->n_items = (uint32_t)items;
   }
 }
 
@@ -1116,11 +1099,10 @@ inline unsigned grid_for(int64_t n, int threads) { return (unsigned)((n + thread
 cudaError_t launch_transform_count(MapState& m, int ns, int64_t total_n) {
   const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(grid_for(total_n, 256), (int64_t)m.sm_count * m.tune.ingest_ctas_per_sm));
   transform_count_kernel<<<blocks, 256, 0, m.stream>>>(m.s.desc, ns, m.g, m.s.world, m.s.cnt, m.dc);
-  m.launches += 1 + 1 + 1;  // transform, scan, check
+  m.launches += 1 + 1;  // transform, prefix sum (which also checks the item count against the capacity)
   cudaError_t e = exclusive_scan_u64_onepass(m.s.cnt, total_n, m.s.scan_tmp, m.stream, &m.dc->n_points, m.sm_count,
-                                             m.dc);
+                                             m.dc, m.s.s_cap);
   if (e != cudaSuccess) return e;
-  check_counts_kernel<<<1, 1, 0, m.stream>>>(m.s.cnt, m.s.s_cap, m.dc);
   return cudaGetLastError();
 }
 

@@ -1502,9 +1502,17 @@ sbki_status sbki_selftest_bounded_wait(int32_t device, int32_t* device_status) {
   if (e == cudaSuccess) e = dalloc(&dc, 1);
   if (e == cudaSuccess) e = cudaMemsetAsync(dc, 0, sizeof(DevCounters), st);
   if (e == cudaSuccess) e = radix_wait_selftest(keys, vals, keys_out, vals_out, n_dev, work, dc, st);
-  int32_t err = 0;
+  int32_t err = 0, err2 = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&err, &dc->err, sizeof(err), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  // the one-pass prefix sum's wait, on the same buffers (keys: the data, work: its scratch)
+  static_assert(kScanSelftestItems + 1 <= kSelftestItems, "self-test buffers");
+  static_assert(scan_tmp_bytes_ce(kScanSelftestItems) <= 4 * radix_work_entries(kSelftestItems), "self-test scratch");
+  if (e == cudaSuccess) e = cudaMemsetAsync(dc, 0, sizeof(DevCounters), st);
+  if (e == cudaSuccess) e = scan_wait_selftest(keys, work, dc, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&err2, &dc->err, sizeof(err2), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (err == SBKI_ERR_TIMEOUT) err = err2;  // both waits must have run out
   void* ptrs[] = {keys, keys_out, vals, vals_out, n_dev, work, dc};
   for (void* p : ptrs) cudaFree(p);
   if (st) cudaStreamDestroy(st);

@@ -51,7 +51,12 @@ struct DevCounters {
   int32_t tbox[6];                    // ds-tile bounding box of the kept hits (min xyz, max xyz)
   uint32_t acc_next;                  // work queue head of the point-major accumulation (reset before it)
   uint32_t n_soft;                    // soft labels: training points with a weight row, this scan
+  uint32_t commit_done;               // CTAs of the commit launch finished (the last one commits the count)
 };
+
+// per-point sample counts of a1/a2: kept hits in bits 40.., free samples below
+constexpr unsigned long long kValidOne = 1ull << 40;
+constexpr unsigned long long kFreeMask = kValidOne - 1;
 
 // ---------------------------------------------------------------- geometry constants
 // Every value that decides an integer (key, count, membership) is computed
@@ -312,8 +317,17 @@ int64_t scan_tmp_bytes(int64_t n);
 // scratch of either form for n entries: the partial sums, or a counter, flags and two values per tile of 2048
 constexpr int64_t scan_tmp_bytes_ce(int64_t n) { return 24 * ((n + 2047) / 2048 + 2); }
 // one launch (chained tiles, bounded look-back: SBKI_ERR_TIMEOUT in dc when a wait runs out); sm_count sizes the grid
+// Failure-detection self-test of the one-pass form: a scan of kScanSelftestItems
+// zeros (data: that many + 1 entries; tmp: scan_tmp_bytes_ce of them; dc
+// zeroed) whose tile counter starts at 1, so tile 0 never publishes and the
+// look-back of tile 1 runs out with SBKI_ERR_TIMEOUT.
+constexpr int64_t kScanSelftestItems = 3 * 2048;
+cudaError_t scan_wait_selftest(unsigned long long* data, void* tmp, DevCounters* dc, cudaStream_t st);
+// items_cap >= 0: data are the per-point sample counts of a1/a2 and the grand
+// total also sets dc->n_valid, n_free and n_items (SBKI_ERR_CAPACITY and no
+// items when they exceed items_cap)
 cudaError_t exclusive_scan_u64_onepass(unsigned long long* data, int64_t n, void* tmp, cudaStream_t st,
-                                       const uint32_t* n_dev, int sm_count, DevCounters* dc);
+                                       const uint32_t* n_dev, int sm_count, DevCounters* dc, int64_t items_cap = -1);
 
 // radix_sort.cu: stable LSD sort of (keys, vals) over bits [0, bits) (at most
 // 8 passes of 8 bits); count read from *n_dev, cap >= count bounds the work

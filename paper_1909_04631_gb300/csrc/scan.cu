@@ -12,6 +12,7 @@ constexpr int kThreads = 256;
 constexpr int kIpt = 8;
 constexpr int kTile = kThreads * kIpt;
 static_assert(scan_tmp_bytes_ce(kTile) == 24 * 3, "scratch sizing assumes tiles of 2048");
+static_assert(kScanSelftestItems == 3 * kTile, "self-test: three tiles");
 
 template <typename T>
 __device__ T block_exclusive_scan(T v, T* warp_tot, T* total) {
@@ -160,9 +161,24 @@ __host__ __device__ inline OnePass onepass_of(void* tmp, int64_t ntiles_cap) {
   return o;
 }
 
+// the grand total of the per-point sample counts: hits, free samples, items (capacity check)
+__device__ __forceinline__ void finish_counts(unsigned long long total, int64_t items_cap, DevCounters* dc) {
+  const uint32_t nv = (uint32_t)(total >> 40);
+  const unsigned long long nf = total & kFreeMask;
+  dc->n_valid = nv;
+  dc->n_free = nf;
+  const unsigned long long items = (unsigned long long)nv + nf;
+  if (items > (unsigned long long)items_cap) {
+    set_error(dc, SBKI_ERR_CAPACITY);
+    dc->n_items = 0;
+  } else {
+    dc->n_items = (uint32_t)items;
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kThreads) scan_onepass(T* data, int64_t cap, const uint32_t* n_dev, OnePass o,
-                                                         DevCounters* dc) {
+                                                         DevCounters* dc, int64_t items_cap) {
   __shared__ T tile[kTile];
   __shared__ T warp_tot[kThreads / 32];
   __shared__ T total;
@@ -172,7 +188,10 @@ __global__ void __launch_bounds__(kThreads) scan_onepass(T* data, int64_t cap, c
   T* incl = static_cast<T*>(o.incl);
   const int64_t n = count_of(cap, n_dev);
   const int64_t nt = (n + kTile - 1) / kTile;
-  if (nt == 0 && blockIdx.x == 0 && threadIdx.x == 0) data[0] = T(0);
+  if (nt == 0 && blockIdx.x == 0 && threadIdx.x == 0) {
+    data[0] = T(0);
+    if (items_cap >= 0) finish_counts(0ull, items_cap, dc);
+  }
   const int lane = threadIdx.x & 31;
   for (;;) {
     if (threadIdx.x == 0) s_t = atomicAdd(o.ctr, 1u);
@@ -249,7 +268,10 @@ __global__ void __launch_bounds__(kThreads) scan_onepass(T* data, int64_t cap, c
     __syncthreads();
     for (int i = threadIdx.x; i < kTile; i += kThreads)
       if (base + i < n) data[base + i] = tile[i];
-    if (t == nt - 1 && threadIdx.x == 0) data[n] = s_excl + total;
+    if (t == nt - 1 && threadIdx.x == 0) {
+      data[n] = s_excl + total;
+      if (items_cap >= 0) finish_counts((unsigned long long)(s_excl + total), items_cap, dc);
+    }
     __syncthreads();
   }
 }
@@ -258,15 +280,28 @@ __global__ void __launch_bounds__(kThreads) scan_onepass(T* data, int64_t cap, c
 
 int64_t scan_tmp_bytes(int64_t n) { return scan_tmp_bytes_ce(n); }
 
+cudaError_t scan_wait_selftest(unsigned long long* data, void* tmp, DevCounters* dc, cudaStream_t st) {
+  const int64_t n = kScanSelftestItems, nt = (n + kTile - 1) / kTile;
+  const OnePass o = onepass_of(tmp, nt);
+  cudaError_t e = cudaMemsetAsync(tmp, 0, sizeof(uint32_t) * (2 + nt), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(data, 0, sizeof(unsigned long long) * (n + 1), st);
+  const uint32_t one = 1u;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(o.ctr, &one, sizeof(one), cudaMemcpyHostToDevice, st);  // skip tile 0
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // `one` lives on this stack frame
+  if (e != cudaSuccess) return e;
+  scan_onepass<unsigned long long><<<2, kThreads, 0, st>>>(data, n, nullptr, o, dc, -1);
+  return cudaGetLastError();
+}
+
 cudaError_t exclusive_scan_u64_onepass(unsigned long long* data, int64_t n, void* tmp, cudaStream_t st,
-                                       const uint32_t* n_dev, int sm_count, DevCounters* dc) {
-  if (n <= 0) return cudaMemsetAsync(data, 0, sizeof(unsigned long long), st);
+                                       const uint32_t* n_dev, int sm_count, DevCounters* dc, int64_t items_cap) {
+  if (n <= 0) n = 0;  // the kernel writes data[0] = 0 (and the counts) for an empty input
   const int64_t nt = (n + kTile - 1) / kTile;
   const OnePass o = onepass_of(tmp, nt);
   cudaError_t e = cudaMemsetAsync(tmp, 0, sizeof(uint32_t) * (2 + nt), st);
   if (e != cudaSuccess) return e;
   const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(nt, (int64_t)sm_count * 4));
-  scan_onepass<unsigned long long><<<grid, kThreads, 0, st>>>(data, n, n_dev, o, dc);
+  scan_onepass<unsigned long long><<<grid, kThreads, 0, st>>>(data, n, n_dev, o, dc, items_cap);
   return cudaGetLastError();
 }
 
