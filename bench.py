@@ -598,13 +598,25 @@ def run_ours(args, rank, world, local_rank):
         secs_all = pool.run(8 * cores)
         pool.close()
         rate, prate, secs = oracle_rate(scans[:2], 12, 8)
+        depth = None
+        if forms_input is not None:  # one ray in eight of a 640x480 depth frame of the room sequence, one core
+            from oracle import oracle as O
+            fr = forms_input[3][0]
+            om = O.OracleMap(O.params(**scenes.ROOM_PARAMS))
+            t0 = time.perf_counter()
+            om.insert_scan(fr["points"][::8], fr["labels"][::8], fr["pose"])
+            dt = time.perf_counter() - t0
+            depth = {"value": 1.0 / (8.0 * dt), "unit": "frames/s", "cores": 1,
+                     "sample": "one ray in eight of a 640x480 depth frame (room sequence, 0.05 m voxels); "
+                               "frames/s = 1 / (8 x %.2f s)" % dt}
         cpu = {"value": cores / secs_all, "unit": "scans/s", "cores": cores, "kind": "oracle",
                "sample": "%d azimuth sectors of 45 deg (sectors of scans 0 and 1 of 64x2048, cycled), FP64, "
                          "%d host cores in parallel (one process and map each); scans/s = %d / %.2f s"
                          % (8 * cores, cores, cores, secs_all),
                "one_core": {"value": rate, "cores": 1, "pairs_per_s": prate,
                             "sample": "12 azimuth sectors of 45 deg (scan 0, half of scan 1) into one map; "
-                                      "scans/s = 1.5 / %.2f s" % secs}}
+                                      "scans/s = 1.5 / %.2f s" % secs},
+               "one_core_depth": depth}
 
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
@@ -675,13 +687,19 @@ def run_ours(args, rank, world, local_rank):
     if rank != 0:
         return 0
     # per-scan counts (untimed): the same scans in the same order into a fresh map, one synchronous update each
-    stats = []
+    # and each such update timed on its own (CUDA events around it): the per-scan latency
+    stats, lat = [], []
     with sb.Map(p, stream=stream) as sm:
         for i in range(args.warmup + args.steps):
             j = i % nscan
+            q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            q0.record(stream)
             s = sm.insert_scan(dpts[j], dlab[j], poses[j])
+            q1.record(stream)
             if i >= args.warmup:
                 stats.append(s)
+                q1.synchronize()
+                lat.append(q0.elapsed_time(q1))
     assert stats[-1]["pairs"] == last["pairs"] and stats[-1]["train_points"] == last["train_points"]
     # voxels touched per scan (untimed): the block-major form counts them; the
     # same scans in the same order into a fresh map give the same touched sets
@@ -745,6 +763,8 @@ def run_ours(args, rank, world, local_rank):
                      "blocks": prof["blocks_ms"] / max(1, prof["inserts"]),
                      "accumulate": prof["accumulate_ms"] / max(1, prof["inserts"])},
         "roofline": roof,
+        "per_scan_ms": {"median": float(np.median(lat)), "p90": float(np.percentile(lat, 90)),
+                        "source": "%d synchronous sbki_insert_scan calls, CUDA events around each" % len(lat)},
         "accumulate_forms_ms": {"point_major": prof["accumulate_ms"] / max(1, prof["inserts"]),
                                 "block_major": acc_prof["accumulate_ms"] / max(1, acc_prof["inserts"])},
         "clocks": clk.summary(),
