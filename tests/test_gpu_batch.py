@@ -164,3 +164,40 @@ def test_tuning_changes_speed_not_results(sb, scans):
     assert mode in (0, 1) and "accumulate_mode" not in shapes
     with pytest.raises(sb.SbkiError):
         sb.Map(_params(sb, 1)).set_tuning(accumulate_chunk=0)
+
+
+@pytest.mark.parametrize("rule", ["l_scale", "association", "sigma0_scale"])
+def test_batch_under_the_other_map_rules(sb, orc, scans, rule):
+    """The recorded update with per-class length scales (fast and weighted
+    forms in one graph), the extended-block association, or per-class kernel
+    scales: every map against the oracle, also after a replay."""
+    K1 = PRM["num_classes"] + 1
+    vals = [1.0 + 0.25 * ((k % 5) - 2) / 2.0 for k in range(K1)]  # 0.75 .. 1.25: some supports above 7 offsets
+    p = _params(sb, 3)
+    oprm = dict(PRM)
+    if rule == "association":
+        p.association = 1
+        oprm["association"] = 1
+    else:
+        sb.set_param(p, rule, vals)
+        oprm[rule] = vals
+    batch = _as_batch(scans[:3], [0, 1, 2])
+    oms = []
+    for sc in scans[:3]:
+        om = orc.OracleMap(orc.params(**oprm))
+        om.insert_scan(sc["points"], sc["labels"], sc["pose"])
+        oms.append(om)
+    with sb.Map(p) as m:
+        m.insert_batch(batch)
+        for i, om in enumerate(oms):
+            _assert_map_equal(m, i, om)
+        m.insert_batch(batch)  # replay: the same increments again
+        for i, om in enumerate(oms):
+            m.select(i)
+            keys, alpha, pairs = m.export(pairs=True)
+            okeys, oalpha, opairs = om.export()
+            np.testing.assert_array_equal(keys, okeys)
+            np.testing.assert_array_equal(pairs, 2 * opairs)
+            a0 = PRM["alpha0"]
+            rel = np.abs((alpha.astype(np.float64) - a0) - 2 * (oalpha - a0)) / (oalpha - a0 + 1e-30)
+            assert rel[oalpha > 2 * a0].max(initial=0.0) <= 2e-5
