@@ -1,14 +1,16 @@
 // Soft labels (reading K15) and per-class length scales (reading K16).
 //
 // Weights: after the downsampling (groups by cell and most probable class),
-// every group holding a hit gets, per class 0..K, the exact mean of its
+// every group of hits (class 1..K) gets, per class 0..K, the exact mean of its
 // members' weights rounded once to FP32 (a hit's weights are 0 for class 0 and
-// its probability vector for classes 1..K; a free sample's are one for class
-// 0).  Groups of free samples only keep the implicit weight vector one-hot(0)
-// and no row.
+// its probability vector for classes 1..K).  Groups of free samples (class 0)
+// keep the implicit weight vector one-hot(0) and no row.
 //
 // Weighted accumulation (Eq. (alpha_kernel) with the one-hot y_i replaced by a
-// weight vector, and class k's kernel sigma0 s_k f(d/l_k) with support l_k):
+// weight vector, and class k's kernel sigma0 s_k f(d/l_k) with support l_k),
+// for what the fast point-major form does not take (class supports beyond 7
+// offsets per axis or below half the voxel diagonal, soft labels without the
+// fast form's tables):
 // one warp per training point sweeps the cube of voxel offsets within
 // +-R of the point's voxel, R the largest of its weighted classes' R_k
 // (offsets j with |j| - 1/2 >= l_k / res hold no voxel centre within l_k of a
