@@ -169,9 +169,11 @@ __global__ void __launch_bounds__(256) transform_count_kernel(const ScanDesc* __
   }
 }
 
-// Step a2 for every scan of the update: one warp per 32 consecutive points
-// (which may belong to different scans); the warp writes each beam's samples
-// together.  Hits go to items [0, hits), free samples after all hits.
+// Step a2 for every scan of the update: one warp per 8 consecutive points
+// (which may belong to different scans; 8 rather than 32 so that four times
+// the warps hide the latency of the per-beam loop); the warp writes each
+// beam's samples together.  Hits go to items [0, hits), free samples after
+// all hits.
 __global__ void __launch_bounds__(256) emit_kernel(const float4* __restrict__ world,
                                                    const unsigned long long* __restrict__ cnt,
                                                    const ScanDesc* __restrict__ desc, int ns, Geom g, KeyFrame kf,
@@ -187,8 +189,9 @@ __global__ void __launch_bounds__(256) emit_kernel(const float4* __restrict__ wo
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const unsigned long long nvalid = cnt[n] >> 40;
-  for (int64_t base = warp * 32; base < n; base += nwarps * 32) {
-    const int64_t i = base + lane;
+  constexpr int kPerWarp = 8;  // points (beams) per warp task
+  for (int64_t base = warp * kPerWarp; base < n; base += nwarps * kPerWarp) {
+    const int64_t i = lane < kPerWarp ? base + lane : n;
     uint32_t nfree = 0;
     unsigned long long fpos = 0;
     float ex = 0.f, ey = 0.f, ez = 0.f, rr = 0.f, ox = 0.f, oy = 0.f, oz = 0.f;
@@ -218,7 +221,7 @@ __global__ void __launch_bounds__(256) emit_kernel(const float4* __restrict__ wo
         rr = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(ex, ex), __fmul_rn(ey, ey)), __fmul_rn(ez, ez)));
       }
     }
-    for (int src = 0; src < 32; ++src) {
+    for (int src = 0; src < kPerWarp; ++src) {
       const uint32_t m = __shfl_sync(0xffffffffu, nfree, src);
       if (m == 0) continue;
       const float sx = __shfl_sync(0xffffffffu, ex, src);
@@ -1107,7 +1110,7 @@ cudaError_t launch_transform_count(MapState& m, int ns, int64_t total_n) {
 }
 
 cudaError_t launch_emit(MapState& m, int ns, int64_t total_n, const KeyFrame& kf, uint32_t* hit_src) {
-  const int64_t warps = (total_n + 31) / 32;
+  const int64_t warps = (total_n + 7) / 8;
   unsigned blocks = (unsigned)std::min<int64_t>((warps + 7) / 8, (int64_t)m.sm_count * m.tune.ingest_ctas_per_sm);
   if (blocks == 0) blocks = 1;
   emit_kernel<<<blocks, 256, 0, m.stream>>>(m.s.world, m.s.cnt, m.s.desc, ns, m.g, kf, m.s.items, m.s.keys, m.s.vals,
