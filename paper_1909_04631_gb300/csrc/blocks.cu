@@ -227,7 +227,7 @@ __device__ __forceinline__ void add_touched(uint32_t nfirst, DevCounters* dc) {
 // inserting lane also adds the number of lanes that touch the block to its
 // point count (used to lay out the per-block point lists).
 template <bool kCount>
-__global__ void __launch_bounds__(256) touch_kernel(TouchArgs a) {
+__global__ void __launch_bounds__(256, 5) touch_kernel(TouchArgs a) {  // 48 registers: five CTAs per SM
   const Geom& g = a.g;
   if (a.dc->err != 0) return;
   const uint32_t P = a.dc->n_train;
