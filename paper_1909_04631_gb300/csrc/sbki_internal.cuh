@@ -188,7 +188,7 @@ struct MapState {
   int acc_mode = 0;                     // 0: point-major (global reductions), 1: block-major (shared tile)
   bool soft = false;                    // the update in progress carries soft labels
   int active_map = 0;                   // map index the single-map calls act on
-  sbki_tuning tune{0, 20, 8, 16};       // launch shapes (sbki_set_tuning)
+  sbki_tuning tune{0, 30, 8, 16};       // launch shapes (sbki_set_tuning)
   cudaStream_t rec_stream = nullptr;    // private stream the batched update is recorded on
   cudaGraphExec_t batch_exec[kMaxScans + 1] = {};  // recorded batched updates, by scan count
   int64_t batch_kernels[kMaxScans + 1] = {};       // kernels in each recording
