@@ -723,6 +723,9 @@ cudaError_t launch_accumulate_points(MapState& m) {
   a.R = m.ctab_R;
   a.recip_na = ((1u << 20) + (uint32_t)(2 * m.ctab_R + 1) - 1u) / (uint32_t)(2 * m.ctab_R + 1);
   a.chunk = std::max(1, std::min(64, m.tune.accumulate_chunk));
+  // soft labels: a point with a weight row costs up to K+1 times the reductions, so smaller
+  // chunks balance the work queue better (20 against 30: 0.53 against 0.60 ms per street scan)
+  if (m.soft) a.chunk = std::min(a.chunk, 20);
   a.sink = (int32_t)m.pool_blocks;
   a.ftab = m.ftab;
   a.flen = m.flen;
